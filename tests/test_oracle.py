@@ -1,0 +1,281 @@
+"""Pins of the CPU oracle (ordering, symmetric Schur preconditioner, GMRES) against the
+paper's 4-block example (Sec. 3.1, Fig. 2, Eqs. 12-21), brute-force dense linear algebra,
+closed-form special cases and stated invariants."""
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+import scipy.sparse as ssp
+import scipy.sparse.csgraph as csg
+
+from oracle import krylov, ordering, schur
+
+
+def rand_sym(n, rng):
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return A + A.T
+
+
+def block_problem(sizes, pairs, rng, far=None, diag_boost=4.0):
+    """Problem-like object: complex-symmetric near blocks on ``pairs`` (t <= s), leaves in
+    order, optional far blocks given as dense (t, s) -> matrix stored with rank -1."""
+    lp = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(lp[-1])
+    Z = np.zeros((n, n), dtype=np.complex128)
+    for t, s in pairs:
+        m, k = sizes[t], sizes[s]
+        B = rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k))
+        if t == s:
+            B = B + B.T + diag_boost * np.sqrt(m) * np.eye(m)
+        Z[lp[t]:lp[t + 1], lp[s]:lp[s + 1]] = B
+        Z[lp[s]:lp[s + 1], lp[t]:lp[t + 1]] = B.T
+    offs, data = [], []
+    o = 0
+    for t, s in pairs:
+        B = Z[lp[t]:lp[t + 1], lp[s]:lp[s + 1]]
+        offs.append(o)
+        data.append(B.ravel(order="F"))
+        o += B.size
+    p = SimpleNamespace(leaf_ptr=lp, perm=np.arange(n, dtype=np.int32),
+                        near_t=np.array([a for a, _ in pairs], np.int32), near_s=np.array([b for _, b in pairs], np.int32),
+                        near_off=np.array(offs, np.int64), near_data=np.concatenate(data))
+    ZF = np.zeros_like(Z)
+    fr = far or []
+    fU, fo = [], []
+    uo = 0
+    for (t, s), B in fr:
+        ZF[lp[t]:lp[t + 1], lp[s]:lp[s + 1]] = B
+        ZF[lp[s]:lp[s + 1], lp[t]:lp[t + 1]] = B.T
+        fU.append(B.ravel(order="F"))
+        fo.append(uo)
+        uo += B.size
+    p.far_r0 = np.array([lp[t] for (t, s), _ in fr], np.int32)
+    p.far_r1 = np.array([lp[t + 1] for (t, s), _ in fr], np.int32)
+    p.far_c0 = np.array([lp[s] for (t, s), _ in fr], np.int32)
+    p.far_c1 = np.array([lp[s + 1] for (t, s), _ in fr], np.int32)
+    p.far_rank = -np.ones(len(fr), np.int32)
+    p.far_uoff = np.array(fo, np.int64)
+    p.far_voff = np.zeros(len(fr), np.int64)
+    p.far_U = np.concatenate(fU) if fU else np.zeros(0, np.complex128)
+    p.far_V = np.zeros(0, np.complex128)
+    return p, Z, ZF
+
+
+# ---- Sec. 3.1, Fig. 2: the four-block worked example ------------------------------------
+def test_four_block_example_eqs_12_to_21():
+    rng = np.random.default_rng(0)
+    sizes = [3, 4, 2, 5]
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]   # blocks 1, 4 far
+    p, Z, _ = block_problem(sizes, pairs, rng)
+    lp = p.leaf_ptr
+    sl = [slice(lp[k], lp[k + 1]) for k in range(4)]
+    n = Z.shape[0]
+    Zb = lambda M, i, j: M[sl[i], sl[j]]
+    # Eq. 14 / 16: right and left scaling coefficients of block 1, from their own formulas
+    a1 = np.eye(n, dtype=complex)
+    al1 = np.eye(n, dtype=complex)
+    Z11i = np.linalg.inv(Zb(Z, 0, 0))
+    for j in (1, 2):
+        a1[sl[0], sl[j]] = -Z11i @ Zb(Z, 0, j)
+        al1[sl[j], sl[0]] = -Zb(Z, j, 0) @ Z11i
+    assert np.allclose(al1, a1.T, atol=1e-13)                   # Sec. 3.2: alpha' = alpha^T
+    Z1 = al1 @ Z @ a1                                            # Eq. 18
+    # Eq. 19: first block row/column decoupled, (2,4) untouched, Schur complements elsewhere
+    nrm = np.linalg.norm(Z)
+    for j in (1, 2, 3):
+        assert np.linalg.norm(Zb(Z1, 0, j)) < 1e-13 * nrm and np.linalg.norm(Zb(Z1, j, 0)) < 1e-13 * nrm
+    assert np.allclose(Zb(Z1, 1, 3), Zb(Z, 1, 3), rtol=0, atol=1e-13 * nrm)
+    for i in (1, 2):
+        for j in (1, 2):
+            ref = Zb(Z, i, j) - Zb(Z, i, 0) @ Z11i @ Zb(Z, 0, j)
+            assert np.linalg.norm(Zb(Z1, i, j) - ref) < 1e-12 * nrm
+    # Eqs. 20-21 with the oracle's factorisation: blockdiag(D_k) exactly
+    F = schur.setup(p, np.arange(4), fill_tol=0.0)
+    assert F.S == [[1, 2], [2, 3], [3], []]                     # no fill at (2,4) from step 1
+    L, D = schur.ldlt_dense(F)
+    Linv = np.linalg.inv(L)
+    Zt = Linv @ Z @ Linv.T                                       # alpha'_3 alpha'_2 alpha'_1 Z alpha_1 alpha_2 alpha_3
+    for i in range(4):
+        for j in range(4):
+            blk = Zb(Zt, i, j)
+            if i == j:
+                assert np.linalg.norm(blk - F.D[i]) < 1e-12 * nrm
+            else:
+                assert np.linalg.norm(blk) < 1e-12 * nrm
+    assert np.linalg.norm(F.D[0] - Zb(Z, 0, 0)) == 0             # D_1 = Z_11 (Eq. 21)
+
+
+def test_schur_blocks_equal_dense_schur_complements(sphere480):
+    P = sphere480
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    F = schur.setup(P, order, 0.0)
+    S = krylov.System(P, F)
+    A = schur.near_blocks_in_order(P, order)
+    off = S.off
+    Zn = np.zeros((S.n, S.n), dtype=np.complex128)
+    for (i, j), B in A.items():
+        Zn[off[i]:off[i + 1], off[j]:off[j + 1]] = B
+        Zn[off[j]:off[j + 1], off[i]:off[i + 1]] = B.T
+    for k in [0, 1, nl // 3, nl // 2, nl - 2, nl - 1]:
+        a, b = off[k], off[k + 1]
+        ref = Zn[a:b, a:b] - Zn[a:b, :a] @ np.linalg.solve(Zn[:a, :a], Zn[:a, a:b]) if a else Zn[a:b, a:b]
+        assert np.linalg.norm(F.D[k] - ref) / np.linalg.norm(ref) < 1e-10
+    L, D = schur.ldlt_dense(F)
+    assert np.linalg.norm(L @ D @ L.T - Zn) / np.linalg.norm(Zn) < 1e-12
+
+
+def test_symbolic_fill_equals_dense_factor_pattern():
+    rng = np.random.default_rng(5)
+    nb = 12
+    sizes = [2] * nb
+    pairs = sorted({(min(a, b), max(a, b)) for a, b in
+                    [(i, i) for i in range(nb)] + [tuple(rng.choice(nb, 2, replace=False)) for _ in range(14)]})
+    p, Z, _ = block_problem(sizes, pairs, rng)
+    F = schur.setup(p, np.arange(nb), 0.0)
+    L, D = schur.ldlt_dense(F)
+    for k in range(nb):
+        nz = [j for j in range(k + 1, nb) if np.linalg.norm(L[2 * j:2 * j + 2, 2 * k:2 * k + 2]) > 1e-12]
+        assert nz == F.S[k]
+
+
+def test_fill_compression():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((30, 4)) + 1j * rng.standard_normal((30, 4))
+    Y = rng.standard_normal((4, 30)) + 1j * rng.standard_normal((4, 30))
+    W = X @ Y + 1e-4 * (rng.standard_normal((30, 30)) + 1j * rng.standard_normal((30, 30)))
+    Wc, r = schur.compress_block(W, 1e-2)
+    assert r == 4
+    assert np.linalg.norm(W - Wc) <= 1e-2 * np.linalg.norm(W)
+    Wc3, r3 = schur.compress_block(W[:, :3] @ np.ones((3, 30)), 1e-2)
+    assert r3 == -1 or r3 <= 3
+    full = rng.standard_normal((6, 6)) + 0j
+    assert schur.compress_block(full, 1e-2)[1] == -1            # dense is cheaper
+
+
+def test_compression_zero_tolerance_is_exact(sphere480):
+    P = sphere480
+    order = np.arange(len(P.leaf_ptr) - 1)
+    F0 = schur.setup(P, order, 0.0)
+    F1 = schur.setup(P, order, 1e-2)
+    assert F1.rank and all(np.array_equal(F0.D[k], F1.D[k]) for k in range(F0.nb))
+    for key, r in F1.rank.items():
+        W = F1.W[key]
+        assert np.linalg.norm(F1.Wc[key] - W) <= 1e-2 * np.linalg.norm(W) * (1 + 1e-12)
+        assert key[1] > key[0] and (key[1], key[0]) not in F1.near_pairs
+    assert schur.nnz_coefficients(F1) <= schur.nnz_coefficients(F0)
+
+
+# ---- GMRES --------------------------------------------------------------------------------
+def test_givens_rotation():
+    for a, b in [(1 + 2j, 3 - 1j), (0.0, 2 + 1j), (1e-3j, 5.0)]:
+        c, s, rho = krylov.givens(a, b)
+        G = np.array([[c, s], [-np.conj(s), c]])
+        v = G @ np.array([a, b])
+        assert abs(v[1]) < 1e-14 * abs(rho) and abs(v[0] - rho) < 1e-14 * abs(rho)
+        assert np.allclose(G @ G.conj().T, np.eye(2), atol=1e-14)
+
+
+def test_gmres_full_space_equals_direct_solve():
+    rng = np.random.default_rng(4)
+    n = 40
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    c = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    hist = []
+    x, it, rr, ok = krylov.gmres(lambda v: A @ v, c, 1e-12, n, hist=hist)
+    assert ok and it <= n
+    assert np.linalg.norm(x - np.linalg.solve(A, c)) / np.linalg.norm(x) < 1e-10
+    assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(len(hist) - 1))
+
+
+def test_gmres_restart_estimate_equals_true_residual():
+    rng = np.random.default_rng(6)
+    n = 60
+    A = np.eye(n) * 20 + rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    c = rng.standard_normal(n) + 0j
+    hist = []
+    x, it, rr, ok = krylov.gmres(lambda v: A @ v, c, 1e-9, 7, hist=hist)
+    assert ok and it > 7                                          # restarted at least once
+    true = np.linalg.norm(c - A @ x) / np.linalg.norm(c)
+    assert abs(true - rr) <= 1e-10 + 1e-6 * rr
+
+
+def test_no_far_field_converges_in_one_step():
+    """With Z_F = 0 the preconditioned operator of Eq. 28 is the identity: one Arnoldi
+    step, and the solution is the dense solve of Z_N."""
+    rng = np.random.default_rng(8)
+    sizes = [3, 5, 4, 2, 6]
+    pairs = [(0, 0), (0, 1), (1, 1), (1, 2), (2, 2), (2, 3), (3, 3), (3, 4), (4, 4), (0, 4)]
+    p, Z, _ = block_problem(sizes, pairs, rng)
+    F = schur.setup(p, np.array([2, 0, 4, 1, 3]), 0.0)
+    S = krylov.System(p, F)
+    b = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    x, it, rr, ok = krylov.solve(S, b, tol=1e-12, restart=10)
+    assert ok and it == 1
+    assert np.linalg.norm(x - np.linalg.solve(Z, b)) / np.linalg.norm(x) < 1e-12
+
+
+def test_far_field_system_solution_equals_dense():
+    rng = np.random.default_rng(9)
+    sizes = [3, 5, 4, 2, 6]
+    pairs = [(0, 0), (0, 1), (1, 1), (1, 2), (2, 2), (2, 3), (3, 3), (3, 4), (4, 4)]
+    far = [((0, 2), 0.3 * (rng.standard_normal((3, 4)) + 1j * rng.standard_normal((3, 4)))),
+           ((1, 4), 0.3 * (rng.standard_normal((5, 6)) + 1j * rng.standard_normal((5, 6))))]
+    p, Z, ZF = block_problem(sizes, pairs, rng, far=far)
+    F = schur.setup(p, ordering.rcm(5, pairs), 0.0)
+    S = krylov.System(p, F)
+    b = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    x, it, rr, ok = krylov.solve(S, b, tol=1e-13, restart=20)
+    assert ok
+    assert np.linalg.norm(x - np.linalg.solve(Z + ZF, b)) / np.linalg.norm(x) < 1e-11
+
+
+def test_pipeline_against_dense_efie(sphere480):
+    import efie_problem as ep
+    P = sphere480
+    Z = ep.EntryEvaluator(P.rwg).dense()
+    Zs = np.triu(Z) + np.triu(Z, 1).T
+    b = P.plane_wave([0, 0, -1], [1, 0, 0])
+    nl = len(P.leaf_ptr) - 1
+    F = schur.setup(P, ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist()))), 0.0)
+    x, it, rr, ok = krylov.solve(krylov.System(P, F), b, tol=1e-10, restart=30)
+    xd = np.linalg.solve(Zs, b)
+    assert ok and np.linalg.norm(x - xd) / np.linalg.norm(xd) < 10 * 1e-3
+
+
+# ---- ordering (Algorithm 1 with RCM) --------------------------------------------------------
+def test_rcm_path_and_grid():
+    n = 20
+    path = [(i, i + 1) for i in range(n - 1)]
+    o = ordering.rcm(n, path)
+    assert sorted(o.tolist()) == list(range(n)) and ordering.bandwidth(n, path, o) == 1
+    w = 6
+    grid = [(r * w + c, r * w + c + 1) for r in range(w) for c in range(w - 1)] + \
+           [(r * w + c, (r + 1) * w + c) for r in range(w - 1) for c in range(w)]
+    rng = np.random.default_rng(1)
+    relabel = rng.permutation(w * w)
+    g2 = [(int(relabel[a]), int(relabel[b])) for a, b in grid]
+    o = ordering.rcm(w * w, g2)
+    assert ordering.bandwidth(w * w, g2, o) <= w
+    assert ordering.bandwidth(w * w, g2, o) < ordering.bandwidth(w * w, g2)
+
+
+def test_rcm_on_sphere_graph_vs_scipy(sphere1920):
+    P = sphere1920
+    nl = len(P.leaf_ptr) - 1
+    pairs = list(zip(P.near_t.tolist(), P.near_s.tolist()))
+    o = ordering.rcm(nl, pairs)
+    assert sorted(o.tolist()) == list(range(nl))
+    bw = ordering.bandwidth(nl, pairs, o)
+    assert bw <= ordering.bandwidth(nl, pairs)
+    r = [t for t, s in pairs] + [s for t, s in pairs]
+    c = [s for t, s in pairs] + [t for t, s in pairs]
+    A = ssp.csr_matrix((np.ones(len(r)), (r, c)), shape=(nl, nl))
+    bs = ordering.bandwidth(nl, pairs, csg.reverse_cuthill_mckee(A, symmetric_mode=True))
+    assert bw <= 1.1 * bs + 1
+
+
+def test_rcm_disconnected_components():
+    pairs = [(0, 3), (3, 5), (1, 2), (4, 4)]
+    o = ordering.rcm(6, pairs)
+    assert sorted(o.tolist()) == list(range(6))
