@@ -1,0 +1,216 @@
+/*
+ * hmsolve — GPU (sm_103a) solver for ACA-compressed H-matrix RWG/EFIE systems Z I = V
+ * with the symmetric near-field Schur-complement preconditioner of arXiv 2111.13483.
+ *
+ * Problem statement (Sec. 3.1, Eq. 11): Z = Z_N + Z_F, Z_N the dense near-field leaf
+ * blocks, Z_F the far-field low-rank blocks (Sec. 2, Eqs. 9-10).  The library reorders
+ * the leaf blocks (Sec. 3.3, Algorithm 1, reverse Cuthill-McKee), eliminates the near
+ * field block by block with symmetric Schur complements (Sec. 3.1-3.2, Eqs. 12-21),
+ * optionally compresses the fill-in coefficient blocks (Sec. 3.4), and solves the
+ * block-diagonally preconditioned transformed system (Eqs. 22-28) with restarted GMRES
+ * (Sec. 5).
+ *
+ * Conventions for every call:
+ *   - complex numbers are hm_c128 (interleaved re, im, 16 bytes), matrices column-major;
+ *   - all indices are 0-based; "cluster order" is the order of the leaves of the
+ *     cluster tree, each leaf a contiguous range of positions;
+ *   - every call returns an HM_* status and never aborts; hm_last_error() explains the
+ *     last failure on a handle;
+ *   - host pointers passed in are read during the call only (the library deep-copies);
+ *     output buffers are caller-allocated;
+ *   - a handle is used from one host thread at a time and orders all its GPU work on
+ *     its stream (hm_opts.stream, or a stream it creates).
+ */
+#ifndef HMSOLVE_H
+#define HMSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_ctx *hm_handle;
+typedef struct {
+    double re, im;
+} hm_c128;
+
+enum {
+    HM_OK = 0,
+    HM_EINVAL = -1,     /* bad argument or inconsistent description */
+    HM_ENOMEM = -2,     /* device allocation failed or hbm_budget exceeded */
+    HM_ESINGULAR = -3,  /* a pivot block D_k is numerically singular (Sec. 3.1, Eq. 14) */
+    HM_ENOCONV = -4,    /* maxit reached; the best iterate, iters and relres are written */
+    HM_ETIMEOUT = -5,   /* a device-side bounded wait expired (no hang; context usable) */
+    HM_ECUDA = -6,      /* CUDA runtime error */
+    HM_ESTATE = -7      /* call out of order (e.g. solve before precond_setup) */
+};
+
+/*
+ * H-matrix description (Sec. 2 Eqs. 8-10, Sec. 3.1 Eq. 11).  All arrays host memory.
+ *   n, n_leaves   unknowns and leaf clusters;
+ *   perm[n]       original RWG index of cluster-order position i;
+ *   leaf_ptr[n_leaves+1]  leaf l covers positions [leaf_ptr[l], leaf_ptr[l+1]), 1..64 each;
+ *   near pairs b < n_near: leaves near_t[b] <= near_s[b]; block Z(t-rows, s-cols) is
+ *       stored column-major at near_data + near_off[b] (n_t x n_s entries); the (s, t)
+ *       block is its transpose (Z is complex symmetric, Sec. 3.2).  Every (t, t) pair must
+ *       be present and each unordered pair at most once;
+ *   far blocks b < n_far: cluster-order ranges rows [far_r0, far_r1), cols [far_c0,
+ *       far_c1) with far_r1 <= far_c0 (upper half; the mirrored block is the transpose);
+ *       far_rank[b] = r >= 0: block = U V^T with U (m x r) at far_U + far_uoff[b] and
+ *       V (n x r) at far_V + far_voff[b]; far_rank[b] = -1: dense m x n block at
+ *       far_U + far_uoff[b].  Near and far blocks together must cover every entry once.
+ *   near_len, far_U_len, far_V_len: lengths (entries) of the three data arrays.
+ */
+typedef struct {
+    int32_t n, n_leaves;
+    const int32_t *perm;
+    const int32_t *leaf_ptr;
+    int32_t n_near;
+    const int32_t *near_t, *near_s;
+    const int64_t *near_off;
+    const hm_c128 *near_data;
+    int64_t near_len;
+    int32_t n_far;
+    const int32_t *far_r0, *far_r1, *far_c0, *far_c1;
+    const int32_t *far_rank;
+    const int64_t *far_uoff, *far_voff;
+    const hm_c128 *far_U, *far_V;
+    int64_t far_U_len, far_V_len;
+} hm_desc;
+
+/*
+ *   ordering   0 = keep the cluster order, 1 = reverse Cuthill-McKee (Algorithm 1);
+ *   fill_tol   Sec. 3.4 compression tolerance for fill-in coefficient blocks, 0 = off;
+ *   precision  0 = complex FP64 throughout; 1 = complex FP32 operator/preconditioner
+ *              inside an FP64 refinement loop on Z (FP64 pivots, Arnoldi, residual);
+ *   device     CUDA device ordinal;
+ *   hbm_budget bytes the handle may allocate on the device, 0 = no limit;
+ *   stream     cudaStream_t to order work on, NULL = the library creates one.
+ */
+typedef struct {
+    int32_t ordering;
+    double fill_tol;
+    int32_t precision;
+    int32_t device;
+    size_t hbm_budget;
+    void *stream;
+} hm_opts;
+
+typedef struct {
+    int32_t n, n_blocks;
+    int64_t near_entries;     /* stored near-field entries (t <= s blocks) */
+    int64_t far_entries;      /* stored far-field entries, sum r (m + n) + dense m n */
+    int64_t fill_blocks;      /* sum_k |S_k| coefficient blocks (Sec. 3.3 fill) */
+    int64_t coef_entries;     /* coefficient entries as stored: dense n_k n_j + r (n_k + n_j) */
+    int64_t coef_entries_dense; /* same without compression */
+    int64_t diag_entries;     /* sum_k n_k^2 */
+    int32_t bandwidth;        /* block bandwidth of the near-field graph in solve order */
+    double setup_ms;          /* device time of the last precond_setup */
+    double setup_gflop;       /* algorithmic flops of setup (8 real flops per complex MAC) */
+    size_t device_bytes;      /* bytes currently allocated on the device by the handle */
+} hm_stats;
+
+/* Fills *o with the defaults: RCM, fill_tol 0, FP64, device 0, no budget, own stream. */
+int hm_default_opts(hm_opts *o);
+
+/*
+ * Validates *d, copies the near blocks, far factors and index maps to the device and
+ * plans the solve order (Algorithm 1 steps 1-5) and the symbolic fill of the scaling
+ * coefficients.  On success *out receives a new handle.  HM_EINVAL on a malformed
+ * description, HM_ENOMEM when allocation fails or exceeds opts->hbm_budget.
+ */
+int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out);
+
+/*
+ * Symmetric near-field Schur elimination (Sec. 3.1-3.2): for each block k in solve
+ * order D_k = A_kk, W_kj = D_k^{-1} A_kj (the negated right coefficients, Eq. 14; the
+ * left ones are their transposes), A_ij -= A_ik W_kj for i >= j later neighbours
+ * (Eq. 19); then the Sec. 3.4 compression of fill-in W blocks when fill_tol > 0, and
+ * D_k^{-1} for the Eq. 28 preconditioner.  Idempotent.  HM_ESINGULAR names the block
+ * in hm_last_error.
+ */
+int precond_setup(hm_handle h);
+
+/*
+ * Solves Z I = V for nrhs right-hand sides given in the ORIGINAL RWG order, host
+ * memory: V column j at V + j*ldv, I column j at I + j*ldi (ldv, ldi >= n).  GMRES(restart)
+ * on Eq. 28 until the preconditioned relative residual is <= tol (FP64 mode) or, in
+ * mixed mode, until ||V - Z I|| / ||V|| <= tol.  iters[j] = Arnoldi steps taken for
+ * column j (inner steps in mixed mode), relres[j] = final relative residual of the
+ * criterion above.  Columns are solved in lockstep batches; each column's Krylov space
+ * is its own.  HM_ENOCONV if some column did not converge within maxit (its best
+ * iterate is still written).
+ */
+int solve(hm_handle h, const hm_c128 *V, int32_t nrhs, int64_t ldv, double tol, int32_t restart,
+          int32_t maxit, hm_c128 *I, int64_t ldi, int32_t *iters, double *relres);
+
+/* As solve(), with V and I in device memory (e.g. torch tensors), ordered on the handle's
+ * stream.  iters and relres are host arrays. */
+int solve_device(hm_handle h, const void *dV, int32_t nrhs, int64_t ldv, double tol, int32_t restart,
+                 int32_t maxit, void *dI, int64_t ldi, int32_t *iters, double *relres);
+
+int hmat_stats(hm_handle h, hm_stats *s);
+const char *hm_last_error(hm_handle h);
+void hmat_destroy(hm_handle h);
+
+/* ---- inspection entry points (parity tests and diagnostics) ---------------------- */
+
+/* Solve order: order[p] = leaf (cluster order) placed at block position p.  n_leaves entries. */
+int hm_get_order(hm_handle h, int32_t *order);
+
+/* Symbolic fill S_k of Sec. 3.3: ptr[n_blocks+1] and idx[ptr[n_blocks]] (sorted block
+ * positions > k).  Pass idx = NULL to query ptr only. */
+int hm_get_fill(hm_handle h, int32_t *ptr, int32_t *idx);
+
+/*
+ * Copies factor blocks to host memory after precond_setup, in solve order:
+ *   what 0: D_k        (n_k x n_k)  the scaled near-field block of Eq. 21;
+ *   what 1: D_k^{-1}   (n_k x n_k);
+ *   what 2: W_k        (n_k x sum_{j in S_k} n_j) the coefficient row of block k,
+ *                      uncompressed, blocks in S_k order;
+ *   what 3: same as 2 after Sec. 3.4 compression (low-rank blocks expanded).
+ * out must hold the stated number of entries.
+ */
+int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out);
+
+/*
+ * Applies one operator to nrhs device vectors (solve order, column-major, ld = n):
+ *   op 0: y = A x   with A = D^{-1}[D + L^{-1} Z_F L^{-T}]  (Eq. 28, paper form);
+ *   op 1: y = L^{-1} x     (Eq. 23, the left scalings);
+ *   op 2: y = L^{-T} x     (Eq. 24, the right scalings);
+ *   op 3: y = Z_F x        (far field, Eq. 11);
+ *   op 4: y = D^{-1} x     (Eq. 28 preconditioner solve);
+ *   op 5: y = Z x          (near + far, ORIGINAL order; the refinement residual operator).
+ * x and y must not overlap.
+ */
+int hm_apply(hm_handle h, int32_t op, const void *dx, void *dy, int32_t nrhs);
+
+/* Solution-order index map: new2orig[p] = original RWG index at solve-order position p. */
+int hm_get_index_map(hm_handle h, int32_t *new2orig);
+
+/* ---- host-only planning (no device work, no handle) -------------------------------- */
+
+/*
+ * Algorithm 1 (Sec. 3.3) steps 1-4 on a leaf graph with n_leaves nodes and n_pairs edges
+ * (t[b], s[b]) (self loops and repeats ignored): reverse Cuthill-McKee, components in order
+ * of their lowest node, George-Liu pseudo-peripheral start from the minimum-(degree,
+ * index) node, neighbours by ascending (degree, index), the whole sequence reversed.
+ * order[p] = node placed at position p (n_leaves entries).  HM_EINVAL on bad input.
+ */
+int hm_plan_order(int32_t n_leaves, int32_t n_pairs, const int32_t *t, const int32_t *s, int32_t *order);
+
+/*
+ * Symbolic fill of the scaling coefficients (Sec. 3.3, Figs. 3b-7b): for blocks numbered
+ * 0..n_blocks-1 with near pairs (i[b], j[b]), S_k = later neighbours of k once the
+ * neighbours of every earlier block have been coupled.  ptr[n_blocks+1] always written;
+ * idx (sorted S_k lists) written when non-NULL and ptr[n_blocks] <= idx_cap.
+ */
+int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int32_t *j, int32_t *ptr,
+                 int32_t *idx, int64_t idx_cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

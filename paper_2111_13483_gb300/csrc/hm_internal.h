@@ -1,0 +1,136 @@
+// Internal declarations of the hmsolve library (host planner, device kernels, C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hmsolve.h"
+
+namespace hm {
+
+// ---- device memory accounted against the handle's HBM budget -------------------------
+struct Arena {
+    size_t used = 0, budget = 0;
+    std::vector<void *> ptrs;
+    std::vector<size_t> sizes;
+    cudaError_t alloc(void **p, size_t bytes);
+    void release(void *p, size_t bytes);
+    void release_all();
+};
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+// ---- host plan: solve order, symbolic fill, storage layout ---------------------------
+struct Plan {
+    int nb = 0, n = 0;
+    std::vector<int> order;      // block p -> leaf
+    std::vector<int> pos;        // leaf -> block p
+    std::vector<int> size;       // n_p
+    std::vector<int> boff;       // first unknown of block p in solve order (nb+1)
+    std::vector<int> new2orig;   // solve-order position -> original RWG index
+    std::vector<int> new2cl;     // solve-order position -> cluster-order position
+    std::vector<int> cl2new;     // cluster-order position -> solve-order position
+    // S_k (sorted block positions > k) in CSR; srow[e] = row offset of block S_k[a] inside
+    // the stacked column k (rows = sum over S_k of n_j), M[k] = that total.
+    std::vector<int> sptr, sidx, srow, M;
+    // stacked columns of the A workspace / W panels: entry offsets (same for both)
+    std::vector<int64_t> coff;   // column k: M_k x n_k (A) and n_k x M_k (W panel)
+    std::vector<int64_t> doff;   // diagonal block k: n_k x n_k
+    int64_t coef_entries = 0, diag_entries = 0;
+    // forward sweep gathers: row i <- blocks W_ki, k < i; rptr/ridx = k, rcol = column
+    // offset of block i inside panel k
+    std::vector<int> rptr, ridx, rcol;
+    int bandwidth = 0;
+    double setup_flops = 0;
+    int max_S = 0, max_M = 0;
+    int64_t n_updates = 0;
+};
+
+// far-field incidence lists (cluster order): per leaf l, entries (b << 2 | kind), kind
+// 0 = low-rank row side, 1 = low-rank column side, 2 = dense row side, 3 = dense column side
+struct FarPlan {
+    int nf = 0;
+    int64_t entries = 0;
+    std::vector<int> lptr, lent;
+    int64_t tlen = 0;                 // sum of ranks
+    std::vector<int64_t> toff;        // per block: offset of its rank vectors
+    // near-field incidence lists (cluster order) for Z_N products: per leaf l, entries
+    // (b << 1 | side), side 0 = l is the row leaf t, 1 = l is the column leaf s (t != s)
+    std::vector<int> nptr, nent;
+};
+
+}  // namespace hm
+
+// ---- the handle -------------------------------------------------------------------------
+struct hm_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    hm_opts opts{};
+    std::string err;
+    hm::Arena arena;
+
+    // host copies of the description (index data only)
+    int n = 0, nl = 0;
+    std::vector<int> perm, leaf_ptr, near_t, near_s;
+    std::vector<int64_t> near_off;
+    std::vector<int> far_r0, far_r1, far_c0, far_c1, far_rank;
+    std::vector<int64_t> far_uoff, far_voff;
+    int64_t near_len = 0, farU_len = 0, farV_len = 0;
+
+    hm::Plan plan;
+    hm::FarPlan fplan;
+
+    // device: inputs
+    double2 *d_near = nullptr, *d_farU = nullptr, *d_farV = nullptr;
+    int *d_near_t = nullptr, *d_near_s = nullptr;
+    int64_t *d_near_off = nullptr;
+    int *d_far_r0 = nullptr, *d_far_r1 = nullptr, *d_far_c0 = nullptr, *d_far_c1 = nullptr, *d_far_rank = nullptr;
+    int64_t *d_far_uoff = nullptr, *d_far_voff = nullptr, *d_far_toff = nullptr;
+    int *d_flptr = nullptr, *d_flent = nullptr, *d_nptr = nullptr, *d_nent = nullptr;
+    int *d_leaf_ptr = nullptr, *d_perm = nullptr;
+    int *d_new2cl = nullptr, *d_cl2new = nullptr, *d_new2orig = nullptr, *d_pos = nullptr;
+    // device: plan
+    int *d_size = nullptr, *d_boff = nullptr, *d_sptr = nullptr, *d_sidx = nullptr, *d_srow = nullptr, *d_M = nullptr;
+    int64_t *d_coff = nullptr, *d_doff = nullptr;
+    int *d_rptr = nullptr, *d_ridx = nullptr, *d_rcol = nullptr;
+    // device: setup outputs / workspace
+    double2 *d_A = nullptr;      // stacked columns workspace (scratch during setup)
+    double2 *d_Ad = nullptr;     // diagonal blocks workspace -> D_k after setup
+    double2 *d_W = nullptr;      // coefficient panels W_k (uncompressed)
+    double2 *d_Dinv = nullptr;   // D_k^{-1}
+    bool setup_done = false;
+    double setup_ms = 0;
+    // device: solve workspace
+    int *d_flags = nullptr, *d_ticket = nullptr, *d_err = nullptr;
+    int epoch = 0;
+    double2 *d_t = nullptr, *d_s = nullptr;  // far rank vectors (per rhs column)
+    int t_cols = 0;
+    double2 *d_work = nullptr;               // operator scratch vectors
+    int work_cols = 0;
+};
+
+namespace hm {
+// planner.cpp
+int validate_and_copy(hm_ctx *h, const hm_desc *d);
+void plan_order(hm_ctx *h);
+void plan_far(hm_ctx *h);
+std::vector<int> rcm_order(int nl, const std::vector<int> &t, const std::vector<int> &s);
+void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &pj, std::vector<int> &sptr,
+                   std::vector<int> &sidx);
+
+// kernels (setup.cu / solve.cu): return cudaError_t of the launches
+cudaError_t setup_run(hm_ctx *h, int *bad_block);
+cudaError_t op_apply(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
+cudaError_t z_apply_orig(hm_ctx *h, const double2 *x, double2 *y, int nrhs);
+cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs);
+int gmres_solve(hm_ctx *h, const double2 *dV, int nrhs, int64_t ldv, double tol, int restart, int maxit,
+                double2 *dI, int64_t ldi, int *iters, double *relres);
+}  // namespace hm

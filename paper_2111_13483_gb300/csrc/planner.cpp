@@ -1,0 +1,384 @@
+// Host planner of the hmsolve library: description checks, the near-field block order
+// (Sec. 3.3, Algorithm 1 with reverse Cuthill-McKee), the symbolic fill of the scaling
+// coefficients (Sec. 3.3, Figs. 3b-7b), storage layout and the far-field incidence lists.
+// Integer work only; every floating-point step runs on the device.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+static int fail(hm_ctx *h, const char *msg)
+{
+    h->err = msg;
+    return HM_EINVAL;
+}
+
+int validate_and_copy(hm_ctx *h, const hm_desc *d)
+{
+    if (!d) return fail(h, "null description");
+    if (d->n <= 0 || d->n_leaves <= 0 || d->n_leaves > d->n) return fail(h, "bad n / n_leaves");
+    if (!d->perm || !d->leaf_ptr) return fail(h, "null perm / leaf_ptr");
+    const int n = d->n, nl = d->n_leaves;
+    h->n = n;
+    h->nl = nl;
+    h->perm.assign(d->perm, d->perm + n);
+    h->leaf_ptr.assign(d->leaf_ptr, d->leaf_ptr + nl + 1);
+    if (h->leaf_ptr[0] != 0 || h->leaf_ptr[nl] != n) return fail(h, "leaf_ptr must start at 0 and end at n");
+    for (int l = 0; l < nl; ++l) {
+        int sz = h->leaf_ptr[l + 1] - h->leaf_ptr[l];
+        if (sz < 1 || sz > 64) return fail(h, "leaf sizes must be 1..64");
+    }
+    {
+        std::vector<char> seen(n, 0);
+        for (int i = 0; i < n; ++i) {
+            int p = h->perm[i];
+            if (p < 0 || p >= n || seen[p]) return fail(h, "perm is not a permutation");
+            seen[p] = 1;
+        }
+    }
+    if (d->n_near < nl || !d->near_t || !d->near_s || !d->near_off || !d->near_data)
+        return fail(h, "near pairs missing");
+    h->near_t.assign(d->near_t, d->near_t + d->n_near);
+    h->near_s.assign(d->near_s, d->near_s + d->n_near);
+    h->near_off.assign(d->near_off, d->near_off + d->n_near);
+    h->near_len = d->near_len;
+    std::vector<char> diag(nl, 0);
+    int64_t covered = 0;
+    {
+        std::vector<std::pair<int, int>> pr;
+        pr.reserve(d->n_near);
+        for (int b = 0; b < d->n_near; ++b) {
+            int t = h->near_t[b], s = h->near_s[b];
+            if (t < 0 || s >= nl || t > s) return fail(h, "near pair out of range or t > s");
+            int64_t m = h->leaf_ptr[t + 1] - h->leaf_ptr[t], c = h->leaf_ptr[s + 1] - h->leaf_ptr[s];
+            if (h->near_off[b] < 0 || h->near_off[b] + m * c > d->near_len) return fail(h, "near block outside near_data");
+            if (t == s) diag[t] = 1;
+            covered += (t == s) ? m * c : 2 * m * c;
+            pr.push_back({t, s});
+        }
+        std::sort(pr.begin(), pr.end());
+        for (size_t i = 1; i < pr.size(); ++i)
+            if (pr[i] == pr[i - 1]) return fail(h, "duplicate near pair");
+    }
+    for (int l = 0; l < nl; ++l)
+        if (!diag[l]) return fail(h, "every leaf needs its diagonal near block");
+    const int nf = d->n_far;
+    if (nf < 0) return fail(h, "n_far < 0");
+    if (nf > 0 && (!d->far_r0 || !d->far_r1 || !d->far_c0 || !d->far_c1 || !d->far_rank || !d->far_uoff ||
+                   !d->far_voff || !d->far_U))
+        return fail(h, "far arrays missing");
+    h->far_r0.assign(d->far_r0, d->far_r0 + nf);
+    h->far_r1.assign(d->far_r1, d->far_r1 + nf);
+    h->far_c0.assign(d->far_c0, d->far_c0 + nf);
+    h->far_c1.assign(d->far_c1, d->far_c1 + nf);
+    h->far_rank.assign(d->far_rank, d->far_rank + nf);
+    h->far_uoff.assign(d->far_uoff, d->far_uoff + nf);
+    h->far_voff.assign(d->far_voff, d->far_voff + nf);
+    h->farU_len = d->far_U_len;
+    h->farV_len = d->far_V_len;
+    std::vector<char> is_bound(n + 1, 0);
+    for (int l = 0; l <= nl; ++l) is_bound[h->leaf_ptr[l]] = 1;
+    for (int b = 0; b < nf; ++b) {
+        int r0 = h->far_r0[b], r1 = h->far_r1[b], c0 = h->far_c0[b], c1 = h->far_c1[b], r = h->far_rank[b];
+        if (r0 < 0 || r0 >= r1 || r1 > c0 || c0 >= c1 || c1 > n) return fail(h, "far block ranges invalid");
+        if (!is_bound[r0] || !is_bound[r1] || !is_bound[c0] || !is_bound[c1])
+            return fail(h, "far block ranges must be unions of whole leaves");
+        int64_t m = r1 - r0, c = c1 - c0;
+        if (r < -1 || r > std::min(m, c)) return fail(h, "far rank out of range");
+        if (r < 0) {
+            if (h->far_uoff[b] < 0 || h->far_uoff[b] + m * c > d->far_U_len) return fail(h, "dense far block outside far_U");
+        } else {
+            if (!d->far_V && r > 0) return fail(h, "far_V missing");
+            if (h->far_uoff[b] < 0 || h->far_uoff[b] + m * r > d->far_U_len) return fail(h, "U factor outside far_U");
+            if (h->far_voff[b] < 0 || h->far_voff[b] + c * r > d->far_V_len) return fail(h, "V factor outside far_V");
+        }
+        covered += 2 * m * c;
+    }
+    if (covered != (int64_t)n * n) return fail(h, "near and far blocks do not cover Z exactly once");
+    return HM_OK;
+}
+
+// Reverse Cuthill-McKee on the near-field leaf graph (Algorithm 1, step 3): components in
+// order of their lowest node; George-Liu pseudo-peripheral start searched from the
+// component's minimum-(degree, index) node; neighbours enqueued by ascending (degree,
+// index); the whole sequence reversed.
+static std::vector<std::vector<int>> bfs_levels(const std::vector<std::vector<int>> &adj, int root,
+                                                std::vector<int> &mark, int stamp)
+{
+    std::vector<std::vector<int>> lv{{root}};
+    mark[root] = stamp;
+    while (true) {
+        std::vector<int> nxt;
+        for (int u : lv.back())
+            for (int v : adj[u])
+                if (mark[v] != stamp) {
+                    mark[v] = stamp;
+                    nxt.push_back(v);
+                }
+        if (nxt.empty()) return lv;
+        lv.push_back(std::move(nxt));
+    }
+}
+
+std::vector<int> rcm_order(int nl, const std::vector<int> &t, const std::vector<int> &s)
+{
+    std::vector<std::vector<int>> adj(nl);
+    for (size_t b = 0; b < t.size(); ++b)
+        if (t[b] != s[b]) {
+            adj[t[b]].push_back(s[b]);
+            adj[s[b]].push_back(t[b]);
+        }
+    for (auto &a : adj) {
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+    std::vector<int> deg(nl);
+    for (int i = 0; i < nl; ++i) deg[i] = (int)adj[i].size();
+    auto key_less = [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; };
+    std::vector<char> seen(nl, 0);
+    std::vector<int> mark(nl, -1), seq;
+    seq.reserve(nl);
+    int stamp = 0;
+    for (int s0 = 0; s0 < nl; ++s0) {
+        if (seen[s0]) continue;
+        // component of s0
+        auto comp_lv = bfs_levels(adj, s0, mark, stamp++);
+        int r = -1;
+        for (auto &L : comp_lv)
+            for (int u : L)
+                if (r < 0 || key_less(u, r)) r = u;
+        auto lv = bfs_levels(adj, r, mark, stamp++);
+        while (true) {
+            int x = *std::min_element(lv.back().begin(), lv.back().end(), key_less);
+            auto lx = bfs_levels(adj, x, mark, stamp++);
+            if (lx.size() > lv.size()) {
+                r = x;
+                lv = std::move(lx);
+            } else
+                break;
+        }
+        size_t head = seq.size();
+        seen[r] = 1;
+        seq.push_back(r);
+        while (head < seq.size()) {
+            int u = seq[head++];
+            std::vector<int> nb;
+            for (int v : adj[u])
+                if (!seen[v]) nb.push_back(v);
+            std::sort(nb.begin(), nb.end(), key_less);
+            for (int v : nb) {
+                seen[v] = 1;
+                seq.push_back(v);
+            }
+        }
+    }
+    std::reverse(seq.begin(), seq.end());
+    return seq;
+}
+
+// Symbolic elimination on bitsets (Sec. 3.3, the fill of Figs. 3b-7b): eliminating block
+// k couples every pair of its later neighbours.  Pairs (i, j) in block numbering; returns
+// S_k (sorted, > k) as CSR.
+void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &pj, std::vector<int> &sptr,
+                   std::vector<int> &sidx)
+{
+    const int W = (nl + 63) / 64;
+    std::vector<uint64_t> bits((size_t)nl * W, 0);
+    for (size_t b = 0; b < pi.size(); ++b) {
+        int i = pi[b], j = pj[b];
+        if (i == j) continue;
+        bits[(size_t)i * W + j / 64] |= 1ull << (j % 64);
+        bits[(size_t)j * W + i / 64] |= 1ull << (i % 64);
+    }
+    sptr.assign(nl + 1, 0);
+    sidx.clear();
+    std::vector<uint64_t> mask(W);
+    std::vector<int> later;
+    for (int k = 0; k < nl; ++k) {
+        const uint64_t *row = &bits[(size_t)k * W];
+        std::fill(mask.begin(), mask.end(), 0);
+        later.clear();
+        for (int w = k / 64; w < W; ++w) {
+            uint64_t x = row[w];
+            if (w == k / 64) x &= (k % 64 == 63) ? 0 : (~0ull << (k % 64 + 1));
+            mask[w] = x;
+            while (x) {
+                int bit = __builtin_ctzll(x);
+                later.push_back(w * 64 + bit);
+                x &= x - 1;
+            }
+        }
+        for (int a : later) {
+            uint64_t *ra = &bits[(size_t)a * W];
+            for (int w = k / 64; w < W; ++w) ra[w] |= mask[w];
+        }
+        sidx.insert(sidx.end(), later.begin(), later.end());
+        sptr[k + 1] = (int)sidx.size();
+    }
+}
+
+void plan_order(hm_ctx *h)
+{
+    Plan &P = h->plan;
+    const int nl = h->nl;
+    P.nb = nl;
+    P.n = h->n;
+    if (h->opts.ordering == 1)
+        P.order = rcm_order(nl, h->near_t, h->near_s);
+    else {
+        P.order.resize(nl);
+        std::iota(P.order.begin(), P.order.end(), 0);
+    }
+    P.pos.assign(nl, 0);
+    for (int p = 0; p < nl; ++p) P.pos[P.order[p]] = p;
+    P.size.resize(nl);
+    P.boff.assign(nl + 1, 0);
+    for (int p = 0; p < nl; ++p) {
+        int l = P.order[p];
+        P.size[p] = h->leaf_ptr[l + 1] - h->leaf_ptr[l];
+        P.boff[p + 1] = P.boff[p] + P.size[p];
+    }
+    P.new2cl.resize(h->n);
+    P.new2orig.resize(h->n);
+    P.cl2new.resize(h->n);
+    for (int p = 0; p < nl; ++p) {
+        int l = P.order[p];
+        for (int i = 0; i < P.size[p]; ++i) {
+            int cl = h->leaf_ptr[l] + i;
+            P.new2cl[P.boff[p] + i] = cl;
+            P.cl2new[cl] = P.boff[p] + i;
+            P.new2orig[P.boff[p] + i] = h->perm[cl];
+        }
+    }
+    std::vector<int> bi(h->near_t.size()), bj(h->near_t.size());
+    P.bandwidth = 0;
+    for (size_t b = 0; b < h->near_t.size(); ++b) {
+        bi[b] = P.pos[h->near_t[b]];
+        bj[b] = P.pos[h->near_s[b]];
+        P.bandwidth = std::max(P.bandwidth, std::abs(bi[b] - bj[b]));
+    }
+    symbolic_fill(nl, bi, bj, P.sptr, P.sidx);
+    // layouts
+    P.srow.resize(P.sidx.size());
+    P.M.assign(nl, 0);
+    P.coff.assign(nl + 1, 0);
+    P.doff.assign(nl + 1, 0);
+    P.max_S = 0;
+    P.max_M = 0;
+    P.n_updates = 0;
+    double macs = 0;
+    for (int k = 0; k < nl; ++k) {
+        int acc = 0;
+        for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e) {
+            P.srow[e] = acc;
+            acc += P.size[P.sidx[e]];
+        }
+        P.M[k] = acc;
+        int64_t nk = P.size[k];
+        P.coff[k + 1] = P.coff[k] + (int64_t)acc * nk;
+        P.doff[k + 1] = P.doff[k] + nk * nk;
+        int ns = P.sptr[k + 1] - P.sptr[k];
+        P.max_S = std::max(P.max_S, ns);
+        P.max_M = std::max(P.max_M, acc);
+        P.n_updates += (int64_t)ns * (ns + 1) / 2;
+        // complex MACs: explicit inverse n^3, panel n^2 M, updates sum_{i>=j} n_i n_k n_j
+        macs += (double)nk * nk * nk + (double)nk * nk * acc;
+        double run = 0;
+        for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e) {
+            run += P.size[P.sidx[e]];
+            macs += (double)P.size[P.sidx[e]] * nk * run;
+        }
+    }
+    P.setup_flops = 8.0 * macs;
+    P.coef_entries = P.coff[nl];
+    P.diag_entries = P.doff[nl];
+    // forward-sweep gather lists: row j <- (k, column offset of block j in panel k)
+    std::vector<int> cnt(nl + 1, 0);
+    for (int k = 0; k < nl; ++k)
+        for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e) cnt[P.sidx[e] + 1]++;
+    P.rptr.assign(nl + 1, 0);
+    for (int i = 0; i < nl; ++i) P.rptr[i + 1] = P.rptr[i] + cnt[i + 1];
+    P.ridx.resize(P.rptr[nl]);
+    P.rcol.resize(P.rptr[nl]);
+    std::vector<int> fillp(P.rptr.begin(), P.rptr.end() - 1);
+    for (int k = 0; k < nl; ++k)
+        for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e) {
+            int j = P.sidx[e];
+            P.ridx[fillp[j]] = k;
+            P.rcol[fillp[j]] = P.srow[e];
+            fillp[j]++;
+        }
+}
+
+void plan_far(hm_ctx *h)
+{
+    FarPlan &F = h->fplan;
+    const int nl = h->nl, nf = (int)h->far_rank.size();
+    F.nf = nf;
+    std::vector<int> leaf_of(h->n + 1, -1);
+    for (int l = 0; l < nl; ++l) leaf_of[h->leaf_ptr[l]] = l;
+    std::vector<std::vector<int>> lists(nl);
+    F.toff.assign(nf + 1, 0);
+    for (int b = 0; b < nf; ++b) {
+        bool lr = h->far_rank[b] >= 0;
+        for (int l = leaf_of[h->far_r0[b]]; l < nl && h->leaf_ptr[l] < h->far_r1[b]; ++l)
+            lists[l].push_back((b << 2) | (lr ? 0 : 2));
+        for (int l = leaf_of[h->far_c0[b]]; l < nl && h->leaf_ptr[l] < h->far_c1[b]; ++l)
+            lists[l].push_back((b << 2) | (lr ? 1 : 3));
+        F.toff[b + 1] = F.toff[b] + (lr ? h->far_rank[b] : 0);
+    }
+    F.tlen = F.toff[nf];
+    F.lptr.assign(nl + 1, 0);
+    for (int l = 0; l < nl; ++l) F.lptr[l + 1] = F.lptr[l] + (int)lists[l].size();
+    F.lent.clear();
+    F.lent.reserve(F.lptr[nl]);
+    for (int l = 0; l < nl; ++l) F.lent.insert(F.lent.end(), lists[l].begin(), lists[l].end());
+    std::vector<std::vector<int>> nl_lists(nl);
+    for (size_t b = 0; b < h->near_t.size(); ++b) {
+        nl_lists[h->near_t[b]].push_back((int)(b << 1));
+        if (h->near_t[b] != h->near_s[b]) nl_lists[h->near_s[b]].push_back((int)((b << 1) | 1));
+    }
+    F.nptr.assign(nl + 1, 0);
+    for (int l = 0; l < nl; ++l) F.nptr[l + 1] = F.nptr[l] + (int)nl_lists[l].size();
+    F.nent.clear();
+    for (int l = 0; l < nl; ++l) F.nent.insert(F.nent.end(), nl_lists[l].begin(), nl_lists[l].end());
+    F.entries = 0;
+    for (int b = 0; b < nf; ++b) {
+        int64_t m = h->far_r1[b] - h->far_r0[b], c = h->far_c1[b] - h->far_c0[b];
+        F.entries += h->far_rank[b] < 0 ? m * c : (int64_t)h->far_rank[b] * (m + c);
+    }
+}
+
+}  // namespace hm
+
+// ---- host-only planning entry points (no device work) -----------------------------------
+extern "C" int hm_plan_order(int32_t n_leaves, int32_t n_pairs, const int32_t *t, const int32_t *s, int32_t *order)
+{
+    if (n_leaves <= 0 || n_pairs < 0 || !order || (n_pairs > 0 && (!t || !s))) return HM_EINVAL;
+    for (int b = 0; b < n_pairs; ++b)
+        if (t[b] < 0 || s[b] < 0 || t[b] >= n_leaves || s[b] >= n_leaves) return HM_EINVAL;
+    std::vector<int> tv(t, t + n_pairs), sv(s, s + n_pairs);
+    std::vector<int> o = hm::rcm_order(n_leaves, tv, sv);
+    std::memcpy(order, o.data(), sizeof(int32_t) * n_leaves);
+    return HM_OK;
+}
+
+extern "C" int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int32_t *j, int32_t *ptr,
+                            int32_t *idx, int64_t idx_cap)
+{
+    if (n_blocks <= 0 || n_pairs < 0 || !ptr || (n_pairs > 0 && (!i || !j))) return HM_EINVAL;
+    for (int b = 0; b < n_pairs; ++b)
+        if (i[b] < 0 || j[b] < 0 || i[b] >= n_blocks || j[b] >= n_blocks) return HM_EINVAL;
+    std::vector<int> iv(i, i + n_pairs), jv(j, j + n_pairs), sp, si;
+    hm::symbolic_fill(n_blocks, iv, jv, sp, si);
+    std::memcpy(ptr, sp.data(), sizeof(int32_t) * (n_blocks + 1));
+    if (idx) {
+        if ((int64_t)si.size() > idx_cap) return HM_EINVAL;
+        std::memcpy(idx, si.data(), sizeof(int32_t) * si.size());
+    }
+    return HM_OK;
+}

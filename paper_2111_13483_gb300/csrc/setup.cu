@@ -1,0 +1,339 @@
+// Symmetric near-field Schur-complement setup (Sec. 3.1-3.2, Eqs. 12-21) on the GPU.
+//
+// Storage (solve order, blocks k = 0..nb-1 of n_k <= 64 unknowns):
+//   Ad + doff[k]        A_kk, n_k x n_k; after the step it is D_k (Eq. 21);
+//   A  + coff[k]        stacked column k: the blocks A_jk, j in S_k, one under the other,
+//                       (M_k x n_k, ld M_k), the lower half of the symmetric near field
+//                       plus its fill (scratch during setup);
+//   W  + coff[k]        coefficient panel W_k = D_k^{-1} [A_kj]_{j in S_k} (n_k x M_k,
+//                       ld n_k): W_kj = -alpha_kj of Eq. 14, the left coefficients being
+//                       their transposes (Sec. 3.2);
+//   Dinv + doff[k]      D_k^{-1} for the Eq. 28 preconditioner.
+// Step k: pivot inverse (one CTA), panel (M_k/64 CTAs), Schur updates
+// A_ij -= A_ik W_kj for i >= j in S_k (Eq. 19; one CTA per block pair, diagonal blocks
+// in full).  Stream order gives the step dependencies.
+#include <cstdio>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c)
+{
+    // c + a*b
+    c.x = fma(a.x, b.x, c.x);
+    c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y);
+    c.y = fma(a.y, b.x, c.y);
+    return c;
+}
+
+// row offset of block i inside stacked column j (binary search in S_j); -1 if absent
+__device__ __forceinline__ int find_row(const int *sptr, const int *sidx, const int *srow, int j, int i)
+{
+    int lo = sptr[j], hi = sptr[j + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        int v = sidx[mid];
+        if (v == i) return srow[mid];
+        if (v < i) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+// Near-field blocks (cluster leaves t <= s) into the solve-order workspace.
+__global__ void k_scatter_near(int n_near, const int *near_t, const int *near_s, const int64_t *near_off,
+                               const double2 *near, const int *leaf_ptr, const int *pos, const int *sptr,
+                               const int *sidx, const int *srow, const int *M, const int64_t *coff,
+                               const int64_t *doff, double2 *A, double2 *Ad, int *err)
+{
+    int b = blockIdx.x;
+    if (b >= n_near) return;
+    int t = near_t[b], s = near_s[b];
+    int m = leaf_ptr[t + 1] - leaf_ptr[t], n = leaf_ptr[s + 1] - leaf_ptr[s];
+    const double2 *B = near + near_off[b];
+    int i = pos[t], j = pos[s];
+    double2 *dst;
+    int ld;
+    bool tr;
+    if (i == j) {
+        dst = Ad + doff[i];
+        ld = m;
+        tr = false;
+    } else if (i > j) {
+        int r = find_row(sptr, sidx, srow, j, i);
+        if (r < 0) { atomicExch(err, 0x7fffffff); return; }
+        dst = A + coff[j] + r;
+        ld = M[j];
+        tr = false;
+    } else {
+        int r = find_row(sptr, sidx, srow, i, j);
+        if (r < 0) { atomicExch(err, 0x7fffffff); return; }
+        dst = A + coff[i] + r;
+        ld = M[i];
+        tr = true;
+    }
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+        int rr = e % m, cc = e / m;
+        double2 v = B[e];
+        if (!tr) dst[rr + (int64_t)cc * ld] = v;
+        else dst[cc + (int64_t)rr * ld] = v;
+    }
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting (largest modulus, lowest row on
+// ties) of D_k = Ad[k]; result to Dinv[k].  err <- k+1 on a singular pivot.
+__global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, const int64_t *doff, const double2 *Ad,
+                                                       double2 *Dinv, int *err)
+{
+    extern __shared__ double2 sm[];
+    const int n = size[k];
+    const int ld = n + 1;                      // padded
+    double2 *a = sm;                           // n x ld, row-major a[r*ld + c]
+    double2 *rowc = sm + n * ld;               // n: pivot row after scaling
+    double2 *colc = rowc + n;                  // n: pivot column before the update
+    __shared__ int piv[64];
+    __shared__ int s_p;
+    __shared__ double red_v[256];
+    __shared__ int red_i[256];
+    const double2 *D = Ad + doff[k];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int r = e % n, c = e / n;
+        a[r * ld + c] = D[e];
+    }
+    __syncthreads();
+    for (int c = 0; c < n; ++c) {
+        // pivot search over rows r >= c
+        double best = -1.0;
+        int bi = n;
+        for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+            double2 v = a[r * ld + c];
+            double m = hypot(v.x, v.y);
+            if (m > best || (m == best && r < bi)) { best = m; bi = r; }
+        }
+        red_v[threadIdx.x] = best;
+        red_i[threadIdx.x] = bi;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                double v2 = red_v[threadIdx.x + w];
+                int i2 = red_i[threadIdx.x + w];
+                if (v2 > red_v[threadIdx.x] || (v2 == red_v[threadIdx.x] && i2 < red_i[threadIdx.x])) {
+                    red_v[threadIdx.x] = v2;
+                    red_i[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_p = red_i[0];
+            piv[c] = s_p;
+            double pv = red_v[0];
+            if (!(pv > 1e-300) || !isfinite(pv)) atomicCAS(err, 0, k + 1);
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != c)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                double2 t = a[c * ld + j];
+                a[c * ld + j] = a[p * ld + j];
+                a[p * ld + j] = t;
+            }
+        __syncthreads();
+        double2 pvv = a[c * ld + c];
+        double den = pvv.x * pvv.x + pvv.y * pvv.y;
+        double2 d = make_double2(pvv.x / den, -pvv.y / den);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            rowc[j] = (j == c) ? d : cmul(a[c * ld + j], d);
+            colc[j] = a[j * ld + c];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            int r = e / n, j = e % n;
+            if (r == c) continue;
+            double2 f = colc[r];
+            double2 rc = rowc[j];
+            double2 nv;
+            if (j == c) {
+                nv = cmul(f, d);
+                nv.x = -nv.x;
+                nv.y = -nv.y;
+            } else {
+                double2 cur = a[r * ld + j];
+                nv = make_double2(cur.x - (f.x * rc.x - f.y * rc.y), cur.y - (f.x * rc.y + f.y * rc.x));
+            }
+            a[r * ld + j] = nv;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) a[c * ld + j] = rowc[j];
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int c = n - 1; c >= 0; --c) {
+        int p = piv[c];
+        if (p != c)
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                double2 t = a[r * ld + c];
+                a[r * ld + c] = a[r * ld + p];
+                a[r * ld + p] = t;
+            }
+        __syncthreads();
+    }
+    double2 *out = Dinv + doff[k];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int r = e % n, c = e / n;
+        out[e] = a[r * ld + c];
+    }
+}
+
+// W_k[:, c0:c0+64] = D_k^{-1} (A_col_k[c0:c0+64, :])^T
+__global__ void __launch_bounds__(256) k_panel(int k, const int *size, const int *M, const int64_t *coff,
+                                               const int64_t *doff, const double2 *Dinv, const double2 *A, double2 *W)
+{
+    extern __shared__ double2 psm[];
+    double2 *dinv = psm;              // dinv[r*65 + q] = D_k^{-1}[r, q]
+    double2 *ac = psm + 64 * 65;      // ac[q*65 + col] = A_col[c0+col, q]
+    const int n = size[k], Mk = M[k];
+    const int c0 = blockIdx.x * 64;
+    const int nc = min(64, Mk - c0);
+    const double2 *Di = Dinv + doff[k];
+    const double2 *Ac = A + coff[k];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int r = e % n, q = e / n;
+        dinv[r * 65 + q] = Di[e];
+    }
+    for (int e = threadIdx.x; e < nc * n; e += blockDim.x) {
+        int col = e % nc, q = e / nc;
+        ac[q * 65 + col] = Ac[(c0 + col) + (int64_t)q * Mk];
+    }
+    __syncthreads();
+    double2 *Wk = W + coff[k];
+    for (int e = threadIdx.x; e < n * nc; e += blockDim.x) {
+        int r = e % n, col = e / n;
+        double2 acc = make_double2(0, 0);
+        for (int q = 0; q < n; ++q) acc = cfma(dinv[r * 65 + q], ac[q * 65 + col], acc);
+        Wk[r + (int64_t)(c0 + col) * n] = acc;
+    }
+}
+
+// Schur updates of step k: one CTA per pair (a >= b) of S_k: A_ij -= A_ik W_kj.
+__global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, const int *sptr, const int *sidx,
+                                                const int *srow, const int *M, const int64_t *coff,
+                                                const int64_t *doff, const double2 *W, double2 *A, double2 *Ad)
+{
+    __shared__ double2 As[16][65];   // As[q][r] = A_ik[r, q0+q]
+    __shared__ double2 Ws[16][65];   // Ws[q][c] = W_kj[q0+q, c]
+    // triangular index -> (a, b), a >= b
+    long t = blockIdx.x;
+    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long)(a + 1) * (a + 2) / 2 <= t) ++a;
+    while ((long)a * (a + 1) / 2 > t) --a;
+    int b = (int)(t - (long)a * (a + 1) / 2);
+    if (a >= ns) return;
+    const int e0 = sptr[k];
+    const int i = sidx[e0 + a], j = sidx[e0 + b];
+    const int nk = size[k], ni = size[i], nj = size[j];
+    const int Mk = M[k];
+    const double2 *Aik = A + coff[k] + srow[e0 + a];          // ld Mk
+    const double2 *Wkj = W + coff[k] + (int64_t)srow[e0 + b] * nk;   // ld nk
+    double2 *C;
+    int ldc;
+    if (i == j) {
+        C = Ad + doff[i];
+        ldc = ni;
+    } else {
+        int r = find_row(sptr, sidx, srow, j, i);
+        if (r < 0) return;   // cannot happen when S is the symbolic fill (i in S_j)
+        C = A + coff[j] + r;
+        ldc = M[j];
+    }
+    const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;   // rows tr, tr+32; cols tc + 8y
+    double2 acc[2][8];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = make_double2(0, 0);
+    for (int q0 = 0; q0 < nk; q0 += 16) {
+        const int nq = min(16, nk - q0);
+        for (int e = threadIdx.x; e < ni * nq; e += blockDim.x) {
+            int r = e % ni, q = e / ni;
+            As[q][r] = Aik[r + (int64_t)(q0 + q) * Mk];
+        }
+        for (int e = threadIdx.x; e < nq * nj; e += blockDim.x) {
+            int q = e % nq, c = e / nq;
+            Ws[q][c] = Wkj[(q0 + q) + (int64_t)c * nk];
+        }
+        __syncthreads();
+        for (int q = 0; q < nq; ++q) {
+            double2 a0 = As[q][tr], a1 = As[q][tr + 32];
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+                double2 w = Ws[q][tc + 8 * y];
+                acc[0][y] = cfma(a0, w, acc[0][y]);
+                acc[1][y] = cfma(a1, w, acc[1][y]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+        int r = tr + 32 * x;
+        if (r >= ni) continue;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            int c = tc + 8 * y;
+            if (c >= nj) continue;
+            double2 *p = C + r + (int64_t)c * ldc;
+            double2 v = *p;
+            v.x -= acc[x][y].x;
+            v.y -= acc[x][y].y;
+            *p = v;
+        }
+    }
+}
+
+cudaError_t setup_run(hm_ctx *h, int *bad_block)
+{
+    Plan &P = h->plan;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    *bad_block = -1;
+    if ((e = cudaMemsetAsync(h->d_A, 0, sizeof(double2) * P.coef_entries, st))) return e;
+    if ((e = cudaMemsetAsync(h->d_Ad, 0, sizeof(double2) * P.diag_entries, st))) return e;
+    if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st))) return e;
+    k_scatter_near<<<(int)h->near_t.size(), 128, 0, st>>>((int)h->near_t.size(), h->d_near_t, h->d_near_s,
+                                                          h->d_near_off, h->d_near, h->d_leaf_ptr, h->d_pos,
+                                                          h->d_sptr, h->d_sidx, h->d_srow, h->d_M, h->d_coff,
+                                                          h->d_doff, h->d_A, h->d_Ad, h->d_err);
+    if ((e = cudaGetLastError())) return e;
+    const size_t inv_smem = sizeof(double2) * (64 * 65 + 128);
+    const size_t panel_smem = sizeof(double2) * (2 * 64 * 65);
+    if ((e = cudaFuncSetAttribute(k_pivot_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem)))
+        return e;
+    for (int k = 0; k < P.nb; ++k) {
+        int nk = P.size[k];
+        k_pivot_inverse<<<1, 256, sizeof(double2) * (nk * (nk + 1) + 2 * nk), st>>>(k, h->d_size, h->d_doff, h->d_Ad,
+                                                                               h->d_Dinv, h->d_err);
+        int ns = P.sptr[k + 1] - P.sptr[k];
+        if (ns > 0) {
+            int Mk = P.M[k];
+            k_panel<<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff, h->d_Dinv, h->d_A,
+                                                   h->d_W);
+            long nt = (long)ns * (ns + 1) / 2;
+            k_update<<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx, h->d_srow, h->d_M,
+                                                   h->d_coff, h->d_doff, h->d_W, h->d_A, h->d_Ad);
+        }
+        if ((e = cudaGetLastError())) return e;
+    }
+    int herr = 0;
+    if ((e = cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    if (herr == 0x7fffffff) return cudaErrorInvalidValue;   // plan / pattern mismatch
+    if (herr > 0) *bad_block = herr - 1;
+    return cudaSuccess;
+}
+
+}  // namespace hm

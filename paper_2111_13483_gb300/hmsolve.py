@@ -1,0 +1,271 @@
+"""Python binding of libhmsolve (include/hmsolve.h): argument marshalling only.
+
+Every function keeps its C name.  Host arrays are numpy; device arrays are torch CUDA
+tensors (PyTorch provides device memory and streams, nothing else).  Device vectors are
+passed as tensors of shape (nrhs, n), complex128, contiguous: row j is column j of the
+column-major n x nrhs matrix the library sees (ld = n).
+
+The library is required: importing this module without a built libhmsolve.so raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HM_OK, HM_EINVAL, HM_ENOMEM, HM_ESINGULAR, HM_ENOCONV, HM_ETIMEOUT, HM_ECUDA, HM_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+_NAMES = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_ESINGULAR", -4: "HM_ENOCONV", -5: "HM_ETIMEOUT",
+          -6: "HM_ECUDA", -7: "HM_ESTATE"}
+
+OP_A, OP_LINV, OP_LTINV, OP_ZF, OP_DINV, OP_Z = 0, 1, 2, 3, 4, 5
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class HMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_NAMES.get(code, code), msg))
+        self.code = code
+
+
+class hm_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_leaves", ctypes.c_int32), ("perm", _i32p), ("leaf_ptr", _i32p),
+                ("n_near", ctypes.c_int32), ("near_t", _i32p), ("near_s", _i32p), ("near_off", _i64p),
+                ("near_data", ctypes.c_void_p), ("near_len", ctypes.c_int64), ("n_far", ctypes.c_int32),
+                ("far_r0", _i32p), ("far_r1", _i32p), ("far_c0", _i32p), ("far_c1", _i32p), ("far_rank", _i32p),
+                ("far_uoff", _i64p), ("far_voff", _i64p), ("far_U", ctypes.c_void_p), ("far_V", ctypes.c_void_p),
+                ("far_U_len", ctypes.c_int64), ("far_V_len", ctypes.c_int64)]
+
+
+class hm_opts(ctypes.Structure):
+    _fields_ = [("ordering", ctypes.c_int32), ("fill_tol", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
+class hm_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_blocks", ctypes.c_int32), ("near_entries", ctypes.c_int64),
+                ("far_entries", ctypes.c_int64), ("fill_blocks", ctypes.c_int64), ("coef_entries", ctypes.c_int64),
+                ("coef_entries_dense", ctypes.c_int64), ("diag_entries", ctypes.c_int64),
+                ("bandwidth", ctypes.c_int32), ("setup_ms", ctypes.c_double), ("setup_gflop", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_device", "hmat_stats",
+           "hm_last_error", "hmat_destroy", "hm_get_order", "hm_get_fill", "hm_get_block", "hm_apply",
+           "hm_get_index_map", "hm_plan_order", "hm_plan_fill"]
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Loads libhmsolve.so (building it in place first if asked); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libhmsolve.so is not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(_build.LIB)
+    vp = ctypes.c_void_p
+    L.hm_default_opts.argtypes = [ctypes.POINTER(hm_opts)]
+    L.hmat_create.argtypes = [ctypes.POINTER(hm_desc), ctypes.POINTER(hm_opts), ctypes.POINTER(vp)]
+    L.precond_setup.argtypes = [vp]
+    L.solve.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                        vp, ctypes.c_int64, _i32p, _f64p]
+    L.solve_device.argtypes = L.solve.argtypes
+    L.hmat_stats.argtypes = [vp, ctypes.POINTER(hm_stats)]
+    L.hm_last_error.argtypes = [vp]
+    L.hm_last_error.restype = ctypes.c_char_p
+    L.hmat_destroy.argtypes = [vp]
+    L.hmat_destroy.restype = None
+    L.hm_get_order.argtypes = [vp, _i32p]
+    L.hm_get_index_map.argtypes = [vp, _i32p]
+    L.hm_get_fill.argtypes = [vp, _i32p, _i32p]
+    L.hm_get_block.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
+    L.hm_apply.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32]
+    L.hm_plan_order.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]
+    L.hm_plan_fill.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int64]
+    _lib = L
+    return L
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+class Handle:
+    """Owns an hm_handle; destroyed with the object (or explicitly by hmat_destroy)."""
+
+    def __init__(self, ptr, keep):
+        self.ptr = ptr
+        self._keep = keep
+        self.n = keep["n"]
+        self.n_leaves = keep["nl"]
+
+    def __del__(self):
+        try:
+            hmat_destroy(self)
+        except Exception:
+            pass
+
+    def check(self, code, what):
+        if code != HM_OK:
+            raise HMError(code, "%s: %s" % (what, hm_last_error(self)))
+
+
+def hmat_create(prob, ordering=1, fill_tol=0.0, precision=0, device=0, hbm_budget=0, stream=None):
+    """``prob`` provides perm, leaf_ptr, near_t/near_s/near_off/near_data and
+    far_r0/far_r1/far_c0/far_c1/far_rank/far_uoff/far_voff/far_U/far_V (numpy)."""
+    L = load()
+    k = {}
+    k["perm"] = np.ascontiguousarray(prob.perm, dtype=np.int32)
+    k["leaf_ptr"] = np.ascontiguousarray(prob.leaf_ptr, dtype=np.int32)
+    for f in ("near_t", "near_s", "far_r0", "far_r1", "far_c0", "far_c1", "far_rank"):
+        k[f] = np.ascontiguousarray(getattr(prob, f), dtype=np.int32)
+    for f in ("near_off", "far_uoff", "far_voff"):
+        k[f] = np.ascontiguousarray(getattr(prob, f), dtype=np.int64)
+    for f in ("near_data", "far_U", "far_V"):
+        k[f] = np.ascontiguousarray(getattr(prob, f), dtype=np.complex128)
+    n = len(k["perm"])
+    nl = len(k["leaf_ptr"]) - 1
+    d = hm_desc()
+    d.n, d.n_leaves = n, nl
+    d.perm, d.leaf_ptr = _p(k["perm"], _i32p), _p(k["leaf_ptr"], _i32p)
+    d.n_near = len(k["near_t"])
+    d.near_t, d.near_s, d.near_off = _p(k["near_t"], _i32p), _p(k["near_s"], _i32p), _p(k["near_off"], _i64p)
+    d.near_data, d.near_len = k["near_data"].ctypes.data, len(k["near_data"])
+    d.n_far = len(k["far_rank"])
+    d.far_r0, d.far_r1 = _p(k["far_r0"], _i32p), _p(k["far_r1"], _i32p)
+    d.far_c0, d.far_c1 = _p(k["far_c0"], _i32p), _p(k["far_c1"], _i32p)
+    d.far_rank = _p(k["far_rank"], _i32p)
+    d.far_uoff, d.far_voff = _p(k["far_uoff"], _i64p), _p(k["far_voff"], _i64p)
+    d.far_U, d.far_U_len = k["far_U"].ctypes.data, len(k["far_U"])
+    d.far_V, d.far_V_len = (k["far_V"].ctypes.data if len(k["far_V"]) else None), len(k["far_V"])
+    o = hm_opts()
+    L.hm_default_opts(ctypes.byref(o))
+    o.ordering, o.fill_tol, o.precision, o.device, o.hbm_budget = ordering, fill_tol, precision, device, hbm_budget
+    o.stream = stream
+    h = ctypes.c_void_p()
+    code = L.hmat_create(ctypes.byref(d), ctypes.byref(o), ctypes.byref(h))
+    if code != HM_OK:
+        raise HMError(code, "hmat_create failed (details on stderr)")
+    return Handle(h, {"n": n, "nl": nl})
+
+
+def precond_setup(h):
+    h.check(load().precond_setup(h.ptr), "precond_setup")
+
+
+def solve(h, V, tol=1e-4, restart=30, maxit=5000, raise_on_noconv=False):
+    """V: complex128 array (n,) or (n, nrhs) in the original RWG order (host).
+    Returns (I, iters, relres, status)."""
+    V = np.asarray(V, dtype=np.complex128)
+    one = V.ndim == 1
+    Vf = np.asfortranarray(V.reshape(h.n, -1))
+    nrhs = Vf.shape[1]
+    I = np.zeros((h.n, nrhs), dtype=np.complex128, order="F")
+    iters = np.zeros(nrhs, dtype=np.int32)
+    relres = np.zeros(nrhs, dtype=np.float64)
+    code = load().solve(h.ptr, Vf.ctypes.data, nrhs, h.n, tol, restart, maxit, I.ctypes.data, h.n,
+                        _p(iters, _i32p), _p(relres, _f64p))
+    if code not in (HM_OK, HM_ENOCONV) or (raise_on_noconv and code == HM_ENOCONV):
+        h.check(code, "solve")
+    return (I[:, 0] if one else I), iters, relres, code
+
+
+def solve_device(h, dV, dI, tol=1e-4, restart=30, maxit=5000):
+    """dV, dI: torch complex128 CUDA tensors of shape (nrhs, n), contiguous (original order)."""
+    nrhs = dV.shape[0]
+    iters = np.zeros(nrhs, dtype=np.int32)
+    relres = np.zeros(nrhs, dtype=np.float64)
+    code = load().solve_device(h.ptr, dV.data_ptr(), nrhs, h.n, tol, restart, maxit, dI.data_ptr(), h.n,
+                               _p(iters, _i32p), _p(relres, _f64p))
+    if code not in (HM_OK, HM_ENOCONV):
+        h.check(code, "solve_device")
+    return iters, relres, code
+
+
+def hmat_stats(h):
+    s = hm_stats()
+    h.check(load().hmat_stats(h.ptr, ctypes.byref(s)), "hmat_stats")
+    return {f: getattr(s, f) for f, _ in hm_stats._fields_}
+
+
+def hm_last_error(h):
+    r = load().hm_last_error(h.ptr)
+    return r.decode() if r else ""
+
+
+def hmat_destroy(h):
+    if getattr(h, "ptr", None):
+        load().hmat_destroy(h.ptr)
+        h.ptr = None
+
+
+def hm_get_order(h):
+    out = np.zeros(h.n_leaves, dtype=np.int32)
+    h.check(load().hm_get_order(h.ptr, _p(out, _i32p)), "hm_get_order")
+    return out
+
+
+def hm_get_index_map(h):
+    out = np.zeros(h.n, dtype=np.int32)
+    h.check(load().hm_get_index_map(h.ptr, _p(out, _i32p)), "hm_get_index_map")
+    return out
+
+
+def hm_get_fill(h):
+    ptr = np.zeros(h.n_leaves + 1, dtype=np.int32)
+    L = load()
+    h.check(L.hm_get_fill(h.ptr, _p(ptr, _i32p), None), "hm_get_fill")
+    idx = np.zeros(int(ptr[-1]), dtype=np.int32)
+    h.check(L.hm_get_fill(h.ptr, _p(ptr, _i32p), _p(idx, _i32p)), "hm_get_fill")
+    return ptr, idx
+
+
+def hm_get_block(h, what, k, shape):
+    """Factor block ``what`` (0 D_k, 1 D_k^{-1}, 2 W_k, 3 compressed W_k) of block k,
+    returned as a (rows, cols) array; ``shape`` = (rows, cols) expected."""
+    out = np.zeros(shape[0] * shape[1], dtype=np.complex128)
+    h.check(load().hm_get_block(h.ptr, what, k, out.ctypes.data), "hm_get_block")
+    return out.reshape(shape[1], shape[0]).T
+
+
+def hm_apply(h, op, dx, dy):
+    """dx, dy: torch complex128 CUDA tensors (nrhs, n); solve order except op 5 (original)."""
+    h.check(load().hm_apply(h.ptr, op, dx.data_ptr(), dy.data_ptr(), dx.shape[0]), "hm_apply")
+
+
+def hm_plan_order(n_leaves, t, s):
+    """Host-only Algorithm 1 ordering (no GPU): order[p] = leaf at position p."""
+    t = np.ascontiguousarray(t, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.int32)
+    out = np.zeros(n_leaves, dtype=np.int32)
+    code = load().hm_plan_order(n_leaves, len(t), _p(t, _i32p), _p(s, _i32p), _p(out, _i32p))
+    if code != HM_OK:
+        raise HMError(code, "hm_plan_order")
+    return out
+
+
+def hm_plan_fill(n_blocks, i, j):
+    """Host-only symbolic fill (no GPU): returns [S_0, S_1, ...] as lists."""
+    i = np.ascontiguousarray(i, dtype=np.int32)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    ptr = np.zeros(n_blocks + 1, dtype=np.int32)
+    L = load()
+    code = L.hm_plan_fill(n_blocks, len(i), _p(i, _i32p), _p(j, _i32p), _p(ptr, _i32p), None, 0)
+    if code != HM_OK:
+        raise HMError(code, "hm_plan_fill")
+    idx = np.zeros(max(1, int(ptr[-1])), dtype=np.int32)
+    code = L.hm_plan_fill(n_blocks, len(i), _p(i, _i32p), _p(j, _i32p), _p(ptr, _i32p), _p(idx, _i32p), len(idx))
+    if code != HM_OK:
+        raise HMError(code, "hm_plan_fill")
+    return [idx[ptr[k]:ptr[k + 1]].tolist() for k in range(n_blocks)]

@@ -1,0 +1,147 @@
+"""GPU-vs-oracle parity through the C-ABI (libhmsolve.so) on seeded problems.
+
+Tolerances: FP64 throughout.  Factor blocks and single operator applications agree to
+1e-10 relative (explicit inverses vs LU solves, different summation order); solutions
+of the full preconditioned GMRES to 1e-8 relative 2-norm with iteration counts within
++-1 (the GPU orthogonalises by CGS2, the oracle by MGS: same Krylov space up to rounding).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2111_13483_gb300 as hm
+from oracle import krylov, ordering, schur
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_factor(P, fill_tol=0.0):
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    F = schur.setup(P, order, fill_tol=fill_tol)
+    return order, F, krylov.System(P, F)
+
+
+@pytest.fixture(scope="module")
+def small(sphere480):
+    P = sphere480
+    order, F, S = oracle_factor(P)
+    h = hm.hmat_create(P, ordering=1, fill_tol=0.0)
+    hm.precond_setup(h)
+    return P, order, F, S, h
+
+
+@pytest.fixture(scope="module")
+def cfg1(sphere1920):
+    P = sphere1920
+    order, F, S = oracle_factor(P)
+    h = hm.hmat_create(P, ordering=1, fill_tol=0.0)
+    hm.precond_setup(h)
+    return P, order, F, S, h
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+@pytest.mark.parametrize("which", ["small", "cfg1"])
+def test_order_and_fill_match_oracle(which, request):
+    P, order, F, S, h = request.getfixturevalue(which)
+    assert np.array_equal(hm.hm_get_order(h), order)
+    ptr, idx = hm.hm_get_fill(h)
+    for k in range(F.nb):
+        assert list(idx[ptr[k]:ptr[k + 1]]) == F.S[k]
+    assert np.array_equal(hm.hm_get_index_map(h), S.new2orig)
+
+
+@pytest.mark.parametrize("which", ["small", "cfg1"])
+def test_factor_blocks_match_oracle(which, request):
+    P, order, F, S, h = request.getfixturevalue(which)
+    for k in range(F.nb):
+        nk = int(F.size[k])
+        D = hm.hm_get_block(h, 0, k, (nk, nk))
+        assert rel(D, F.D[k]) < 1e-10, k
+        Di = hm.hm_get_block(h, 1, k, (nk, nk))
+        assert rel(Di, np.linalg.inv(F.D[k])) < 1e-9, k
+        if F.S[k]:
+            M = int(sum(F.size[j] for j in F.S[k]))
+            Wk = hm.hm_get_block(h, 2, k, (nk, M))
+            Wo = np.concatenate([F.W[(k, j)] for j in F.S[k]], axis=1)
+            assert rel(Wk, Wo) < 1e-10, k
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x.T)).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy().T
+
+
+@pytest.mark.parametrize("which", ["small", "cfg1"])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_operators_match_oracle(which, nrhs, request):
+    P, order, F, S, h = request.getfixturevalue(which)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((S.n, nrhs)) + 1j * rng.standard_normal((S.n, nrhs))
+    dx = _dev(X)
+    dy = torch.empty_like(dx)
+    refs = {hm.hmsolve.OP_A: S.apply_A, hm.hmsolve.OP_LINV: S.L_inv, hm.hmsolve.OP_LTINV: S.LT_inv,
+            hm.hmsolve.OP_ZF: S.far_new, hm.hmsolve.OP_DINV: S.D_solve, hm.hmsolve.OP_Z: S.Z_orig}
+    for op, f in refs.items():
+        hm.hm_apply(h, op, dx, dy)
+        torch.cuda.synchronize()
+        Y = _host(dy)
+        for c in range(nrhs):
+            assert rel(Y[:, c], f(X[:, c])) < 1e-10, (op, c)
+
+
+@pytest.mark.parametrize("which", ["small", "cfg1"])
+def test_solve_matches_oracle(which, request):
+    P, order, F, S, h = request.getfixturevalue(which)
+    b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
+    x, it, rr, code = hm.solve(h, b, tol=1e-4, restart=30, maxit=2000)
+    xo, ito, rro, ok = krylov.solve(S, b, tol=1e-4, restart=30)
+    assert code == 0 and ok
+    assert abs(int(it[0]) - ito) <= 1
+    assert rel(x, xo) <= 1e-8
+    assert rr[0] <= 1e-4
+
+
+def test_solve_tight_tolerance_and_restarts(cfg1):
+    P, order, F, S, h = cfg1
+    b = P.plane_wave([1.0, 0.0, 0.0], [0.0, 0.0, 1.0])
+    x, it, rr, code = hm.solve(h, b, tol=1e-10, restart=5, maxit=2000)
+    xo, ito, rro, ok = krylov.solve(S, b, tol=1e-10, restart=5)
+    assert code == 0 and ok and abs(int(it[0]) - ito) <= 1
+    assert rel(x, xo) <= 1e-8
+
+
+def test_multi_rhs_equals_single(cfg1):
+    P, order, F, S, h = cfg1
+    rng = np.random.default_rng(3)
+    B = np.stack([P.plane_wave([np.cos(p), np.sin(p), 0.0], [0.0, 0.0, 1.0]) for p in rng.uniform(0, 6.28, 5)], 1)
+    X, its, rrs, code = hm.solve(h, B, tol=1e-6, restart=30)
+    assert code == 0
+    for c in range(B.shape[1]):
+        x1, it1, rr1, c1 = hm.solve(h, B[:, c], tol=1e-6, restart=30)
+        assert it1[0] == its[c]
+        assert np.array_equal(x1, X[:, c]), c          # batch invariant: bitwise
+
+
+def test_solve_device_matches_host(cfg1):
+    P, order, F, S, h = cfg1
+    b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
+    x, it, rr, code = hm.solve(h, b, tol=1e-6)
+    dV = torch.from_numpy(b[None, :].copy()).cuda()
+    dI = torch.zeros_like(dV)
+    it2, rr2, code2 = hm.solve_device(h, dV, dI, tol=1e-6)
+    assert code2 == 0 and it2[0] == it[0]
+    assert np.array_equal(dI.cpu().numpy()[0], x)
+
+
+def test_true_residual_small(cfg1):
+    P, order, F, S, h = cfg1
+    b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
+    x, it, rr, code = hm.solve(h, b, tol=1e-8)
+    assert np.linalg.norm(b - S.Z_orig(x)) / np.linalg.norm(b) < 1e-6
