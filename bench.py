@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of the preconditioned H-matrix EFIE solve (arXiv 2111.13483) on one GB300.
+
+One step = one pass of the whole hot path over a batch of B plane-wave right-hand sides
+on the 30,720-unknown PEC sphere (icosphere subdivision 5, radius 2.4 lambda, leaf 64,
+eta = 1, ACA 1e-3): precond_setup (pivot inverses, coefficient panels, Schur updates of
+Sec. 3.1-3.2 in reverse Cuthill-McKee order) followed by solve_device (Eq. 28 GMRES(30)
+to a preconditioned relative residual of 1e-4 for all B columns).  The H-matrix and the
+right-hand sides are resident in HBM before timing; every step refactors from the
+resident near-field blocks.  value = RHS solved per second over all ranks.
+
+e2e: the same step through the public API from pinned host memory: hmat_create (upload
+of near blocks, far factors and index maps), precond_setup, solve (host V -> host I),
+hmat_destroy.
+
+--impl reference runs the CPU oracle (numpy, the paper's algorithm step by step) on a
+bounded sample of the same step and extrapolates to a full step (see cpu_baseline.sample).
+
+Multi-GPU: replicas (each rank solves its own batch on its own geometry copy; no
+collective on the data path), weak scaling; barrier + max over ranks around the timed
+region.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere30720")
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--fill-tol", type=float, default=0.0)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def rhs_batch(P, B):
+    """Monostatic plane waves theta = 90 deg, phi_j = 360 j / B, VV (theta-hat) polarisation."""
+    cols = []
+    for j in range(B):
+        ph = 2.0 * np.pi * j / B
+        khat = -np.array([np.cos(ph), np.sin(ph), 0.0])
+        pol = np.array([0.0, 0.0, -1.0])
+        cols.append(P.plane_wave(khat, pol))
+    return np.stack(cols, axis=1)
+
+
+def load_problem(name, rank, world):
+    import efie_problem as ep
+    if world > 1:
+        import torch.distributed as td
+        if rank == 0:
+            P = ep.build(name)
+        td.barrier()
+        if rank != 0:
+            P = ep.build(name)
+        return P
+    return ep.build(name)
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                mx = max(mx, float(v[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, v[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fill_structure(hm, h, P):
+    order = hm.hm_get_order(h)
+    sz = np.diff(P.leaf_ptr)[order].astype(np.int64)
+    ptr, idx = hm.hm_get_fill(h)
+    nnzL = 0
+    upd = 0.0
+    upd_launch = 0
+    for k in range(len(sz)):
+        S = idx[ptr[k]:ptr[k + 1]]
+        if len(S) == 0:
+            continue
+        s = sz[S]
+        nnzL += int(sz[k] * s.sum())
+        cs = np.cumsum(s)
+        upd += 8.0 * sz[k] * float(np.sum(s * cs))          # sum_{i>=j} n_i n_k n_j
+        upd_launch += 1
+    return {"nnzL": nnzL, "diag": int(np.sum(sz * sz)), "update_flops": upd, "update_launches": upd_launch,
+            "order": order, "sz": sz, "ptr": ptr, "idx": idx}
+
+
+def roofline(prof, fs, stats, n, nrhs_launch, prof_steps):
+    """Roofline entry for the kernel class with the largest device time."""
+    cls = max(prof, key=lambda c: prof[c][2])
+    launches, timed, ms = prof[cls]
+    avg_s = ms / max(timed, 1) / 1e3
+    if cls == "update":
+        work = fs["update_flops"] / fs["update_launches"]
+        return cls, {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": work / avg_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                     "work_per_launch": work, "avg_launch_ms": avg_s * 1e3}
+    if cls in ("sweep_fwd", "sweep_bwd"):
+        work = 8.0 * fs["nnzL"] * nrhs_launch
+        return cls, {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": work / avg_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                     "bytes_per_launch": 16.0 * (fs["nnzL"] + 2 * n * nrhs_launch),
+                     "work_per_launch": work, "avg_launch_ms": avg_s * 1e3}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    far_b = 16.0 * stats["far_entries"]
+    work = {"far1": far_b, "far2": far_b}.get(cls, 16.0 * n * nrhs_launch * 2)
+    return cls, {"bound": "hbm", "achieved": work / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": work / avg_s / 1e9 / peaks["hbm_gbs"], "traffic": None, "avg_launch_ms": avg_s * 1e3}
+
+
+def cpu_reference(P, B, iters_per_rhs, fill_tol, budget_s=15.0):
+    """The oracle on a bounded sample of one step, extrapolated to the full step.
+    Returns (seconds per full step, description)."""
+    from oracle import krylov, ordering, schur
+    t0 = time.perf_counter()
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    pos = np.empty(nl, dtype=np.int64)
+    pos[order] = np.arange(nl)
+    pairs = [(int(pos[t]), int(pos[s])) for t, s in zip(P.near_t, P.near_s)]
+    S = schur.symbolic_fill(nl, pairs)
+    t_plan = time.perf_counter() - t0
+    sz = np.diff(P.leaf_ptr)[order].astype(np.int64)
+    step_flops = np.array([8.0 * (sz[k] ** 3 + sz[k] ** 2 * sz[S[k]].sum() + sz[k] *
+                                  float(np.sum(sz[S[k]] * np.cumsum(sz[S[k]])))) if S[k] else 8.0 * sz[k] ** 3
+                           for k in range(nl)])
+    # calibrate the number of elimination steps to ~budget/2 seconds
+    k1 = 8
+    t1 = time.perf_counter()
+    schur.setup(P, order, fill_tol, max_steps=k1)
+    dt1 = time.perf_counter() - t1
+    rate = step_flops[:k1].sum() / max(dt1, 1e-6)
+    ks = k1
+    while ks < nl and step_flops[:ks + 1].sum() / rate < 0.5 * budget_s:
+        ks += 1
+    t1 = time.perf_counter()
+    F = schur.setup(P, order, fill_tol, max_steps=ks)
+    t_samp = time.perf_counter() - t1
+    setup_est = t_plan + t_samp * step_flops.sum() / step_flops[:ks].sum()
+    # operator application: far field (whole), sweeps and block solves over the sampled
+    # blocks, scaled by stored entries
+    sysm = krylov.System(P, F)
+    x = np.random.default_rng(0).standard_normal(sysm.n) + 0j
+    t2 = time.perf_counter()
+    sysm.far_new(x)
+    t_far = time.perf_counter() - t2
+    v = sysm.split(x)
+    W = {key: val for key, val in F.W.items()}
+    t3 = time.perf_counter()
+    for k in range(ks):
+        for j in F.S[k]:
+            v[j] = v[j] - W[(k, j)].T @ v[k]
+    for k in range(ks - 1, -1, -1):
+        for j in F.S[k]:
+            v[k] = v[k] - W[(k, j)] @ v[j]
+    import scipy.linalg as sla
+    for k in range(ks):
+        v[k] = sla.lu_solve(F.lu[k], F.D[k] @ v[k])
+    t_sw = time.perf_counter() - t3
+    nnz_s = sum(int(sz[k] * sz[S[k]].sum()) for k in range(ks))
+    nnz_t = sum(int(sz[k] * sz[S[k]].sum()) for k in range(nl))
+    t_iter = t_far + t_sw * nnz_t / max(nnz_s, 1)
+    step = setup_est + B * (iters_per_rhs + 3) * t_iter
+    desc = ("oracle (numpy, 1 BLAS thread): RCM + symbolic fill in full (%.1f s), first %d of %d Schur elimination "
+            "steps (%.1f s, %.2f%% of setup flops) extrapolated by flops; one far-field product in full (%.1f s); "
+            "sweeps and block solves over the sampled blocks scaled by stored coefficient entries; "
+            "%d RHS x (%.1f GPU-measured iterations + 3 operator applications)"
+            % (t_plan, ks, nl, t_samp, 100 * step_flops[:ks].sum() / step_flops.sum(), t_far, B, iters_per_rhs))
+    return step, desc, time.perf_counter() - t0
+
+
+def run_reference(args):
+    world, rank, local = dist()
+    if rank != 0:
+        return
+    P = load_problem(args.workload, 0, 1)
+    B = args.nrhs
+    iters = float(os.environ.get("HM_REF_ITERS", "0")) or 60.0
+    steps = []
+    desc = ""
+    wall = 0.0
+    for _ in range(args.warmup + args.steps):
+        s, desc, w = cpu_reference(P, B, iters, args.fill_tol, budget_s=10.0)
+        steps.append(s)
+        wall += w
+    st = steps[args.warmup:]
+    ms = 1e3 * float(np.mean(st))
+    val = B / (ms / 1e3)
+    line = {"metric": "RHS/s at rel. residual 1e-4 (30,720-unk sphere)", "value": val, "unit": "RHS/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "PEC sphere r=2.4 lambda, icosphere d=5, 30720 RWG unknowns, leaf 64, eta 1, "
+                                   "ACA 1e-3; %d plane-wave RHS per step, GMRES(%d) tol %g" % (B, args.restart, args.tol),
+                       "nrhs_per_step": B},
+            "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    import paper_2111_13483_gb300 as hm
+    P = load_problem(args.workload, rank, world)
+    B = args.nrhs
+    Vh = rhs_batch(P, B)
+    stream = torch.cuda.current_stream()
+    h = hm.hmat_create(P, ordering=1, fill_tol=args.fill_tol, device=local, stream=stream.cuda_stream)
+    stats = hm.hmat_stats(h)
+    dV = torch.from_numpy(np.ascontiguousarray(Vh.T)).to("cuda")
+    dI = torch.zeros_like(dV)
+    iters_all = []
+
+    def step():
+        hm.precond_setup(h)
+        it, rr, code = hm.solve_device(h, dV, dI, tol=args.tol, restart=args.restart, maxit=5000)
+        if code != 0:
+            raise RuntimeError("solve did not converge (code %d)" % code)
+        iters_all.append(it.copy())
+
+    for _ in range(args.warmup):
+        step()
+    fs = fill_structure(hm.hmsolve, h, P)
+    hm.hm_profile(h, 2)
+    hm.hm_profile(h, 1)
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = e0.elapsed_time(e1)
+    prof = hm.hm_get_profile(h)
+    hm.hm_profile(h, 0)
+    launches = int(sum(v[0] for v in prof.values()))
+    setup_ms = hm.hmat_stats(h)["setup_ms"]
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = B * args.steps * world / (ms_total / 1e3)
+    iters = np.concatenate(iters_all[-args.steps:])
+    cls, roof = roofline(prof, fs, stats, P.n, min(B, 16), args.steps)
+
+    # ---- end to end through the public API from pinned host memory ---------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = {}
+        for f in ("near_data", "far_U", "far_V"):
+            a = getattr(P, f)
+            t = torch.empty(len(a), dtype=torch.complex128).pin_memory()
+            t.numpy()[:] = a
+            pin[f] = t
+        Vp = torch.empty((B, P.n), dtype=torch.complex128).pin_memory()
+        Vp.numpy()[:] = Vh.T
+        Ip = torch.empty((B, P.n), dtype=torch.complex128).pin_memory()
+
+        class PP:
+            pass
+        Q = PP()
+        for f in ("perm", "leaf_ptr", "near_t", "near_s", "near_off", "far_r0", "far_r1", "far_c0", "far_c1",
+                  "far_rank", "far_uoff", "far_voff"):
+            setattr(Q, f, getattr(P, f))
+        for f in pin:
+            setattr(Q, f, pin[f].numpy())
+        h2d = sum(pin[f].numel() * 16 for f in pin) + B * P.n * 16
+        for f in ("perm", "leaf_ptr", "near_t", "near_s", "near_off", "far_r0", "far_r1", "far_c0", "far_c1",
+                  "far_rank", "far_uoff", "far_voff"):
+            h2d += getattr(P, f).nbytes
+        d2h = B * P.n * 16
+        del h
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.e2e_steps):
+            g = hm.hmat_create(Q, ordering=1, fill_tol=args.fill_tol, device=local, stream=stream.cuda_stream)
+            hm.precond_setup(g)
+            I, it2, rr2, code = hm.solve(g, Vp.numpy().T, tol=args.tol, restart=args.restart, maxit=5000)
+            hm.hmat_destroy(g)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": B * args.e2e_steps * world / (ems / 1e3), "unit": "RHS/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ems / args.e2e_steps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and os.environ.get("HM_BENCH_NO_CPU") != "1":
+        s, desc, _ = cpu_reference(P, B, float(np.mean(iters)), args.fill_tol, budget_s=20.0)
+        cpu = {"value": B / s, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": desc}
+    line = {"metric": "RHS/s at rel. residual 1e-4 (30,720-unk sphere)", "value": value, "unit": "RHS/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "PEC sphere r=2.4 lambda, icosphere d=5, 30720 RWG unknowns, leaf 64, eta 1, "
+                                   "ACA 1e-3; %d plane-wave RHS per step (theta 90 deg, phi sweep, VV), "
+                                   "GMRES(%d) tol %g, FP64, fill_tol %g" % (B, args.restart, args.tol, args.fill_tol),
+                       "nrhs_per_step": B, "parallelism": "replicas x%d" % world,
+                       "l2": "inputs larger than L2 (H-matrix %.2f GB, coefficients %.2f GB resident)" % (
+                           16e-9 * (stats["near_entries"] + stats["far_entries"]), 16e-9 * fs["nnzL"])},
+            "setup_ms": setup_ms, "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
+            "solve_rhs_per_s": B / max((ms_step - setup_ms) / 1e3, 1e-9),
+            "roofline": roof, "roofline_kernel": cls,
+            "kernel_ms_per_step": {k: v[2] / args.steps for k, v in prof.items() if v[0]},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+            "stats": {k: stats[k] for k in ("n", "n_blocks", "near_entries", "far_entries", "fill_blocks",
+                                            "coef_entries", "diag_entries", "bandwidth", "setup_gflop")}}
+    s = json.dumps(line)
+    print(s, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(s + "\n")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

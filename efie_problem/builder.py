@@ -279,8 +279,10 @@ SPECS = {
     "plate29800": dict(kind="plate", n=100, w=10.0, jitter=0.1, seed=0, leaf=64, eta=1.0, aca_eps=1e-3),
     # 122,880-unknown sphere: icosphere d=6, radius 5 lambda, ACA 1e-4
     "sphere122880": dict(kind="sphere", d=6, a=5.0, leaf=64, eta=1.0, aca_eps=1e-4),
+    # mid-size sphere (profiling captures, mid-size parity): icosphere d=4, radius 1.2 lambda
+    "sphere7680": dict(kind="sphere", d=4, a=1.2, leaf=64, eta=1.0, aca_eps=1e-3),
     # small cases for tests
-    "sphere480": dict(kind="sphere", d=2, a=0.3, leaf=32, eta=1.0, aca_eps=1e-3),
+    "sphere480":dict(kind="sphere", d=2, a=0.3, leaf=32, eta=1.0, aca_eps=1e-3),
     "plate_tiny": dict(kind="plate", n=8, w=0.8, jitter=0.1, seed=0, leaf=16, eta=1.0, aca_eps=1e-3),
 }
 

@@ -128,8 +128,9 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out);
  * order D_k = A_kk, W_kj = D_k^{-1} A_kj (the negated right coefficients, Eq. 14; the
  * left ones are their transposes), A_ij -= A_ik W_kj for i >= j later neighbours
  * (Eq. 19); then the Sec. 3.4 compression of fill-in W blocks when fill_tol > 0, and
- * D_k^{-1} for the Eq. 28 preconditioner.  Idempotent.  HM_ESINGULAR names the block
- * in hm_last_error.
+ * D_k^{-1} for the Eq. 28 preconditioner.  Every call recomputes the factors from the
+ * resident near-field blocks (same result each time).  HM_ESINGULAR names the block in
+ * hm_last_error.
  */
 int precond_setup(hm_handle h);
 
@@ -189,6 +190,18 @@ int hm_apply(hm_handle h, int32_t op, const void *dx, void *dy, int32_t nrhs);
 
 /* Solution-order index map: new2orig[p] = original RWG index at solve-order position p. */
 int hm_get_index_map(hm_handle h, int32_t *new2orig);
+
+/*
+ * Kernel accounting.  Every launch is counted by kernel class:
+ *   0 near scatter, 1 pivot inverse, 2 coefficient panel, 3 Schur update, 4 forward sweep,
+ *   5 backward sweep, 6 far phase 1, 7 far phase 2, 8 block diagonal, 9 permutations,
+ *   10 near product, 11 dot products, 12 vector updates, 13 small GMRES kernels.
+ * hm_profile(mode): 1 = also time each launch with CUDA events on the handle's stream,
+ * 0 = stop timing, 2 = zero all counters.  hm_get_profile returns, for one class, the
+ * launches counted, the launches timed and their summed device time in ms.
+ */
+int hm_profile(hm_handle h, int32_t mode);
+int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, double *ms);
 
 /* ---- host-only planning (no device work, no handle) -------------------------------- */
 

@@ -67,8 +67,10 @@ def near_blocks_in_order(prob, order):
     return A
 
 
-def setup(prob, order, fill_tol=1e-2):
-    """The preconditioner of Sec. 3 for block order ``order`` (Algorithm 1 output)."""
+def setup(prob, order, fill_tol=1e-2, max_steps=None):
+    """The preconditioner of Sec. 3 for block order ``order`` (Algorithm 1 output).
+    ``max_steps`` stops after that many elimination steps (a timing sample; the factor is
+    then incomplete and only its first steps are valid)."""
     nb = len(order)
     size = np.array([prob.leaf_ptr[order[p] + 1] - prob.leaf_ptr[order[p]] for p in range(nb)], dtype=np.int64)
     A = near_blocks_in_order(prob, order)
@@ -80,7 +82,7 @@ def setup(prob, order, fill_tol=1e-2):
     F.D = []
     F.lu = []
     F.W = {}
-    for k in range(nb):
+    for k in range(nb if max_steps is None else min(nb, max_steps)):
         Dk = A.pop((k, k))
         lu = sla.lu_factor(Dk)
         F.D.append(Dk)

@@ -45,6 +45,62 @@ void Arena::release_all()
     used = 0;
 }
 
+void Prof::begin(cudaStream_t st)
+{
+    if (!on) return;
+    if (pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        pool.push_back(e);
+    }
+    cur_start = pool.back();
+    pool.pop_back();
+    cudaEventRecord(cur_start, st);
+}
+
+void Prof::end(cudaStream_t st, int cls)
+{
+    count[cls]++;
+    if (!on || !cur_start) return;
+    cudaEvent_t e1;
+    if (pool.empty()) cudaEventCreate(&e1);
+    else {
+        e1 = pool.back();
+        pool.pop_back();
+    }
+    cudaEventRecord(e1, st);
+    pending.push_back({cls, {cur_start, e1}});
+    cur_start = nullptr;
+    if (pending.size() > 4096) flush();
+}
+
+void Prof::flush()
+{
+    for (auto &p : pending) {
+        cudaEventSynchronize(p.second.second);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+        this->ms[p.first] += ms;
+        timed[p.first]++;
+        pool.push_back(p.second.first);
+        pool.push_back(p.second.second);
+    }
+    pending.clear();
+}
+
+void Prof::reset()
+{
+    flush();
+    for (int c = 0; c < K_NCLASS; ++c) count[c] = 0, ms[c] = 0, timed[c] = 0;
+}
+
+void Prof::destroy()
+{
+    flush();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+}
+
 template <class T>
 static cudaError_t upload(hm_ctx *h, T **dst, const T *src, size_t count)
 {
@@ -171,8 +227,8 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
 int precond_setup(hm_handle h)
 {
     if (!h) return HM_EINVAL;
-    if (h->setup_done) return HM_OK;
     cudaSetDevice(h->dev);
+    h->setup_done = false;
     Plan &P = h->plan;
     cudaError_t e;
     if (!h->d_W) {
@@ -297,6 +353,7 @@ void hmat_destroy(hm_handle h)
     if (!h) return;
     cudaSetDevice(h->dev);
     cudaStreamSynchronize(h->stream);
+    h->prof.destroy();
     h->arena.release_all();
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -351,6 +408,29 @@ int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out)
     if ((e = cudaMemcpyAsync(out, src, sizeof(double2) * cnt, cudaMemcpyDeviceToHost, h->stream)) ||
         (e = cudaStreamSynchronize(h->stream)))
         return cuda_fail(h, e, "hm_get_block");
+    return HM_OK;
+}
+
+int hm_profile(hm_handle h, int32_t mode)
+{
+    if (!h || mode < 0 || mode > 2) return HM_EINVAL;
+    cudaSetDevice(h->dev);
+    if (mode == 2) h->prof.reset();
+    else {
+        h->prof.flush();
+        h->prof.on = mode == 1;
+    }
+    return HM_OK;
+}
+
+int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, double *ms)
+{
+    if (!h || cls < 0 || cls >= K_NCLASS) return HM_EINVAL;
+    cudaSetDevice(h->dev);
+    h->prof.flush();
+    if (launches) *launches = h->prof.count[cls];
+    if (timed) *timed = h->prof.timed[cls];
+    if (ms) *ms = h->prof.ms[cls];
     return HM_OK;
 }
 

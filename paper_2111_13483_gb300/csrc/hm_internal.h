@@ -27,6 +27,27 @@ struct DBuf {
     size_t n = 0;
 };
 
+// ---- per-kernel-class launch counts and (opt-in) CUDA-event timings ------------------
+enum KClass {
+    K_SCATTER = 0, K_PIVOT, K_PANEL, K_UPDATE, K_SWEEP_FWD, K_SWEEP_BWD, K_FAR1, K_FAR2, K_DIAG, K_PERMUTE,
+    K_NEAR, K_DOTS, K_VEC, K_SMALL, K_NCLASS
+};
+
+struct Prof {
+    bool on = false;
+    int64_t count[K_NCLASS] = {};
+    double ms[K_NCLASS] = {};
+    int64_t timed[K_NCLASS] = {};
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    cudaEvent_t cur_start = nullptr;
+    void begin(cudaStream_t st);
+    void end(cudaStream_t st, int cls);
+    void flush();          // synchronises on the pending events and accumulates ms
+    void reset();
+    void destroy();
+};
+
 // ---- host plan: solve order, symbolic fill, storage layout ---------------------------
 struct Plan {
     int nb = 0, n = 0;
@@ -76,6 +97,7 @@ struct hm_ctx {
     hm_opts opts{};
     std::string err;
     hm::Arena arena;
+    hm::Prof prof;
 
     // host copies of the description (index data only)
     int n = 0, nl = 0;
@@ -116,6 +138,15 @@ struct hm_ctx {
     double2 *d_work = nullptr;               // operator scratch vectors
     int work_cols = 0;
 };
+
+// Launch wrapper: counts every launch by kernel class and, when profiling is on, brackets
+// it with CUDA events on the handle's stream.
+#define HM_LAUNCH(hp, cls, ...)                 \
+    do {                                        \
+        (hp)->prof.begin((hp)->stream);         \
+        __VA_ARGS__;                            \
+        (hp)->prof.end((hp)->stream, (cls));    \
+    } while (0)
 
 namespace hm {
 // planner.cpp

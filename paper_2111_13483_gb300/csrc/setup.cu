@@ -302,10 +302,10 @@ cudaError_t setup_run(hm_ctx *h, int *bad_block)
     if ((e = cudaMemsetAsync(h->d_A, 0, sizeof(double2) * P.coef_entries, st))) return e;
     if ((e = cudaMemsetAsync(h->d_Ad, 0, sizeof(double2) * P.diag_entries, st))) return e;
     if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st))) return e;
-    k_scatter_near<<<(int)h->near_t.size(), 128, 0, st>>>((int)h->near_t.size(), h->d_near_t, h->d_near_s,
+    HM_LAUNCH(h, K_SCATTER, k_scatter_near<<<(int)h->near_t.size(), 128, 0, st>>>((int)h->near_t.size(), h->d_near_t, h->d_near_s,
                                                           h->d_near_off, h->d_near, h->d_leaf_ptr, h->d_pos,
                                                           h->d_sptr, h->d_sidx, h->d_srow, h->d_M, h->d_coff,
-                                                          h->d_doff, h->d_A, h->d_Ad, h->d_err);
+                                                          h->d_doff, h->d_A, h->d_Ad, h->d_err));
     if ((e = cudaGetLastError())) return e;
     const size_t inv_smem = sizeof(double2) * (64 * 65 + 128);
     const size_t panel_smem = sizeof(double2) * (2 * 64 * 65);
@@ -315,16 +315,16 @@ cudaError_t setup_run(hm_ctx *h, int *bad_block)
         return e;
     for (int k = 0; k < P.nb; ++k) {
         int nk = P.size[k];
-        k_pivot_inverse<<<1, 256, sizeof(double2) * (nk * (nk + 1) + 2 * nk), st>>>(k, h->d_size, h->d_doff, h->d_Ad,
-                                                                               h->d_Dinv, h->d_err);
+        HM_LAUNCH(h, K_PIVOT, k_pivot_inverse<<<1, 256, sizeof(double2) * (nk * (nk + 1) + 2 * nk), st>>>(k, h->d_size, h->d_doff, h->d_Ad,
+                                                                               h->d_Dinv, h->d_err));
         int ns = P.sptr[k + 1] - P.sptr[k];
         if (ns > 0) {
             int Mk = P.M[k];
-            k_panel<<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff, h->d_Dinv, h->d_A,
-                                                   h->d_W);
+            HM_LAUNCH(h, K_PANEL, k_panel<<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff, h->d_Dinv, h->d_A,
+                                                   h->d_W));
             long nt = (long)ns * (ns + 1) / 2;
-            k_update<<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx, h->d_srow, h->d_M,
-                                                   h->d_coff, h->d_doff, h->d_W, h->d_A, h->d_Ad);
+            HM_LAUNCH(h, K_UPDATE, k_update<<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx, h->d_srow, h->d_M,
+                                                   h->d_coff, h->d_doff, h->d_W, h->d_A, h->d_Ad));
         }
         if ((e = cudaGetLastError())) return e;
     }

@@ -566,13 +566,13 @@ static cudaError_t sweep(hm_ctx *h, bool forward, const double2 *x, double2 *y, 
     int ep = ++h->epoch;
     size_t smem = sizeof(double2) * (128 * nrhs + 64 * 65);
     if (forward)
-        k_sweep_fwd<<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol,
+        HM_LAUNCH(h, K_SWEEP_FWD, k_sweep_fwd<<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol,
                                                      h->d_coff, h->d_W, x, y, P.n, nrhs, h->d_flags, ep,
-                                                     h->d_ticket, h->d_err);
+                                                     h->d_ticket, h->d_err));
     else
-        k_sweep_bwd<<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow,
+        HM_LAUNCH(h, K_SWEEP_BWD, k_sweep_bwd<<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow,
                                                      h->d_coff, h->d_W, x, y, P.n, nrhs, h->d_flags, ep,
-                                                     h->d_ticket, h->d_err);
+                                                     h->d_ticket, h->d_err));
     return cudaGetLastError();
 }
 
@@ -583,23 +583,23 @@ static cudaError_t far_apply(hm_ctx *h, const double2 *x, double2 *y, int nrhs, 
     FarPlan &F = h->fplan;
     const int n = P.n;
     // u_cl[i] = x[cl2new[i]]: cluster-order copy of the solve-order input
-    k_gather<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_cl2new, x, ucl);
+    HM_LAUNCH(h, K_PERMUTE, k_gather<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_cl2new, x, ucl));
     if (F.nf > 0 && F.tlen > 0)
-        k_far1<<<nblk((int64_t)F.nf * 32, 256), 256, 0, h->stream>>>(
+        HM_LAUNCH(h, K_FAR1, k_far1<<<nblk((int64_t)F.nf * 32, 256), 256, 0, h->stream>>>(
             F.nf, h->d_far_r0, h->d_far_r1, h->d_far_c0, h->d_far_c1, h->d_far_rank, h->d_far_uoff, h->d_far_voff,
-            h->d_far_toff, h->d_farU, h->d_farV, ucl, n, nrhs, h->d_t, h->d_s, F.tlen);
-    k_far2<<<h->nl, 128, 0, h->stream>>>(h->nl, h->d_leaf_ptr, h->d_flptr, h->d_flent, h->d_far_r0, h->d_far_r1,
+            h->d_far_toff, h->d_farU, h->d_farV, ucl, n, nrhs, h->d_t, h->d_s, F.tlen));
+    HM_LAUNCH(h, K_FAR2, k_far2<<<h->nl, 128, 0, h->stream>>>(h->nl, h->d_leaf_ptr, h->d_flptr, h->d_flent, h->d_far_r0, h->d_far_r1,
                                          h->d_far_c0, h->d_far_c1, h->d_far_rank, h->d_far_uoff, h->d_far_voff,
                                          h->d_far_toff, h->d_farU, h->d_farV, h->d_t, h->d_s, ucl, h->d_cl2new, n,
-                                         nrhs, y, F.tlen);
+                                         nrhs, y, F.tlen));
     return cudaGetLastError();
 }
 
 static cudaError_t diag(hm_ctx *h, int mode, const double2 *x, const double2 *w, double2 *y, int nrhs)
 {
     Plan &P = h->plan;
-    k_diag<<<P.nb, 256, sizeof(double2) * 128 * nrhs, h->stream>>>(mode, P.nb, h->d_size, h->d_boff, h->d_doff,
-                                                                    h->d_Ad, h->d_Dinv, x, w, y, P.n, nrhs);
+    HM_LAUNCH(h, K_DIAG, k_diag<<<P.nb, 256, sizeof(double2) * 128 * nrhs, h->stream>>>(mode, P.nb, h->d_size, h->d_boff, h->d_doff,
+                                                                    h->d_Ad, h->d_Dinv, x, w, y, P.n, nrhs));
     return cudaGetLastError();
 }
 
@@ -642,11 +642,11 @@ cudaError_t z_apply_orig(hm_ctx *h, const double2 *x, double2 *y, int nrhs)
     if ((e = ensure_solve_workspace(h, nrhs))) return e;
     const int n = h->plan.n;
     double2 *w0 = h->d_work, *w1 = h->d_work + (size_t)n * nrhs, *w2 = h->d_work + (size_t)2 * n * nrhs;
-    k_gather_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, x, n, w0);
+    HM_LAUNCH(h, K_PERMUTE, k_gather_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, x, n, w0));
     if ((e = far_apply(h, w0, w1, nrhs, w2))) return e;   // leaves the cluster-order copy in w2
-    k_near_mv<<<h->nl, 128, 0, h->stream>>>(h->nl, h->d_leaf_ptr, h->d_nptr, h->d_nent, h->d_near_t, h->d_near_s,
-                                            h->d_near_off, h->d_near, w2, h->d_cl2new, n, nrhs, w1);
-    k_scatter_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, w1, y, n);
+    HM_LAUNCH(h, K_NEAR, k_near_mv<<<h->nl, 128, 0, h->stream>>>(h->nl, h->d_leaf_ptr, h->d_nptr, h->d_nent, h->d_near_t, h->d_near_s,
+                                            h->d_near_off, h->d_near, w2, h->d_cl2new, n, nrhs, w1));
+    HM_LAUNCH(h, K_PERMUTE, k_scatter_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, w1, y, n));
     return cudaGetLastError();
 }
 
@@ -729,9 +729,9 @@ static int gmres_batch(hm_ctx *h, const double2 *cvec, double2 *x, int nc, doubl
     s.hj = hcol;
     // ||v[:, c]|| for all columns -> out (device) and returned to the host
     auto norms = [&](const double2 *v, double *out) {
-        k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, v, v, part, nchunk);
-        k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1, 0);
-        k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, out);
+        HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, v, v, part, nchunk));
+        HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1, 0));
+        HM_LAUNCH(h, K_SMALL, k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, out));
         std::vector<double> nv(nc);
         cudaMemcpyAsync(nv.data(), out, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
@@ -750,7 +750,7 @@ static int gmres_batch(hm_ctx *h, const double2 *cvec, double2 *x, int nc, doubl
             cudaMemcpyAsync(r, cvec, sizeof(double2) * (size_t)n * nc, cudaMemcpyDeviceToDevice, st);
         else {
             if ((e = op_apply(h, 0, x, r, nc))) break;
-            k_sub_from<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>((int64_t)n * nc, cvec, r);
+            HM_LAUNCH(h, K_VEC, k_sub_from<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>((int64_t)n * nc, cvec, r));
         }
         first = false;
         std::vector<double> beta = norms(r, s.nrm);
@@ -772,7 +772,7 @@ static int gmres_batch(hm_ctx *h, const double2 *cvec, double2 *x, int nc, doubl
         }
         if (!any) break;
         cudaMemcpyAsync(s.active, act.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st);
-        k_scale<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.nrm, r, Vb);   // V_0 = r / beta
+        HM_LAUNCH(h, K_VEC, k_scale<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.nrm, r, Vb));   // V_0 = r / beta
         std::vector<double2> g0((size_t)nc * (m + 1), make_double2(0, 0));
         for (int c = 0; c < nc; ++c) g0[(size_t)c * (m + 1)] = make_double2(beta[c], 0);
         cudaMemcpyAsync(s.g, g0.data(), sizeof(double2) * g0.size(), cudaMemcpyHostToDevice, st);
@@ -784,23 +784,23 @@ static int gmres_batch(hm_ctx *h, const double2 *cvec, double2 *x, int nc, doubl
             double2 *vj = Vb + (size_t)j * nc * n, *vj1 = Vb + (size_t)(j + 1) * nc * n;
             if ((e = op_apply(h, 0, vj, w, nc))) break;
             // ||w|| before orthogonalisation (happy-breakdown reference)
-            k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, w, w, part, nchunk);
-            k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1, 0);
-            k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, s.wn);
+            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, w, w, part, nchunk));
+            HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1, 0));
+            HM_LAUNCH(h, K_SMALL, k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, s.wn));
             // CGS2: h = V^H w, w -= V h, twice; h accumulated in hcol
-            k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, j + 1, Vb, w, part, nchunk);
-            k_dots_final<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, nchunk, part, hcol, m + 1, 0);
-            k_axpy_basis<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, j + 1, Vb, hcol, m + 1, w);
-            k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, j + 1, Vb, w, part, nchunk);
-            k_dots_final<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, nchunk, part, h2, m + 1, 0);
-            k_axpy_basis<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, j + 1, Vb, h2, m + 1, w);
-            k_hfold<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, h2, m + 1, hcol, m + 1);
+            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, j + 1, Vb, w, part, nchunk));
+            HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, nchunk, part, hcol, m + 1, 0));
+            HM_LAUNCH(h, K_VEC, k_axpy_basis<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, j + 1, Vb, hcol, m + 1, w));
+            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, j + 1, Vb, w, part, nchunk));
+            HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, nchunk, part, h2, m + 1, 0));
+            HM_LAUNCH(h, K_VEC, k_axpy_basis<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, j + 1, Vb, h2, m + 1, w));
+            HM_LAUNCH(h, K_SMALL, k_hfold<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, h2, m + 1, hcol, m + 1));
             // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
-            k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, w, w, part, nchunk);
-            k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1, 0);
-            k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, s.nrm);
-            k_scale<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.nrm, w, vj1);
-            k_givens<<<nblk(nc, 64), 64, 0, st>>>(nc, m, j, s, 0.0);
+            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, w, w, part, nchunk));
+            HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1, 0));
+            HM_LAUNCH(h, K_SMALL, k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, s.nrm));
+            HM_LAUNCH(h, K_VEC, k_scale<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.nrm, w, vj1));
+            HM_LAUNCH(h, K_SMALL, k_givens<<<nblk(nc, 64), 64, 0, st>>>(nc, m, j, s, 0.0));
             cudaMemcpyAsync(res.data(), s.res, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
             cudaMemcpyAsync(wpre.data(), s.wn, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
             cudaMemcpyAsync(wn.data(), s.nrm, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
@@ -827,8 +827,8 @@ static int gmres_batch(hm_ctx *h, const double2 *cvec, double2 *x, int nc, doubl
         }
         if (e) break;
         // x += V y per column (J[c] = steps of this cycle, 0 for columns that sat it out)
-        k_trisolve<<<nblk(nc, 64), 64, 0, st>>>(nc, m, s);
-        k_update_x<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.J, Vb, s.y, m, x);
+        HM_LAUNCH(h, K_SMALL, k_trisolve<<<nblk(nc, 64), 64, 0, st>>>(nc, m, s));
+        HM_LAUNCH(h, K_VEC, k_update_x<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.J, Vb, s.y, m, x));
         if ((e = cudaStreamSynchronize(st))) break;
         bool all_done = true;
         for (int c = 0; c < nc; ++c)
@@ -874,7 +874,7 @@ int gmres_solve(hm_ctx *h, const double2 *dV, int nrhs, int64_t ldv, double tol,
     for (int c0 = 0; c0 < nrhs && status != HM_ECUDA && status != HM_ETIMEOUT; c0 += BATCH) {
         const int nc = std::min(BATCH, nrhs - c0);
         // b (original order) -> solve order; c = D^{-1} L^{-1} b
-        k_gather_cols<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, h->d_new2orig, dV + c0 * ldv, ldv, bnew);
+        HM_LAUNCH(h, K_PERMUTE, k_gather_cols<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, h->d_new2orig, dV + c0 * ldv, ldv, bnew));
         if ((e = op_apply(h, 1, bnew, xt, nc)) || (e = op_apply(h, 4, xt, cvec, nc))) {
             status = HM_ECUDA;
             break;
@@ -891,7 +891,7 @@ int gmres_solve(hm_ctx *h, const double2 *dV, int nrhs, int64_t ldv, double tol,
             status = HM_ECUDA;
             break;
         }
-        k_scatter_cols<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, h->d_new2orig, bnew, dI + c0 * ldi, ldi);
+        HM_LAUNCH(h, K_PERMUTE, k_scatter_cols<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, h->d_new2orig, bnew, dI + c0 * ldi, ldi));
     }
     if (status != HM_ECUDA && (e = cudaStreamSynchronize(st))) status = HM_ECUDA;
     int herr = 0;

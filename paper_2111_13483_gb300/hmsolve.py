@@ -55,7 +55,10 @@ class hm_stats(ctypes.Structure):
 
 EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_device", "hmat_stats",
            "hm_last_error", "hmat_destroy", "hm_get_order", "hm_get_fill", "hm_get_block", "hm_apply",
-           "hm_get_index_map", "hm_plan_order", "hm_plan_fill"]
+           "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile"]
+
+KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
+          "near", "dots", "vec", "small"]
 
 _lib = None
 
@@ -93,6 +96,8 @@ def load(build_if_missing=True):
     L.hm_apply.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32]
     L.hm_plan_order.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]
     L.hm_plan_fill.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int64]
+    L.hm_profile.argtypes = [vp, ctypes.c_int32]
+    L.hm_get_profile.argtypes = [vp, ctypes.c_int32, _i64p, _i64p, _f64p]
     _lib = L
     return L
 
@@ -269,3 +274,19 @@ def hm_plan_fill(n_blocks, i, j):
     if code != HM_OK:
         raise HMError(code, "hm_plan_fill")
     return [idx[ptr[k]:ptr[k + 1]].tolist() for k in range(n_blocks)]
+
+
+def hm_profile(h, mode):
+    """mode 1: time every launch with CUDA events; 0: stop timing; 2: zero the counters."""
+    h.check(load().hm_profile(h.ptr, mode), "hm_profile")
+
+
+def hm_get_profile(h):
+    """{class name: (launches, timed launches, device ms)} for every kernel class."""
+    out = {}
+    L = load()
+    for c, name in enumerate(KCLASS):
+        a, b, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        h.check(L.hm_get_profile(h.ptr, c, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)), "hm_get_profile")
+        out[name] = (a.value, b.value, ms.value)
+    return out
