@@ -203,6 +203,21 @@ int hm_get_index_map(hm_handle h, int32_t *new2orig);
 int hm_profile(hm_handle h, int32_t mode);
 int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, double *ms);
 
+/*
+ * Far-field product y = Z_F x (as hm_apply op 3) that allocates no device memory; the paper
+ * has no counterpart, it exists for callers that must not call cudaMalloc / cudaFree at
+ * the point of the call (cudaFree synchronises the whole device, which a serving loop with
+ * several busy streams cannot afford; a process whose device memory sits in another
+ * allocator's pool may see cudaMalloc fail).  x, y: nrhs device vectors in solve order,
+ * column-major, ld = n, not overlapping.  Scratch is one static 16 MiB device array
+ * (1,048,576 complex doubles) held by every GPU that loads the library until exit; a call
+ * needing more than n*nrhs + 2*sum(rank)*nrhs entries of it returns HM_EINVAL.  The first
+ * call on a device looks up the array's device address: make it before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU race and must be serialised.
+ * Synchronises the handle's stream before returning.
+ */
+int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
+
 /* ---- host-only planning (no device work, no handle) -------------------------------- */
 
 /*

@@ -55,7 +55,8 @@ class hm_stats(ctypes.Structure):
 
 EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_device", "hmat_stats",
            "hm_last_error", "hmat_destroy", "hm_get_order", "hm_get_fill", "hm_get_block", "hm_apply",
-           "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile"]
+           "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
+           "hm_far_apply_noalloc"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small"]
@@ -98,6 +99,7 @@ def load(build_if_missing=True):
     L.hm_plan_fill.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int64]
     L.hm_profile.argtypes = [vp, ctypes.c_int32]
     L.hm_get_profile.argtypes = [vp, ctypes.c_int32, _i64p, _i64p, _f64p]
+    L.hm_far_apply_noalloc.argtypes = [vp, vp, vp, ctypes.c_int32]
     _lib = L
     return L
 
@@ -290,3 +292,10 @@ def hm_get_profile(h):
         h.check(L.hm_get_profile(h.ptr, c, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)), "hm_get_profile")
         out[name] = (a.value, b.value, ms.value)
     return out
+
+
+def hm_far_apply_noalloc(h, dx, dy):
+    """y = Z_F x without any device allocation (static library scratch; see the header).
+    dx, dy: torch complex128 CUDA tensors (nrhs, n) in solve order.  Returns the status code
+    (HM_EINVAL when the call needs more scratch than the static array holds)."""
+    return load().hm_far_apply_noalloc(h.ptr, dx.data_ptr(), dy.data_ptr(), dx.shape[0])
