@@ -35,7 +35,8 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 FMA/clk/SM x 2 flop x max SM clock
 
 
 def parse():
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--fill-tol", type=float, default=0.0)
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: complex FP64; 1: complex-FP32 operator inside FP64 refinement")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
@@ -155,30 +158,46 @@ def fill_structure(hm, h, P):
             "order": order, "sz": sz, "ptr": ptr, "idx": idx}
 
 
-def roofline(prof, fs, stats, n, nrhs_launch, prof_steps):
+def roofline(prof, fs, stats, n, nrhs_launch, precision):
     """Roofline entry for the kernel class with the largest device time."""
     cls = max(prof, key=lambda c: prof[c][2])
     launches, timed, ms = prof[cls]
     avg_s = ms / max(timed, 1) / 1e3
-    if cls == "update":
-        work = fs["update_flops"] / fs["update_launches"]
-        return cls, {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": work / avg_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "work_per_launch": work, "avg_launch_ms": avg_s * 1e3}
-    if cls in ("sweep_fwd", "sweep_bwd"):
-        work = 8.0 * fs["nnzL"] * nrhs_launch
-        return cls, {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": work / avg_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "bytes_per_launch": 16.0 * (fs["nnzL"] + 2 * n * nrhs_launch),
-                     "work_per_launch": work, "avg_launch_ms": avg_s * 1e3}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-    far_b = 16.0 * stats["far_entries"]
-    work = {"far1": far_b, "far2": far_b}.get(cls, 16.0 * n * nrhs_launch * 2)
-    return cls, {"bound": "hbm", "achieved": work / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": work / avg_s / 1e9 / peaks["hbm_gbs"], "traffic": None, "avg_launch_ms": avg_s * 1e3}
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if "when" in peaks else "fallback 6.8 TB/s"
+    E = 8.0 if precision == 1 else 16.0
+    alu_peak = FP32_PEAK_TFLOPS if precision == 1 else FP64_PEAK_TFLOPS
+    alu_src = ("derived: 152 SMs x %d %s FMA/clk x 2 flop x 2.07 GHz" % ((128, "FP32") if precision == 1 else (2, "FP64")))
+
+    def alu(work, extra):
+        d = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+             "frac": work / avg_s / 1e12 / alu_peak, "traffic": None, "peak_source": alu_src,
+             "work_per_launch": work, "avg_launch_ms": avg_s * 1e3}
+        d.update(extra)
+        return d
+
+    def hbm(bytes_, extra):
+        d = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "frac": bytes_ / avg_s / 1e9 / peaks["hbm_gbs"], "traffic": None, "peak_source": hbm_src,
+             "bytes_per_launch": bytes_, "avg_launch_ms": avg_s * 1e3}
+        d.update(extra)
+        return d
+
+    if cls == "update":
+        return cls, alu(fs["update_flops"] / fs["update_launches"], {})
+    if cls in ("sweep_fwd", "sweep_bwd"):
+        flops = 8.0 * fs["nnzL"] * nrhs_launch
+        bytes_ = E * (fs["nnzL"] + 2 * n * nrhs_launch)
+        # FP64: 0.5 flop/B x 6.8 TB/s exceeds the FP64 pipe, so the ALU bounds it
+        return cls, (hbm(bytes_, {"flops_per_launch": flops}) if precision == 1
+                     else alu(flops, {"bytes_per_launch": bytes_}))
+    if cls in ("far1", "far2"):
+        bytes_ = E * stats["far_entries"]
+        flops = 8.0 * stats["far_entries"] * nrhs_launch
+        return cls, (hbm(bytes_, {"flops_per_launch": flops}) if precision == 1
+                     else alu(flops, {"bytes_per_launch": bytes_}))
+    return cls, hbm(16.0 * n * nrhs_launch * 2, {})
 
 
 def cpu_reference(P, B, iters_per_rhs, fill_tol, budget_s=15.0):
@@ -284,7 +303,8 @@ def run_ours(args):
     B = args.nrhs
     Vh = rhs_batch(P, B)
     stream = torch.cuda.current_stream()
-    h = hm.hmat_create(P, ordering=1, fill_tol=args.fill_tol, device=local, stream=stream.cuda_stream)
+    h = hm.hmat_create(P, ordering=1, fill_tol=args.fill_tol, precision=args.precision, device=local,
+                       stream=stream.cuda_stream)
     stats = hm.hmat_stats(h)
     dV = torch.from_numpy(np.ascontiguousarray(Vh.T)).to("cuda")
     dI = torch.zeros_like(dV)
@@ -329,7 +349,7 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     value = B * args.steps * world / (ms_total / 1e3)
     iters = np.concatenate(iters_all[-args.steps:])
-    cls, roof = roofline(prof, fs, stats, P.n, min(B, 16), args.steps)
+    cls, roof = roofline(prof, fs, stats, P.n, min(B, 16), args.precision)
 
     # ---- end to end through the public API from pinned host memory ---------------------
     e2e = None
@@ -365,7 +385,8 @@ def run_ours(args):
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for _ in range(args.e2e_steps):
-            g = hm.hmat_create(Q, ordering=1, fill_tol=args.fill_tol, device=local, stream=stream.cuda_stream)
+            g = hm.hmat_create(Q, ordering=1, fill_tol=args.fill_tol, precision=args.precision, device=local,
+                               stream=stream.cuda_stream)
             hm.precond_setup(g)
             I, it2, rr2, code = hm.solve(g, Vp.numpy().T, tol=args.tol, restart=args.restart, maxit=5000)
             hm.hmat_destroy(g)
@@ -387,10 +408,14 @@ def run_ours(args):
         cpu = {"value": B / s, "unit": "RHS/s", "cores": 1, "kind": "oracle", "sample": desc}
     line = {"metric": "RHS/s at rel. residual 1e-4 (30,720-unk sphere)", "value": value, "unit": "RHS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+c128" if args.precision == 1 else "c128", "data": "synthetic",
             "config": {"workload": "PEC sphere r=2.4 lambda, icosphere d=5, 30720 RWG unknowns, leaf 64, eta 1, "
                                    "ACA 1e-3; %d plane-wave RHS per step (theta 90 deg, phi sweep, VV), "
-                                   "GMRES(%d) tol %g, FP64, fill_tol %g" % (B, args.restart, args.tol, args.fill_tol),
+                                   "GMRES(%d) tol %g, %s, fill_tol %g" % (
+                                       B, args.restart, args.tol,
+                                       "complex-FP32 operator + FP64 refinement on ||V - Z I||/||V||"
+                                       if args.precision == 1 else "FP64, preconditioned residual", args.fill_tol),
                        "nrhs_per_step": B, "parallelism": "replicas x%d" % world,
                        "l2": "inputs larger than L2 (H-matrix %.2f GB, coefficients %.2f GB resident)" % (
                            16e-9 * (stats["near_entries"] + stats["far_entries"]), 16e-9 * fs["nnzL"])},

@@ -193,7 +193,8 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
         (e = upload(h, &h->d_far_r1, h->far_r1)) || (e = upload(h, &h->d_far_c0, h->far_c0)) ||
         (e = upload(h, &h->d_far_c1, h->far_c1)) || (e = upload(h, &h->d_far_rank, h->far_rank)) ||
         (e = upload(h, &h->d_far_uoff, h->far_uoff)) || (e = upload(h, &h->d_far_voff, h->far_voff)) ||
-        (e = upload(h, &h->d_far_toff, F.toff)) || (e = upload(h, &h->d_flptr, F.lptr)) ||
+        (e = upload(h, &h->d_far_toff, F.toff)) || (e = upload(h, &h->d_far_item, F.item_blk)) ||
+        (e = upload(h, &h->d_flptr, F.lptr)) ||
         (e = upload(h, &h->d_flent, F.lent)) || (e = upload(h, &h->d_nptr, F.nptr)) ||
         (e = upload(h, &h->d_nent, F.nent)) || (e = upload(h, &h->d_leaf_ptr, h->leaf_ptr)) ||
         (e = upload(h, &h->d_new2cl, P.new2cl)) || (e = upload(h, &h->d_cl2new, P.cl2new)) ||
@@ -213,7 +214,8 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
     }
     if ((e = h->arena.alloc((void **)&h->d_err, sizeof(int))) ||
         (e = h->arena.alloc((void **)&h->d_ticket, sizeof(int))) ||
-        (e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream)) || (e = cudaStreamSynchronize(h->stream))) {
+        (e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream)) ||
+        (h->opts.precision == 1 && (e = make_fp32_copies(h, false))) || (e = cudaStreamSynchronize(h->stream))) {
         int s = cuda_fail(h, e, "hmat_create");
         h->arena.release_all();
         if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -245,6 +247,7 @@ int precond_setup(hm_handle h)
     cudaEventRecord(e0, h->stream);
     int bad = -1;
     e = setup_run(h, &bad);
+    if (!e && bad < 0 && h->opts.precision == 1) e = make_fp32_copies(h, true);
     cudaEventRecord(e1, h->stream);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -436,7 +439,7 @@ int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, 
 
 int hm_apply(hm_handle h, int32_t op, const void *dx, void *dy, int32_t nrhs)
 {
-    if (!h || !dx || !dy || nrhs < 1 || nrhs > 64 || op < 0 || op > 5) return HM_EINVAL;
+    if (!h || !dx || !dy || nrhs < 1 || op < 0 || op > 5) return HM_EINVAL;
     if (op != 3 && op != 5 && !h->setup_done) {
         h->err = "hm_apply: operator needs precond_setup";
         return HM_ESTATE;

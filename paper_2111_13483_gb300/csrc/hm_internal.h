@@ -82,6 +82,7 @@ struct FarPlan {
     std::vector<int> lptr, lent;
     int64_t tlen = 0;                 // sum of ranks
     std::vector<int64_t> toff;        // per block: offset of its rank vectors
+    std::vector<int> item_blk;        // rank item e (toff[b] <= e < toff[b+1]) -> block b
     // near-field incidence lists (cluster order) for Z_N products: per leaf l, entries
     // (b << 1 | side), side 0 = l is the row leaf t, 1 = l is the column leaf s (t != s)
     std::vector<int> nptr, nent;
@@ -116,7 +117,7 @@ struct hm_ctx {
     int64_t *d_near_off = nullptr;
     int *d_far_r0 = nullptr, *d_far_r1 = nullptr, *d_far_c0 = nullptr, *d_far_c1 = nullptr, *d_far_rank = nullptr;
     int64_t *d_far_uoff = nullptr, *d_far_voff = nullptr, *d_far_toff = nullptr;
-    int *d_flptr = nullptr, *d_flent = nullptr, *d_nptr = nullptr, *d_nent = nullptr;
+    int *d_flptr = nullptr, *d_flent = nullptr, *d_nptr = nullptr, *d_nent = nullptr, *d_far_item = nullptr;
     int *d_leaf_ptr = nullptr, *d_perm = nullptr;
     int *d_new2cl = nullptr, *d_cl2new = nullptr, *d_new2orig = nullptr, *d_pos = nullptr;
     // device: plan
@@ -137,6 +138,10 @@ struct hm_ctx {
     int t_cols = 0;
     double2 *d_work = nullptr;               // operator scratch vectors
     int work_cols = 0;
+    // complex-FP32 copies for the mixed-precision inner operator
+    float2 *d_W32 = nullptr, *d_Ad32 = nullptr, *d_Dinv32 = nullptr, *d_farU32 = nullptr, *d_farV32 = nullptr;
+    float2 *d_t32 = nullptr, *d_s32 = nullptr, *d_work32 = nullptr;
+    int t32_cols = 0;
 };
 
 // Launch wrapper: counts every launch by kernel class and, when profiling is on, brackets
@@ -149,6 +154,8 @@ struct hm_ctx {
     } while (0)
 
 namespace hm {
+constexpr int ERR_TIMEOUT = 0x40000000;   // d_err bit: a bounded device-side wait expired
+
 // planner.cpp
 int validate_and_copy(hm_ctx *h, const hm_desc *d);
 void plan_order(hm_ctx *h);
@@ -160,7 +167,13 @@ void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &p
 // kernels (setup.cu / solve.cu): return cudaError_t of the launches
 cudaError_t setup_run(hm_ctx *h, int *bad_block);
 cudaError_t op_apply(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
+cudaError_t op_apply32(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
+cudaError_t make_fp32_copies(hm_ctx *h, bool factors);
+cudaError_t to_solve_order(hm_ctx *h, const double2 *src, int64_t lds, double2 *dst, int nrhs);
+cudaError_t to_orig_order(hm_ctx *h, const double2 *src, double2 *dst, int64_t ldd, int nrhs);
 cudaError_t z_apply_orig(hm_ctx *h, const double2 *x, double2 *y, int nrhs);
+template <class T>
+cudaError_t far_product(hm_ctx *h, const T *U, const T *V, T *t, T *s, const T *ucl, T *y, int nrhs);
 cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs);
 int gmres_solve(hm_ctx *h, const double2 *dV, int nrhs, int64_t ldv, double tol, int restart, int maxit,
                 double2 *dI, int64_t ldi, int *iters, double *relres);

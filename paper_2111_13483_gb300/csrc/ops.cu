@@ -1,0 +1,632 @@
+// Operator of the preconditioned system (Eq. 28) on the GPU, in complex FP64 or FP32:
+//
+//   A x~ = D^{-1} [ D x~ + L^{-1} Z_F L^{-T} x~ ],   c = D^{-1} L^{-1} b,   x = L^{-T} x~
+//
+// L^{-1} / L^{-T} are the products of the left / right scaling coefficients (Eqs. 20, 23,
+// 24) applied as block-triangular sweeps over the coefficient panels W_k (L_jk = W_kj^T).
+// Each sweep is one sync-free launch: a CTA takes the next block row from a ticket counter
+// (so every block it waits on belongs to a CTA that is already running), stages the
+// coefficient blocks of its dependencies in fixed chunks, waits on their ready flags (a
+// bounded wait that reports HM_ETIMEOUT instead of hanging), and publishes its own block
+// with a flag.  The most recently finished dependency is always alone in the last chunk,
+// so the chain's critical path carries one small block product per step.  Chunking does not
+// change the order of the arithmetic: every output subtracts its terms block by block in
+// dependency order, so results are bitwise reproducible and independent of the batch width.
+//
+// Z_F is applied by far_product (far.cu) in cluster order.
+// Vectors are column-major n x nrhs (ld n) in solve order.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "cplx.cuh"
+#include "hm_internal.h"
+
+namespace hm {
+
+namespace {
+
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One thread waits until flags[k] == epoch; false (and ERR_TIMEOUT recorded) when the
+// bound expires or another CTA already failed.
+__device__ bool wait_ready(const int *flags, int k, int epoch, int *err)
+{
+    const volatile int *f = flags + k;
+    if (*f == epoch) {
+        __threadfence();
+        return true;
+    }
+    unsigned long long t0 = gtimer();
+    while (*f != epoch) {
+        if (*(volatile int *)err) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            atomicCAS(err, 0, ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+__device__ __forceinline__ void publish(int *flags, int i, int epoch)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicExch(flags + i, epoch);
+}
+
+// Dependencies finishing last (the final TAIL entries of a list) are taken one per chunk,
+// so that the chain's critical path never carries more than one block product.
+constexpr int TAIL = 4;
+// Threads that share one output in a single-block chunk (the inner sum split in SPLIT
+// contiguous parts, added in a fixed order).
+constexpr int SPLIT = 4;
+
+// Next chunk [p, q) of a dependency list walked from p towards pend (step +1 or -1): blocks
+// are added while their staged entries (coefficient block + vector block) fit the budget;
+// each of the last TAIL dependencies forms a chunk of its own.
+__device__ __forceinline__ int next_chunk(int p, int pend, int step, const int *dep, const int *size, int nrow,
+                                          int nrhs, int budget)
+{
+    const int tail0 = pend - TAIL * step;   // first position of the tail
+    if ((step > 0 && p >= tail0) || (step < 0 && p <= tail0)) return p + step;
+    const int last = tail0;
+    int q = p, used = 0, cnt = 0;
+    while (q != last && cnt < 16) {
+        const int nk = size[dep[q]];
+        const int need = nk * nrow + nk * nrhs;
+        if (cnt > 0 && used + need > budget) break;
+        used += need;
+        ++cnt;
+        q += step;
+    }
+    return q;
+}
+
+// acc[row + r*nrow] -= sum_q w[q*ldw + row] * y[q + r*len] for one staged block, every output
+// shared by SPLIT consecutive lanes that each sum a contiguous part of q; the parts are
+// combined as (p0 + p1) + (p2 + p3).  blockDim.x must be a multiple of 32.
+template <class T>
+__device__ __forceinline__ void single_block(T *acc, const T *w, int ldw, const T *y, int len, int nrow, int nrhs)
+{
+    const int total = nrow * nrhs * SPLIT;
+    for (int base = 0; base < total; base += blockDim.x) {
+        const int e2 = base + threadIdx.x;
+        const bool act = e2 < total;
+        const int e = e2 / SPLIT, part = e2 % SPLIT;
+        T v = czero(T());
+        if (act) {
+            const int row = e % nrow, r = e / nrow;
+            const int q0 = part * len / SPLIT, q1 = (part + 1) * len / SPLIT;
+            const T *wr = w + row, *yr = y + r * len;
+            for (int q = q0; q < q1; ++q) v = cfma(wr[q * ldw], yr[q], v);
+        }
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+        if (act && part == 0) {
+            acc[e].x -= v.x;
+            acc[e].y -= v.y;
+        }
+    }
+}
+
+}  // namespace
+
+// y = L^{-1} x : y_i = x_i - sum_{k < i, i in S_k} W_ki^T y_k   (Eq. 23)
+template <class T>
+__global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, const int *boff, const int *rptr,
+                                                   const int *ridx, const int *rcol, const int64_t *coff,
+                                                   const T *W, const T *x, T *y, int n, int nrhs, int budget,
+                                                   int *flags, int epoch, int *ticket, int *err)
+{
+    extern __shared__ unsigned char smraw[];
+    T *acc = (T *)smraw;                 // ni x nrhs
+    T *buf = acc + 64 * nrhs;            // staged chunk: W blocks (transposed) then y blocks
+    __shared__ int s_i;
+    if (threadIdx.x == 0) s_i = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int i = s_i;
+    if (i >= nb) return;
+    const int ni = size[i], o = boff[i];
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+        const int c = e % ni, r = e / ni;
+        acc[e] = x[o + c + (int64_t)r * n];
+    }
+    const int p0 = rptr[i], p1 = rptr[i + 1];
+    for (int p = p0; p < p1;) {
+        const int q = next_chunk(p, p1, 1, ridx, size, ni, nrhs, budget);
+        // stage the coefficient blocks (static data) before waiting
+        int off = 0;
+        for (int b = p; b < q; ++b) {
+            const int k = ridx[b], nk = size[k];
+            const T *Wki = W + coff[k] + (int64_t)rcol[b] * nk;   // nk x ni, column-major
+            for (int e = threadIdx.x; e < nk * ni; e += blockDim.x) {
+                const int qq = e % nk, c = e / nk;
+                buf[off + qq * ni + c] = Wki[e];
+            }
+            off += nk * ni;
+        }
+        if (threadIdx.x == 0)
+            for (int b = p; b < q; ++b) wait_ready(flags, ridx[b], epoch, err);
+        __syncthreads();
+        const int yoff0 = off;
+        for (int b = p; b < q; ++b) {
+            const int k = ridx[b], nk = size[k], ok = boff[k];
+            for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
+                const int qq = e % nk, r = e / nk;
+                buf[off + e] = ldcg(y + ok + qq + (int64_t)r * n);
+            }
+            off += nk * nrhs;
+        }
+        __syncthreads();
+        if (p >= p1 - TAIL)   // a tail singleton (decided by position only: batch invariant)
+            single_block(acc, buf, ni, buf + yoff0, size[ridx[p]], ni, nrhs);
+        else
+        for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+            const int c = e % ni, r = e / ni;
+            T s = acc[e];
+            int wo = 0, yo = yoff0;
+            for (int b = p; b < q; ++b) {
+                const int nk = size[ridx[b]];
+                const T *wb = buf + wo + c;
+                const T *yb = buf + yo + r * nk;
+                for (int qq = 0; qq < nk; ++qq) s = cfms(wb[qq * ni], yb[qq], s);
+                wo += nk * ni;
+                yo += nk * nrhs;
+            }
+            acc[e] = s;
+        }
+        __syncthreads();
+        p = q;
+    }
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+        const int c = e % ni, r = e / ni;
+        y[o + c + (int64_t)r * n] = acc[e];
+    }
+    publish(flags, i, epoch);
+}
+
+// y = L^{-T} x : y_k = x_k - sum_{j in S_k} W_kj y_j   (Eq. 24); j walked downwards
+template <class T>
+__global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, const int *boff, const int *sptr,
+                                                   const int *sidx, const int *srow, const int64_t *coff,
+                                                   const T *W, const T *x, T *y, int n, int nrhs, int budget,
+                                                   int *flags, int epoch, int *ticket, int *err)
+{
+    extern __shared__ unsigned char smraw[];
+    T *acc = (T *)smraw;                 // nk x nrhs
+    T *buf = acc + 64 * nrhs;
+    __shared__ int s_k;
+    if (threadIdx.x == 0) s_k = nb - 1 - atomicAdd(ticket, 1);
+    __syncthreads();
+    const int k = s_k;
+    if (k < 0) return;
+    const int nk = size[k], o = boff[k];
+    for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
+        const int rw = e % nk, r = e / nk;
+        acc[e] = x[o + rw + (int64_t)r * n];
+    }
+    const int pend = sptr[k] - 1;
+    for (int p = sptr[k + 1] - 1; p > pend;) {
+        const int q = next_chunk(p, pend, -1, sidx, size, nk, nrhs, budget);
+        int off = 0;
+        for (int b = p; b > q; --b) {
+            const int nj = size[sidx[b]];
+            const T *Wkj = W + coff[k] + (int64_t)srow[b] * nk;     // nk x nj, column-major
+            for (int e = threadIdx.x; e < nk * nj; e += blockDim.x) buf[off + e] = Wkj[e];
+            off += nk * nj;
+        }
+        if (threadIdx.x == 0)
+            for (int b = p; b > q; --b) wait_ready(flags, sidx[b], epoch, err);
+        __syncthreads();
+        const int yoff0 = off;
+        for (int b = p; b > q; --b) {
+            const int j = sidx[b], nj = size[j], oj = boff[j];
+            for (int e = threadIdx.x; e < nj * nrhs; e += blockDim.x) {
+                const int c = e % nj, r = e / nj;
+                buf[off + e] = ldcg(y + oj + c + (int64_t)r * n);
+            }
+            off += nj * nrhs;
+        }
+        __syncthreads();
+        if (p <= pend + TAIL)   // a tail singleton (decided by position only: batch invariant)
+            single_block(acc, buf, nk, buf + yoff0, size[sidx[p]], nk, nrhs);
+        else
+        for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
+            const int rw = e % nk, r = e / nk;
+            T s = acc[e];
+            int wo = 0, yo = yoff0;
+            for (int b = p; b > q; --b) {
+                const int nj = size[sidx[b]];
+                const T *wb = buf + wo + rw;
+                const T *yb = buf + yo + r * nj;
+                for (int c = 0; c < nj; ++c) s = cfms(wb[c * nk], yb[c], s);
+                wo += nk * nj;
+                yo += nj * nrhs;
+            }
+            acc[e] = s;
+        }
+        __syncthreads();
+        p = q;
+    }
+    for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
+        const int rw = e % nk, r = e / nk;
+        y[o + rw + (int64_t)r * n] = acc[e];
+    }
+    publish(flags, k, epoch);
+}
+
+// dst[i + r*n] = src[idx[i] + r*n]
+template <class T>
+__global__ void k_gather(int n, int nrhs, const int *idx, const T *src, T *dst)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * nrhs) return;
+    int i = (int)(e % n), r = (int)(e / n);
+    dst[e] = src[idx[i] + (int64_t)r * n];
+}
+
+// dst[idx[i] + r*ldd] = src[i + r*n]
+__global__ void k_scatter_cols(int n, int nrhs, const int *idx, const double2 *src, double2 *dst, int64_t ldd)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * nrhs) return;
+    int i = (int)(e % n), r = (int)(e / n);
+    dst[idx[i] + r * ldd] = src[e];
+}
+
+// dst[i + r*n] = src[idx[i] + r*lds]
+__global__ void k_gather_cols(int n, int nrhs, const int *idx, const double2 *src, int64_t lds, double2 *dst)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * nrhs) return;
+    int i = (int)(e % n), r = (int)(e / n);
+    dst[e] = src[idx[i] + r * lds];
+}
+
+__global__ void k_narrow(int64_t len, const double2 *src, float2 *dst)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < len) dst[e] = make_float2((float)src[e].x, (float)src[e].y);
+}
+
+__global__ void k_widen(int64_t len, const float2 *src, double2 *dst)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < len) dst[e] = make_double2((double)src[e].x, (double)src[e].y);
+}
+
+// Block-diagonal operations (Eq. 28), one CTA per block:
+//   mode 0: y = D^{-1} (D x + w);  mode 1: y = D^{-1} x;  mode 2: y = D x
+template <class T>
+__global__ void __launch_bounds__(256) k_diag(int mode, int nb, const int *size, const int *boff,
+                                              const int64_t *doff, const T *D, const T *Dinv, const T *x,
+                                              const T *w, T *y, int n, int nrhs)
+{
+    extern __shared__ unsigned char smraw[];
+    T *xs = (T *)smraw, *ts = xs + 64 * nrhs;
+    const int k = blockIdx.x;
+    if (k >= nb) return;
+    const int nk = size[k], o = boff[k];
+    for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
+        const int rw = e % nk, r = e / nk;
+        xs[e] = x[o + rw + (int64_t)r * n];
+    }
+    __syncthreads();
+    const T *Dk = D + doff[k], *Ik = Dinv + doff[k];
+    if (mode == 0) {
+        for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
+            const int rw = e % nk, r = e / nk;
+            T acc = w[o + rw + (int64_t)r * n];
+            for (int c = 0; c < nk; ++c) acc = cfma(Dk[rw + c * nk], xs[c + r * nk], acc);
+            ts[e] = acc;
+        }
+        __syncthreads();
+        xs = ts;
+    }
+    const T *Mk = (mode == 2) ? Dk : Ik;
+    for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
+        const int rw = e % nk, r = e / nk;
+        T acc = czero(T());
+        for (int c = 0; c < nk; ++c) acc = cfma(Mk[rw + c * nk], xs[c + r * nk], acc);
+        y[o + rw + (int64_t)r * n] = acc;
+    }
+}
+
+// Near-field product for the refinement residual: y += Z_N u, u in cluster order, y in solve
+// order.  One CTA per leaf, summing near blocks (t, s) and mirrored (s, t) blocks (FP64).
+__global__ void __launch_bounds__(128) k_near_mv(int nl, const int *leaf_ptr, const int *nptr, const int *nent,
+                                                 const int *near_t, const int *near_s, const int64_t *near_off,
+                                                 const double2 *near, const double2 *u, const int *cl2new, int n,
+                                                 int nrhs, double2 *y)
+{
+    const int l = blockIdx.x;
+    if (l >= nl) return;
+    const int a = leaf_ptr[l], ni = leaf_ptr[l + 1] - a;
+    const int on = cl2new[a];
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+        const int i = e % ni, r = e / ni;
+        double2 acc = y[on + i + (int64_t)r * n];
+        for (int p = nptr[l]; p < nptr[l + 1]; ++p) {
+            const int b = nent[p] >> 1, side = nent[p] & 1;
+            const int t = near_t[b], s = near_s[b];
+            const int mt = leaf_ptr[t + 1] - leaf_ptr[t];
+            const double2 *B = near + near_off[b];
+            if (side == 0) {   // row l = t: sum_c B[i, c] u_s[c]
+                const int ms = leaf_ptr[s + 1] - leaf_ptr[s];
+                const double2 *us = u + leaf_ptr[s] + (int64_t)r * n;
+                for (int c = 0; c < ms; ++c) acc = cfma(B[i + (int64_t)c * mt], us[c], acc);
+            } else {           // row l = s (t != s): sum_q B[q, i] u_t[q]
+                const double2 *ut = u + leaf_ptr[t] + (int64_t)r * n;
+                for (int q = 0; q < mt; ++q) acc = cfma(B[q + (int64_t)i * mt], ut[q], acc);
+            }
+        }
+        y[on + i + (int64_t)r * n] = acc;
+    }
+}
+
+// ---- host side -------------------------------------------------------------------------
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <class T> struct OpData {
+    const T *W, *Ad, *Dinv, *U, *V;
+    T *t, *s, *work;
+};
+
+static OpData<double2> data64(hm_ctx *h)
+{
+    return {h->d_W, h->d_Ad, h->d_Dinv, h->d_farU, h->d_farV, h->d_t, h->d_s, h->d_work};
+}
+static OpData<float2> data32(hm_ctx *h)
+{
+    return {h->d_W32, h->d_Ad32, h->d_Dinv32, h->d_farU32, h->d_farV32, h->d_t32, h->d_s32, h->d_work32};
+}
+
+// Widest column batch one sweep launch takes (wider requests are split into slices); the
+// shared memory of a sweep CTA (accumulator + one staged 64-row block and its vector block)
+// then allows two CTAs per SM, so the resident CTAs cover the ~band of pending block rows.
+template <class T> static int max_cols() { return sizeof(T) == 16 ? 16 : 64; }
+template <class T> static int sweep_budget(int nrhs) { return 4096 + 64 * nrhs; }
+
+template <class T>
+static size_t sweep_smem(int nrhs)
+{
+    return sizeof(T) * (size_t)(64 * nrhs + sweep_budget<T>(nrhs));
+}
+
+template <class T>
+static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs)
+{
+    Plan &P = h->plan;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->d_ticket, 0, sizeof(int), h->stream))) return e;
+    const int ep = ++h->epoch;
+    const size_t smem = sweep_smem<T>(nrhs);
+    const int budget = sweep_budget<T>(nrhs);
+    if (forward)
+        HM_LAUNCH(h, K_SWEEP_FWD,
+                  k_sweep_fwd<T><<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx,
+                                                                 h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs, budget,
+                                                                 h->d_flags, ep, h->d_ticket, h->d_err));
+    else
+        HM_LAUNCH(h, K_SWEEP_BWD,
+                  k_sweep_bwd<T><<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx,
+                                                                 h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs, budget,
+                                                                 h->d_flags, ep, h->d_ticket, h->d_err));
+    return cudaGetLastError();
+}
+
+// y (solve order) = Z_F x (solve order); ucl receives the cluster-order copy of x
+template <class T>
+static cudaError_t far_apply(hm_ctx *h, const OpData<T> &d, const T *x, T *y, int nrhs, T *ucl)
+{
+    Plan &P = h->plan;
+    FarPlan &F = h->fplan;
+    const int n = P.n;
+    HM_LAUNCH(h, K_PERMUTE, k_gather<T><<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_cl2new, x,
+                                                                                            ucl));
+    (void)F;
+    cudaError_t e = far_product<T>(h, d.U, d.V, d.t, d.s, ucl, y, nrhs);
+    if (e) return e;
+    return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t diag(hm_ctx *h, const OpData<T> &d, int mode, const T *x, const T *w, T *y, int nrhs)
+{
+    Plan &P = h->plan;
+    HM_LAUNCH(h, K_DIAG,
+              k_diag<T><<<P.nb, 256, sizeof(T) * 128 * nrhs, h->stream>>>(mode, P.nb, h->d_size, h->d_boff,
+                                                                           h->d_doff, d.Ad, d.Dinv, x, w, y, P.n,
+                                                                           nrhs));
+    return cudaGetLastError();
+}
+
+template <class T>
+static void set_attrs()
+{
+    const int smax = (int)sweep_smem<T>(max_cols<T>());
+    cudaFuncSetAttribute(k_sweep_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_sweep_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    cudaFuncSetAttribute(k_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * 128 * 64));
+}
+
+cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs)
+{
+    cudaError_t e;
+    const int n = h->plan.n;
+    if (!h->d_flags) {
+        if ((e = h->arena.alloc((void **)&h->d_flags, sizeof(int) * h->plan.nb))) return e;
+        if ((e = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->plan.nb, h->stream))) return e;
+        h->epoch = 0;
+    }
+    const size_t tl = std::max<int64_t>(1, h->fplan.tlen);
+    if (h->t_cols < nrhs) {
+        if (h->d_t) h->arena.release(h->d_t, 0), h->arena.release(h->d_s, 0);
+        h->d_t = h->d_s = nullptr;
+        h->t_cols = 0;
+        if ((e = h->arena.alloc((void **)&h->d_t, sizeof(double2) * tl * nrhs))) return e;
+        if ((e = h->arena.alloc((void **)&h->d_s, sizeof(double2) * tl * nrhs))) return e;
+        h->t_cols = nrhs;
+    }
+    if (h->work_cols < 3 * nrhs) {
+        if (h->d_work) h->arena.release(h->d_work, 0);
+        h->d_work = nullptr;
+        h->work_cols = 0;
+        if ((e = h->arena.alloc((void **)&h->d_work, sizeof(double2) * (size_t)n * 3 * nrhs))) return e;
+        h->work_cols = 3 * nrhs;
+    }
+    if (h->opts.precision == 1 && h->t32_cols < nrhs) {
+        if (h->d_t32) h->arena.release(h->d_t32, 0), h->arena.release(h->d_s32, 0), h->arena.release(h->d_work32, 0);
+        h->d_t32 = h->d_s32 = nullptr;
+        h->d_work32 = nullptr;
+        h->t32_cols = 0;
+        if ((e = h->arena.alloc((void **)&h->d_t32, sizeof(float2) * tl * nrhs))) return e;
+        if ((e = h->arena.alloc((void **)&h->d_s32, sizeof(float2) * tl * nrhs))) return e;
+        if ((e = h->arena.alloc((void **)&h->d_work32, sizeof(float2) * (size_t)n * 5 * nrhs))) return e;
+        h->t32_cols = nrhs;
+    }
+    static bool attr = false;
+    if (!attr) {
+        set_attrs<double2>();
+        set_attrs<float2>();
+        attr = true;
+    }
+    return cudaSuccess;
+}
+
+// Complex FP32 copies of the far factors (at create) and of the factors (after setup).
+cudaError_t make_fp32_copies(hm_ctx *h, bool factors)
+{
+    cudaError_t e;
+    auto narrow = [&](const double2 *src, float2 **dst, size_t len) -> cudaError_t {
+        cudaError_t r;
+        if (!*dst && (r = h->arena.alloc((void **)dst, sizeof(float2) * std::max<size_t>(len, 1)))) return r;
+        if (len)
+            HM_LAUNCH(h, K_VEC, k_narrow<<<nblk((int64_t)len, 256), 256, 0, h->stream>>>((int64_t)len, src, *dst));
+        return cudaGetLastError();
+    };
+    if (!factors) {
+        if ((e = narrow(h->d_farU, &h->d_farU32, (size_t)h->farU_len))) return e;
+        return narrow(h->d_farV, &h->d_farV32, (size_t)h->farV_len);
+    }
+    const Plan &P = h->plan;
+    if ((e = narrow(h->d_W, &h->d_W32, (size_t)P.coef_entries))) return e;
+    if ((e = narrow(h->d_Ad, &h->d_Ad32, (size_t)P.diag_entries))) return e;
+    return narrow(h->d_Dinv, &h->d_Dinv32, (size_t)P.diag_entries);
+}
+
+template <class T>
+static cudaError_t op_chain(hm_ctx *h, const OpData<T> &d, int op, const T *x, T *y, int nrhs)
+{
+    const int n = h->plan.n;
+    T *w0 = d.work, *w1 = d.work + (size_t)n * nrhs, *w2 = d.work + (size_t)2 * n * nrhs;
+    cudaError_t e;
+    switch (op) {
+    case 0:   // A x = D^{-1} [D x + L^{-1} Z_F L^{-T} x]
+        if ((e = sweep<T>(h, d, false, x, w0, nrhs))) return e;
+        if ((e = far_apply<T>(h, d, w0, w1, nrhs, w2))) return e;
+        if ((e = sweep<T>(h, d, true, w1, w0, nrhs))) return e;
+        return diag<T>(h, d, 0, x, w0, y, nrhs);
+    case 1: return sweep<T>(h, d, true, x, y, nrhs);
+    case 2: return sweep<T>(h, d, false, x, y, nrhs);
+    case 3: return far_apply<T>(h, d, x, y, nrhs, w2);
+    case 4: return diag<T>(h, d, 1, x, (const T *)nullptr, y, nrhs);
+    case 6: return diag<T>(h, d, 2, x, (const T *)nullptr, y, nrhs);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// op codes as in hm_apply (0-4, plus 6 = D x); FP64 data; columns in slices of max_cols
+cudaError_t op_apply(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs)
+{
+    cudaError_t e;
+    const int w = max_cols<double2>();
+    if (nrhs > w) {
+        for (int c0 = 0; c0 < nrhs; c0 += w)
+            if ((e = op_apply(h, op, x + (size_t)c0 * h->plan.n, y + (size_t)c0 * h->plan.n, std::min(w, nrhs - c0))))
+                return e;
+        return cudaSuccess;
+    }
+    if ((e = ensure_solve_workspace(h, nrhs))) return e;
+    return op_chain<double2>(h, data64(h), op, x, y, nrhs);
+}
+
+// The same operators with complex-FP32 data and arithmetic; x, y stay complex FP64.
+cudaError_t op_apply32(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs)
+{
+    cudaError_t e;
+    const int w = max_cols<float2>();
+    if (nrhs > w) {
+        for (int c0 = 0; c0 < nrhs; c0 += w)
+            if ((e = op_apply32(h, op, x + (size_t)c0 * h->plan.n, y + (size_t)c0 * h->plan.n,
+                                std::min(w, nrhs - c0))))
+                return e;
+        return cudaSuccess;
+    }
+    if ((e = ensure_solve_workspace(h, nrhs))) return e;
+    const int64_t len = (int64_t)h->plan.n * nrhs;
+    OpData<float2> d = data32(h);
+    float2 *x32 = h->d_work32 + 3 * len, *y32 = h->d_work32 + 4 * len;
+    HM_LAUNCH(h, K_VEC, k_narrow<<<nblk(len, 256), 256, 0, h->stream>>>(len, x, x32));
+    if ((e = op_chain<float2>(h, d, op, x32, y32, nrhs))) return e;
+    HM_LAUNCH(h, K_VEC, k_widen<<<nblk(len, 256), 256, 0, h->stream>>>(len, y32, y));
+    return cudaGetLastError();
+}
+
+// y = Z x with x, y in the ORIGINAL RWG order (near blocks + far factors, FP64).
+cudaError_t z_apply_orig(hm_ctx *h, const double2 *x, double2 *y, int nrhs)
+{
+    cudaError_t e;
+    const int w = max_cols<double2>();
+    if (nrhs > w) {
+        for (int c0 = 0; c0 < nrhs; c0 += w)
+            if ((e = z_apply_orig(h, x + (size_t)c0 * h->plan.n, y + (size_t)c0 * h->plan.n, std::min(w, nrhs - c0))))
+                return e;
+        return cudaSuccess;
+    }
+    if ((e = ensure_solve_workspace(h, nrhs))) return e;
+    const int n = h->plan.n;
+    double2 *w0 = h->d_work, *w1 = h->d_work + (size_t)n * nrhs, *w2 = h->d_work + (size_t)2 * n * nrhs;
+    HM_LAUNCH(h, K_PERMUTE,
+              k_gather_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, x, n, w0));
+    if ((e = far_apply<double2>(h, data64(h), w0, w1, nrhs, w2))) return e;   // leaves the cluster-order copy in w2
+    HM_LAUNCH(h, K_NEAR,
+              k_near_mv<<<h->nl, 128, 0, h->stream>>>(h->nl, h->d_leaf_ptr, h->d_nptr, h->d_nent, h->d_near_t,
+                                                      h->d_near_s, h->d_near_off, h->d_near, w2, h->d_cl2new, n,
+                                                      nrhs, w1));
+    HM_LAUNCH(h, K_PERMUTE,
+              k_scatter_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, w1, y, n));
+    return cudaGetLastError();
+}
+
+// original order (ld ldv) -> solve order (ld n)
+cudaError_t to_solve_order(hm_ctx *h, const double2 *src, int64_t lds, double2 *dst, int nrhs)
+{
+    const int n = h->plan.n;
+    HM_LAUNCH(h, K_PERMUTE,
+              k_gather_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, src, lds, dst));
+    return cudaGetLastError();
+}
+
+// solve order (ld n) -> original order (ld ldd)
+cudaError_t to_orig_order(hm_ctx *h, const double2 *src, double2 *dst, int64_t ldd, int nrhs)
+{
+    const int n = h->plan.n;
+    HM_LAUNCH(h, K_PERMUTE,
+              k_scatter_cols<<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_new2orig, src, dst, ldd));
+    return cudaGetLastError();
+}
+
+}  // namespace hm

@@ -332,6 +332,9 @@ void plan_far(hm_ctx *h)
         F.toff[b + 1] = F.toff[b] + (lr ? h->far_rank[b] : 0);
     }
     F.tlen = F.toff[nf];
+    F.item_blk.resize(F.tlen);
+    for (int b = 0; b < nf; ++b)
+        for (int64_t e = F.toff[b]; e < F.toff[b + 1]; ++e) F.item_blk[e] = b;
     F.lptr.assign(nl + 1, 0);
     for (int l = 0; l < nl; ++l) F.lptr[l + 1] = F.lptr[l] + (int)lists[l].size();
     F.lent.clear();

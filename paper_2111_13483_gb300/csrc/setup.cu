@@ -11,23 +11,14 @@
 //   Dinv + doff[k]      D_k^{-1} for the Eq. 28 preconditioner.
 // Step k: pivot inverse (one CTA), panel (M_k/64 CTAs), Schur updates
 // A_ij -= A_ik W_kj for i >= j in S_k (Eq. 19; one CTA per block pair, diagonal blocks
-// in full).  Stream order gives the step dependencies.
+// in full; FP32 products in the mixed-precision setup).  Stream order gives the step
+// dependencies.
 #include <cstdio>
 
+#include "cplx.cuh"
 #include "hm_internal.h"
 
 namespace hm {
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c)
-{
-    // c + a*b
-    c.x = fma(a.x, b.x, c.x);
-    c.x = fma(-a.y, b.y, c.x);
-    c.y = fma(a.x, b.y, c.y);
-    c.y = fma(a.y, b.x, c.y);
-    return c;
-}
 
 // row offset of block i inside stacked column j (binary search in S_j); -1 if absent
 __device__ __forceinline__ int find_row(const int *sptr, const int *sidx, const int *srow, int j, int i)
@@ -95,8 +86,7 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, c
     double2 *colc = rowc + n;                  // n: pivot column before the update
     __shared__ int piv[64];
     __shared__ int s_p;
-    __shared__ double red_v[256];
-    __shared__ int red_i[256];
+    __shared__ double2 s_d;
     const double2 *D = Ad + doff[k];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int r = e % n, c = e / n;
@@ -104,33 +94,32 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, c
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
-        // pivot search over rows r >= c
-        double best = -1.0;
-        int bi = n;
-        for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
-            double2 v = a[r * ld + c];
-            double m = hypot(v.x, v.y);
-            if (m > best || (m == best && r < bi)) { best = m; bi = r; }
-        }
-        red_v[threadIdx.x] = best;
-        red_i[threadIdx.x] = bi;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) {
-                double v2 = red_v[threadIdx.x + w];
-                int i2 = red_i[threadIdx.x + w];
-                if (v2 > red_v[threadIdx.x] || (v2 == red_v[threadIdx.x] && i2 < red_i[threadIdx.x])) {
-                    red_v[threadIdx.x] = v2;
-                    red_i[threadIdx.x] = i2;
-                }
+        // Pivot search over rows r >= c by one warp: largest |a_rc|^2, lowest row on ties.
+        // The squares are compared as the integer bit patterns of non-negative doubles
+        // (same order as the values), which keeps the compares off the slow FP64 pipe.
+        if (threadIdx.x < 32) {
+            unsigned long long best = 0;
+            int bi = n;
+            for (int r = c + threadIdx.x; r < n; r += 32) {
+                double2 v = a[r * ld + c];
+                unsigned long long key = (unsigned long long)__double_as_longlong(fma(v.x, v.x, v.y * v.y));
+                if (key > best || (key == best && r < bi) || bi == n) { best = key; bi = r; }
             }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            s_p = red_i[0];
-            piv[c] = s_p;
-            double pv = red_v[0];
-            if (!(pv > 1e-300) || !isfinite(pv)) atomicCAS(err, 0, k + 1);
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (oi < n && (ob > best || (ob == best && oi < bi) || bi == n)) { best = ob; bi = oi; }
+            }
+            if (threadIdx.x == 0) {
+                s_p = bi;
+                piv[c] = bi;
+                // singular: |pivot|^2 <= 1e-300 or not finite (exponent bits all ones)
+                const double pv = __longlong_as_double((long long)best);
+                const bool bad = !(pv > 1e-300) || best >= 0x7ff0000000000000ull;
+                double2 pvv = a[bi * ld + c];
+                s_d = make_double2(pvv.x / pv, -pvv.y / pv);   // 1 / pivot
+                if (bad) atomicCAS(err, 0, k + 1);
+            }
         }
         __syncthreads();
         const int p = s_p;
@@ -141,9 +130,7 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, c
                 a[p * ld + j] = t;
             }
         __syncthreads();
-        double2 pvv = a[c * ld + c];
-        double den = pvv.x * pvv.x + pvv.y * pvv.y;
-        double2 d = make_double2(pvv.x / den, -pvv.y / den);
+        const double2 d = s_d;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             rowc[j] = (j == c) ? d : cmul(a[c * ld + j], d);
             colc[j] = a[j * ld + c];
@@ -217,13 +204,73 @@ __global__ void __launch_bounds__(256) k_panel(int k, const int *size, const int
     }
 }
 
-// Schur updates of step k: one CTA per pair (a >= b) of S_k: A_ij -= A_ik W_kj.
+// Schur updates of step k (Eq. 19): one CTA per pair (a >= b) of S_k, A_ij -= A_ik W_kj.
+// TC is the arithmetic type: double2 (FP64 setup) or float2 (mixed-precision setup: FP32
+// products of the FP64-stored blocks, subtracted in FP64).  A 16 x 16 thread grid covers
+// the output block with up to 4 x 4 outputs per thread; every loop runs over the block's
+// actual rows and columns, so no issue slot is spent on padding.
+// C (ni x nj) -= A (ni x nk) W (nk x nj) on a 16U x 16U tile: thread (tx, ty) owns rows
+// tx + 16u and columns ty + 16v (u, v < U).  The shared tiles are zero-padded to the tile
+// size, so every thread runs the same unpredicated FMA sequence; padded outputs are dropped.
+template <class TC, int QC, int U>
+__device__ __forceinline__ void update_tile(TC (*As)[65], TC (*Ws)[65], const double2 *Aik, int Mk, const double2 *Wkj,
+                                            int nk, int ni, int nj, double2 *C, int ldc)
+{
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    constexpr int TS = 16 * U;
+    TC acc[U][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < U; ++v) acc[u][v] = czero(TC());
+    for (int q0 = 0; q0 < nk; q0 += QC) {
+        const int nq = min(QC, nk - q0);
+        for (int e = threadIdx.x; e < TS * nq; e += blockDim.x) {
+            const int r = e % TS, q = e / TS;
+            As[q][r] = r < ni ? cconv<TC>(Aik[r + (int64_t)(q0 + q) * Mk]) : czero(TC());
+        }
+        for (int e = threadIdx.x; e < nq * TS; e += blockDim.x) {
+            const int q = e % nq, c = e / nq;
+            Ws[q][c] = c < nj ? cconv<TC>(Wkj[(q0 + q) + (int64_t)c * nk]) : czero(TC());
+        }
+        __syncthreads();
+        for (int q = 0; q < nq; ++q) {
+            TC av[U], wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) av[u] = As[q][tx + 16 * u];
+#pragma unroll
+            for (int v = 0; v < U; ++v) wv[v] = Ws[q][ty + 16 * v];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int v = 0; v < U; ++v) acc[u][v] = cfma(av[u], wv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < U; ++v) {
+            const int r = tx + 16 * u, c = ty + 16 * v;
+            if (r < ni && c < nj) {
+                double2 *p = C + r + (int64_t)c * ldc;
+                const double2 d = cwiden(acc[u][v]);
+                double2 o = *p;
+                o.x -= d.x;
+                o.y -= d.y;
+                *p = o;
+            }
+        }
+}
+
+template <class TC>
 __global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, const int *sptr, const int *sidx,
                                                 const int *srow, const int *M, const int64_t *coff,
                                                 const int64_t *doff, const double2 *W, double2 *A, double2 *Ad)
 {
-    __shared__ double2 As[16][65];   // As[q][r] = A_ik[r, q0+q]
-    __shared__ double2 Ws[16][65];   // Ws[q][c] = W_kj[q0+q, c]
+    constexpr int QC = sizeof(TC) == 16 ? 16 : 32;
+    __shared__ TC As[QC][65];   // As[q][r] = A_ik[r, q0+q]
+    __shared__ TC Ws[QC][65];   // Ws[q][c] = W_kj[q0+q, c]
     // triangular index -> (a, b), a >= b
     long t = blockIdx.x;
     int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
@@ -235,7 +282,7 @@ __global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, 
     const int i = sidx[e0 + a], j = sidx[e0 + b];
     const int nk = size[k], ni = size[i], nj = size[j];
     const int Mk = M[k];
-    const double2 *Aik = A + coff[k] + srow[e0 + a];          // ld Mk
+    const double2 *Aik = A + coff[k] + srow[e0 + a];                 // ld Mk
     const double2 *Wkj = W + coff[k] + (int64_t)srow[e0 + b] * nk;   // ld nk
     double2 *C;
     int ldc;
@@ -248,49 +295,10 @@ __global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, 
         C = A + coff[j] + r;
         ldc = M[j];
     }
-    const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;   // rows tr, tr+32; cols tc + 8y
-    double2 acc[2][8];
-#pragma unroll
-    for (int x = 0; x < 2; ++x)
-#pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = make_double2(0, 0);
-    for (int q0 = 0; q0 < nk; q0 += 16) {
-        const int nq = min(16, nk - q0);
-        for (int e = threadIdx.x; e < ni * nq; e += blockDim.x) {
-            int r = e % ni, q = e / ni;
-            As[q][r] = Aik[r + (int64_t)(q0 + q) * Mk];
-        }
-        for (int e = threadIdx.x; e < nq * nj; e += blockDim.x) {
-            int q = e % nq, c = e / nq;
-            Ws[q][c] = Wkj[(q0 + q) + (int64_t)c * nk];
-        }
-        __syncthreads();
-        for (int q = 0; q < nq; ++q) {
-            double2 a0 = As[q][tr], a1 = As[q][tr + 32];
-#pragma unroll
-            for (int y = 0; y < 8; ++y) {
-                double2 w = Ws[q][tc + 8 * y];
-                acc[0][y] = cfma(a0, w, acc[0][y]);
-                acc[1][y] = cfma(a1, w, acc[1][y]);
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int x = 0; x < 2; ++x) {
-        int r = tr + 32 * x;
-        if (r >= ni) continue;
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-            int c = tc + 8 * y;
-            if (c >= nj) continue;
-            double2 *p = C + r + (int64_t)c * ldc;
-            double2 v = *p;
-            v.x -= acc[x][y].x;
-            v.y -= acc[x][y].y;
-            *p = v;
-        }
-    }
+    if (ni <= 32 && nj <= 32)
+        update_tile<TC, QC, 2>(As, Ws, Aik, Mk, Wkj, nk, ni, nj, C, ldc);
+    else
+        update_tile<TC, QC, 4>(As, Ws, Aik, Mk, Wkj, nk, ni, nj, C, ldc);
 }
 
 cudaError_t setup_run(hm_ctx *h, int *bad_block)
@@ -323,8 +331,16 @@ cudaError_t setup_run(hm_ctx *h, int *bad_block)
             HM_LAUNCH(h, K_PANEL, k_panel<<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff, h->d_Dinv, h->d_A,
                                                    h->d_W));
             long nt = (long)ns * (ns + 1) / 2;
-            HM_LAUNCH(h, K_UPDATE, k_update<<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx, h->d_srow, h->d_M,
-                                                   h->d_coff, h->d_doff, h->d_W, h->d_A, h->d_Ad));
+            if (h->opts.precision == 1)
+                HM_LAUNCH(h, K_UPDATE,
+                          k_update<float2><<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx,
+                                                                         h->d_srow, h->d_M, h->d_coff, h->d_doff,
+                                                                         h->d_W, h->d_A, h->d_Ad));
+            else
+                HM_LAUNCH(h, K_UPDATE,
+                          k_update<double2><<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx,
+                                                                          h->d_srow, h->d_M, h->d_coff, h->d_doff,
+                                                                          h->d_W, h->d_A, h->d_Ad));
         }
         if ((e = cudaGetLastError())) return e;
     }

@@ -145,3 +145,53 @@ def test_true_residual_small(cfg1):
     b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
     x, it, rr, code = hm.solve(h, b, tol=1e-8)
     assert np.linalg.norm(b - S.Z_orig(x)) / np.linalg.norm(b) < 1e-6
+
+
+# ---- mixed precision: complex-FP32 operator inside FP64 refinement ----------------------
+@pytest.fixture(scope="module")
+def cfg1_mixed(sphere1920):
+    h = hm.hmat_create(sphere1920, ordering=1, fill_tol=0.0, precision=1)
+    hm.precond_setup(h)
+    return h
+
+
+@pytest.fixture(scope="module")
+def cfg1_tight(cfg1):
+    """The oracle's solve of the same discrete system at tolerance 1e-10 (per column)."""
+    P, order, F, S, h = cfg1
+    B = np.stack([P.plane_wave([-np.cos(p), -np.sin(p), 0.0], [0.0, 0.0, -1.0])
+                  for p in (0.0, 1.3, 2.9)], axis=1)
+    X = np.stack([krylov.solve(S, B[:, c], tol=1e-10, restart=30)[0] for c in range(B.shape[1])], axis=1)
+    return B, X
+
+
+def test_mixed_factors_close_to_fp64(cfg1, cfg1_mixed):
+    """FP32 Schur products, FP64 pivots: the factors stay within FP32 rounding of the oracle."""
+    P, order, F, S, h = cfg1
+    for k in range(0, F.nb, 5):
+        nk = int(F.size[k])
+        D = hm.hm_get_block(cfg1_mixed, 0, k, (nk, nk))
+        assert rel(D, F.D[k]) < 1e-4, k
+
+
+def test_mixed_solution_error_against_tight_oracle(cfg1, cfg1_mixed, cfg1_tight):
+    """The FP64 refinement loop stops on the true residual ||V - Z I||/||V||; at 3e-5 the
+    solution is within 1e-4 of the oracle's tight solve, and the residual is verified with
+    the oracle's own H-matrix product."""
+    P, order, F, S, h = cfg1
+    B, X = cfg1_tight
+    I, its, rr, code = hm.solve(cfg1_mixed, B, tol=3e-5, restart=30)
+    assert code == 0
+    for c in range(B.shape[1]):
+        assert rr[c] <= 3e-5
+        assert np.linalg.norm(B[:, c] - S.Z_orig(I[:, c])) / np.linalg.norm(B[:, c]) <= 3.1e-5
+        assert rel(I[:, c], X[:, c]) <= 1e-4
+
+
+def test_mixed_multi_rhs_equals_single(cfg1_mixed, cfg1_tight):
+    B, X = cfg1_tight
+    I, its, rr, code = hm.solve(cfg1_mixed, B, tol=1e-5, restart=30)
+    assert code == 0
+    for c in range(B.shape[1]):
+        x1, it1, rr1, c1 = hm.solve(cfg1_mixed, B[:, c], tol=1e-5, restart=30)
+        assert it1[0] == its[c] and np.array_equal(x1, I[:, c]), c
