@@ -169,12 +169,18 @@ int hm_get_fill(hm_handle h, int32_t *ptr, int32_t *idx);
  * Copies factor blocks to host memory after precond_setup, in solve order:
  *   what 0: D_k        (n_k x n_k)  the scaled near-field block of Eq. 21;
  *   what 1: D_k^{-1}   (n_k x n_k);
- *   what 2: W_k        (n_k x sum_{j in S_k} n_j) the coefficient row of block k,
- *                      uncompressed, blocks in S_k order;
- *   what 3: same as 2 after Sec. 3.4 compression (low-rank blocks expanded).
+ *   what 2: W_k        (n_k x sum_{j in S_k} n_j) the coefficient row of block k as the
+ *                      sweeps apply it, blocks in S_k order: with fill_tol > 0 the fill-in
+ *                      blocks are their Sec. 3.4 truncations (low-rank blocks expanded);
+ *   what 3: same as 2.
  * out must hold the stated number of entries.
  */
 int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out);
+
+/* Sec. 3.4 ranks of the last precond_setup, one per entry of the S_k lists (hm_get_fill
+ * order): r >= 0 = fill-in block kept at rank r, -1 = dense (near-pattern block, no
+ * compression requested, or a truncation that would not save storage). */
+int hm_get_fill_ranks(hm_handle h, int32_t *rank);
 
 /*
  * Applies one operator to nrhs device vectors (solve order, column-major, ld = n):
@@ -195,7 +201,8 @@ int hm_get_index_map(hm_handle h, int32_t *new2orig);
  * Kernel accounting.  Every launch is counted by kernel class:
  *   0 near scatter, 1 pivot inverse, 2 coefficient panel, 3 Schur update, 4 forward sweep,
  *   5 backward sweep, 6 far phase 1, 7 far phase 2, 8 block diagonal, 9 permutations,
- *   10 near product, 11 dot products, 12 vector updates, 13 small GMRES kernels.
+ *   10 near product, 11 dot products, 12 vector updates, 13 small GMRES kernels,
+ *   14 fill-in compression.
  * hm_profile(mode): 1 = also time each launch with CUDA events on the handle's stream,
  * 0 = stop timing, 2 = zero all counters.  hm_get_profile returns, for one class, the
  * launches counted, the launches timed and their summed device time in ms.

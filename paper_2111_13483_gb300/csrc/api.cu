@@ -204,7 +204,8 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
         (e = upload(h, &h->d_sidx, P.sidx)) || (e = upload(h, &h->d_srow, P.srow)) ||
         (e = upload(h, &h->d_M, P.M)) || (e = upload(h, &h->d_coff, P.coff)) || (e = upload(h, &h->d_doff, P.doff)) ||
         (e = upload(h, &h->d_rptr, P.rptr)) || (e = upload(h, &h->d_ridx, P.ridx)) ||
-        (e = upload(h, &h->d_rcol, P.rcol))) {
+        (e = upload(h, &h->d_rcol, P.rcol)) || (e = upload(h, &h->d_fill_e, P.fill_e)) ||
+        (e = upload(h, &h->d_fill_k, P.fill_k))) {
         int s = cuda_fail(h, e, "hmat_create upload");
         std::fprintf(stderr, "hmat_create: %s\n", h->err.c_str());
         h->arena.release_all();
@@ -247,6 +248,7 @@ int precond_setup(hm_handle h)
     cudaEventRecord(e0, h->stream);
     int bad = -1;
     e = setup_run(h, &bad);
+    if (!e && bad < 0) e = compress_run(h);
     if (!e && bad < 0 && h->opts.precision == 1) e = make_fp32_copies(h, true);
     cudaEventRecord(e1, h->stream);
     cudaEventSynchronize(e1);
@@ -335,7 +337,14 @@ int hmat_stats(hm_handle h, hm_stats *s)
     s->near_entries = ne;
     s->far_entries = h->fplan.entries;
     s->fill_blocks = P.sptr.empty() ? 0 : P.sptr[P.nb];
-    s->coef_entries = P.coef_entries;
+    int64_t ce = P.coef_entries;
+    for (size_t f = 0; f < h->fill_ranks.size() && f < P.fill_e.size(); ++f) {
+        const int r = h->fill_ranks[f];
+        if (r < 0) continue;
+        const int64_t nk = P.size[P.fill_k[f]], nj = P.size[P.sidx[P.fill_e[f]]];
+        ce += (int64_t)r * (nk + nj) - nk * nj;
+    }
+    s->coef_entries = ce;
     s->coef_entries_dense = P.coef_entries;
     s->diag_entries = P.diag_entries;
     s->bandwidth = P.bandwidth;
@@ -381,6 +390,16 @@ int hm_get_fill(hm_handle h, int32_t *ptr, int32_t *idx)
     if (!h || !ptr) return HM_EINVAL;
     std::memcpy(ptr, h->plan.sptr.data(), sizeof(int32_t) * (h->plan.nb + 1));
     if (idx) std::memcpy(idx, h->plan.sidx.data(), sizeof(int32_t) * h->plan.sidx.size());
+    return HM_OK;
+}
+
+int hm_get_fill_ranks(hm_handle h, int32_t *rank)
+{
+    if (!h || !rank) return HM_EINVAL;
+    const Plan &P = h->plan;
+    const int ne = P.sptr.empty() ? 0 : P.sptr[P.nb];
+    for (int e = 0; e < ne; ++e) rank[e] = -1;
+    for (size_t f = 0; f < h->fill_ranks.size() && f < P.fill_e.size(); ++f) rank[P.fill_e[f]] = h->fill_ranks[f];
     return HM_OK;
 }
 

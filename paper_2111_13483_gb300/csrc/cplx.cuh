@@ -58,6 +58,10 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
 
 template <class T> __device__ __forceinline__ T cconv(double2 v);
 template <> __device__ __forceinline__ double2 cconv<double2>(double2 v) { return v; }

@@ -30,7 +30,7 @@ struct DBuf {
 // ---- per-kernel-class launch counts and (opt-in) CUDA-event timings ------------------
 enum KClass {
     K_SCATTER = 0, K_PIVOT, K_PANEL, K_UPDATE, K_SWEEP_FWD, K_SWEEP_BWD, K_FAR1, K_FAR2, K_DIAG, K_PERMUTE,
-    K_NEAR, K_DOTS, K_VEC, K_SMALL, K_NCLASS
+    K_NEAR, K_DOTS, K_VEC, K_SMALL, K_COMPRESS, K_NCLASS
 };
 
 struct Prof {
@@ -68,6 +68,9 @@ struct Plan {
     // forward sweep gathers: row i <- blocks W_ki, k < i; rptr/ridx = k, rcol = column
     // offset of block i inside panel k
     std::vector<int> rptr, ridx, rcol;
+    // fill-in blocks (Sec. 3.4): entries e of sidx whose pair (k, S_k[e]) is not a near pair
+    std::vector<int> fill_e;     // entry index into sidx
+    std::vector<int> fill_k;     // its block row k
     int bandwidth = 0;
     double setup_flops = 0;
     int max_S = 0, max_M = 0;
@@ -131,6 +134,9 @@ struct hm_ctx {
     double2 *d_Dinv = nullptr;   // D_k^{-1}
     bool setup_done = false;
     double setup_ms = 0;
+    // fill-in compression (Sec. 3.4): block lists and the ranks of the last setup (-1 dense)
+    int *d_fill_e = nullptr, *d_fill_k = nullptr, *d_fill_rank = nullptr;
+    std::vector<int> fill_ranks;
     // device: solve workspace
     int *d_flags = nullptr, *d_ticket = nullptr, *d_err = nullptr;
     int epoch = 0;
@@ -166,6 +172,7 @@ void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &p
 
 // kernels (setup.cu / solve.cu): return cudaError_t of the launches
 cudaError_t setup_run(hm_ctx *h, int *bad_block);
+cudaError_t compress_run(hm_ctx *h);
 cudaError_t op_apply(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
 cudaError_t op_apply32(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
 cudaError_t make_fp32_copies(hm_ctx *h, bool factors);

@@ -262,6 +262,22 @@ void plan_order(hm_ctx *h)
         P.bandwidth = std::max(P.bandwidth, std::abs(bi[b] - bj[b]));
     }
     symbolic_fill(nl, bi, bj, P.sptr, P.sidx);
+    {
+        // entries of the coefficient pattern that are not near pairs: the fill-in blocks
+        std::vector<int64_t> nk;
+        nk.reserve(bi.size());
+        for (size_t b = 0; b < bi.size(); ++b)
+            if (bi[b] != bj[b]) nk.push_back((int64_t)std::max(bi[b], bj[b]) * nl + std::min(bi[b], bj[b]));
+        std::sort(nk.begin(), nk.end());
+        P.fill_e.clear();
+        P.fill_k.clear();
+        for (int k = 0; k < nl; ++k)
+            for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e)
+                if (!std::binary_search(nk.begin(), nk.end(), (int64_t)P.sidx[e] * nl + k)) {
+                    P.fill_e.push_back(e);
+                    P.fill_k.push_back(k);
+                }
+    }
     // layouts
     P.srow.resize(P.sidx.size());
     P.M.assign(nl, 0);

@@ -56,10 +56,10 @@ class hm_stats(ctypes.Structure):
 EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_device", "hmat_stats",
            "hm_last_error", "hmat_destroy", "hm_get_order", "hm_get_fill", "hm_get_block", "hm_apply",
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
-           "hm_far_apply_noalloc"]
+           "hm_far_apply_noalloc", "hm_get_fill_ranks"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
-          "near", "dots", "vec", "small"]
+          "near", "dots", "vec", "small", "compress"]
 
 _lib = None
 
@@ -100,6 +100,7 @@ def load(build_if_missing=True):
     L.hm_profile.argtypes = [vp, ctypes.c_int32]
     L.hm_get_profile.argtypes = [vp, ctypes.c_int32, _i64p, _i64p, _f64p]
     L.hm_far_apply_noalloc.argtypes = [vp, vp, vp, ctypes.c_int32]
+    L.hm_get_fill_ranks.argtypes = [vp, _i32p]
     _lib = L
     return L
 
@@ -299,3 +300,11 @@ def hm_far_apply_noalloc(h, dx, dy):
     dx, dy: torch complex128 CUDA tensors (nrhs, n) in solve order.  Returns the status code
     (HM_EINVAL when the call needs more scratch than the static array holds)."""
     return load().hm_far_apply_noalloc(h.ptr, dx.data_ptr(), dy.data_ptr(), dx.shape[0])
+
+
+def hm_get_fill_ranks(h):
+    """Sec. 3.4 ranks per S_k entry (hm_get_fill order): r >= 0 compressed, -1 dense."""
+    ptr, idx = hm_get_fill(h)
+    out = np.zeros(max(1, len(idx)), dtype=np.int32)
+    h.check(load().hm_get_fill_ranks(h.ptr, _p(out, _i32p)), "hm_get_fill_ranks")
+    return out[:len(idx)]

@@ -195,3 +195,46 @@ def test_mixed_multi_rhs_equals_single(cfg1_mixed, cfg1_tight):
     for c in range(B.shape[1]):
         x1, it1, rr1, c1 = hm.solve(cfg1_mixed, B[:, c], tol=1e-5, restart=30)
         assert it1[0] == its[c] and np.array_equal(x1, I[:, c]), c
+
+
+# ---- Sec. 3.4 fill-in compression ------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg1_compressed(sphere1920):
+    P = sphere1920
+    order, F, S = oracle_factor(P, fill_tol=1e-2)
+    h = hm.hmat_create(P, ordering=1, fill_tol=1e-2)
+    hm.precond_setup(h)
+    return P, order, F, S, h
+
+
+def test_compression_ranks_and_blocks_match_oracle(cfg1_compressed):
+    """Ranks equal the oracle's truncated-SVD ranks (the same Frobenius-tail rule), and the
+    compressed coefficient blocks equal the oracle's truncations."""
+    P, order, F, S, h = cfg1_compressed
+    ptr, idx = hm.hm_get_fill(h)
+    ranks = hm.hmsolve.hm_get_fill_ranks(h)
+    n_comp = 0
+    for k in range(F.nb):
+        for a, j in enumerate(F.S[k]):
+            r_gpu = int(ranks[ptr[k] + a])
+            r_ora = F.rank.get((k, j), -1)
+            assert r_gpu == r_ora, (k, j, r_gpu, r_ora)
+            n_comp += r_gpu >= 0
+        if F.S[k]:
+            nk = int(F.size[k])
+            M = int(sum(F.size[j] for j in F.S[k]))
+            Wk = hm.hm_get_block(h, 2, k, (nk, M))
+            Wo = np.concatenate([F.Wc[(k, j)] for j in F.S[k]], axis=1)
+            assert rel(Wk, Wo) < 1e-8, k
+    assert n_comp > 0
+    st = hm.hmat_stats(h)
+    assert st["coef_entries"] < st["coef_entries_dense"]
+
+
+def test_compressed_solve_matches_oracle(cfg1_compressed):
+    P, order, F, S, h = cfg1_compressed
+    b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
+    x, it, rr, code = hm.solve(h, b, tol=1e-6, restart=30)
+    xo, ito, rro, ok = krylov.solve(S, b, tol=1e-6, restart=30)
+    assert code == 0 and ok and abs(int(it[0]) - ito) <= 1
+    assert rel(x, xo) <= 1e-8
