@@ -44,7 +44,8 @@ enum {
     HM_ENOCONV = -4,    /* maxit reached; the best iterate, iters and relres are written */
     HM_ETIMEOUT = -5,   /* a device-side bounded wait expired (no hang; context usable) */
     HM_ECUDA = -6,      /* CUDA runtime error */
-    HM_ESTATE = -7      /* call out of order (e.g. solve before precond_setup) */
+    HM_ESTATE = -7,     /* call out of order (e.g. solve before precond_setup) */
+    HM_EBUSY = -8       /* hm_batch_submit: every slot is occupied */
 };
 
 /*
@@ -140,9 +141,13 @@ int precond_setup(hm_handle h);
  * on Eq. 28 until the preconditioned relative residual is <= tol (FP64 mode) or, in
  * mixed mode, until ||V - Z I|| / ||V|| <= tol.  iters[j] = Arnoldi steps taken for
  * column j (inner steps in mixed mode), relres[j] = final relative residual of the
- * criterion above.  Columns are solved in lockstep batches; each column's Krylov space
- * is its own.  HM_ENOCONV if some column did not converge within maxit (its best
- * iterate is still written).
+ * criterion above.  Each column has its own Krylov space; up to 64 columns (mixed mode)
+ * or 16 (FP64) are in flight at a time, sharing each operator launch, and a finished
+ * column's place is taken by the next (the hm_batch engine below).  A column's result
+ * does not depend on the others.  HM_ENOCONV if some column did not converge within
+ * maxit (its best iterate is still written).  In mixed mode the inner solves run to
+ * min(0.5, max(1e-7, 0.3 tol ||V|| / ||V - Z I||)) and at most 40 refinement passes are
+ * made.
  */
 int solve(hm_handle h, const hm_c128 *V, int32_t nrhs, int64_t ldv, double tol, int32_t restart,
           int32_t maxit, hm_c128 *I, int64_t ldi, int32_t *iters, double *relres);
@@ -224,6 +229,52 @@ int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, 
  * Synchronises the handle's stream before returning.
  */
 int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
+
+/* ---- continuous batching (serving) ---------------------------------------------------- */
+
+/*
+ * A slot engine over one handle: each of `slots` slots holds one right-hand side and runs
+ * its own solve of Z I = V (Eq. 11) through the preconditioned system (Eq. 28) with
+ * GMRES(restart) -- FP64, or the mixed-precision refinement loop when the handle's
+ * precision is 1 -- exactly as solve() does.  hm_batch_step advances every occupied slot
+ * by one GMRES step (one operator application; all slots that need the same operator in a
+ * step share one multi-column launch); a slot whose solve has ended is reported, its
+ * result is read with hm_batch_result, which frees the slot for the next submission.
+ * Requests can therefore join while others are in flight.  A column's result is bitwise
+ * the same as solve() on that column alone.  The paper has no serving loop: this layer
+ * only schedules its solve.
+ *
+ * One batch per handle at a time; the handle's stream carries all of its work and a batch
+ * is used from one host thread.  The workspace (hm_batch_bytes) is taken from the
+ * handle's hbm_budget at open (HM_ENOMEM if it does not fit) and returned at close.
+ */
+typedef struct hm_batch_s *hm_batch;
+
+/* Device bytes hm_batch_open(h, slots, restart) takes (beyond the operator's own scratch). */
+int hm_batch_bytes(hm_handle h, int32_t slots, int32_t restart, int64_t *bytes);
+/* 1 <= slots <= 1024, restart >= 1.  HM_ESTATE before precond_setup or with a batch open. */
+int hm_batch_open(hm_handle h, int32_t slots, int32_t restart, hm_batch *out);
+/*
+ * Copies V (n entries, ORIGINAL order; host or device memory) into a free slot, which
+ * starts at the next step; *slot = its index.  tol and maxit as in solve().  HM_EBUSY
+ * (*slot = -2) when no slot is free.
+ */
+int hm_batch_submit(hm_batch b, const hm_c128 *V, double tol, int32_t maxit, int32_t *slot);
+/*
+ * One step of every occupied slot.  finished[] (room for `slots` entries) receives the
+ * slots whose solve ended in this step, *nfinished their count, *nactive (may be NULL) the
+ * slots still running.  Returns HM_OK, HM_ETIMEOUT or HM_ECUDA (then the batch should be
+ * closed).  Synchronises the handle's stream.
+ */
+int hm_batch_step(hm_batch b, int32_t *finished, int32_t *nfinished, int32_t *nactive);
+/*
+ * Copies the finished slot's solution I (n entries, ORIGINAL order) to host or device
+ * memory and frees the slot.  Returns the solve's status (HM_OK or HM_ENOCONV, with
+ * iters/relres as in solve()), or HM_ESTATE when the slot holds no finished solve.
+ */
+int hm_batch_result(hm_batch b, int32_t slot, hm_c128 *I, int32_t *iters, double *relres);
+/* Frees the workspace; unread results are dropped. */
+int hm_batch_close(hm_batch b);
 
 /* ---- host-only planning (no device work, no handle) -------------------------------- */
 

@@ -1,14 +1,22 @@
-// Restarted GMRES (Sec. 5) on the preconditioned system of Eq. 28, for batches of columns
-// in lockstep (each column its own Krylov space), and the mixed-precision refinement loop.
+// Restarted GMRES (Sec. 5) on the preconditioned system of Eq. 28 and the mixed-precision
+// refinement loop, run by a slot engine.  Every slot holds one right-hand side with its own
+// Krylov space, restart cycle and refinement state; one engine tick advances every occupied
+// slot by one step, and the operator applications of all slots that need the same operator
+// in that tick are packed into one multi-column launch.  A slot freed by a finished solve
+// takes a new right-hand side at the next tick (continuous batching), and solve() runs
+// through the same engine.  Every per-column reduction has a fixed order that does not
+// depend on the other columns of the pack, so a column's result is bitwise the same alone
+// and in any mix.
 //
 // FP64 mode: GMRES on A x~ = c with the FP64 operator, stop at |g_{j+1}| <= tol ||c||.
 // Mixed mode: an outer FP64 loop r = V - Z I (near blocks + far factors in FP64), inner
-// GMRES on A d~ = D^{-1} L^{-1} r with the complex-FP32 operator, I += L^{-T} d~, until
-// ||V - Z I|| <= tol ||V||.  Arnoldi vectors, Gram-Schmidt, Givens rotations and the
-// refinement residual are FP64 in both modes.
+// GMRES on A d~ = D^{-1} L^{-1} r with the complex-FP32 operator to the tolerance
+// clamp(0.3 tol ||V|| / ||r||, 1e-7, 0.5), I += L^{-T} d~, until ||V - Z I|| <= tol ||V||.
+// Krylov vectors, Gram-Schmidt, Givens rotations and the refinement residual are FP64 in
+// both modes.
 #include <algorithm>
 #include <cmath>
-#include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "cplx.cuh"
@@ -17,19 +25,32 @@
 namespace hm {
 
 constexpr int DOT_CHUNK = 4096;
+constexpr int MAX_OUTER = 40;
 
-// part[((c*J + i) * nchunk + chunk)] = sum over the chunk's rows of conj(V_i) w (i < J);
-// basis V_i of column c at Vb + (i*nc + c)*n
-__global__ void __launch_bounds__(256) k_dots(int n, int nc, int J, const double2 *Vb, const double2 *w,
-                                              double2 *part, int nchunk)
+// Packed column p, vector i of a family: base + (idx[p] + i * istep) * n.
+struct VRef {
+    double2 *base;
+    const int *idx;
+    int64_t istep, n;
+    __device__ __forceinline__ double2 *at(int p, int i = 0) const
+    {
+        return base + ((int64_t)idx[p] + (int64_t)i * istep) * n;
+    }
+};
+
+// part[((p*ldp + i) * nchunk + chunk)] = sum over the chunk's rows of conj(basis_i) w, i < J[p]
+// (J == nullptr: one vector)
+__global__ void __launch_bounds__(256) k_dots(int n, VRef basis, const int *J, VRef w, double2 *part, int nchunk,
+                                              int ldp)
 {
     __shared__ double2 red[8][33];
-    const int chunk = blockIdx.x, c = blockIdx.y;
+    const int chunk = blockIdx.x, p = blockIdx.y;
     const int lo = chunk * DOT_CHUNK, hi = min(n, lo + DOT_CHUNK);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const double2 *wc = w + (int64_t)c * n;
-    for (int i0 = 0; i0 < J; i0 += 32) {
-        const int ni = min(32, J - i0);
+    const int Jp = J ? J[p] : 1;
+    const double2 *wc = w.at(p);
+    for (int i0 = 0; i0 < Jp; i0 += 32) {
+        const int ni = min(32, Jp - i0);
         double2 acc[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) acc[q] = make_double2(0, 0);
@@ -37,7 +58,7 @@ __global__ void __launch_bounds__(256) k_dots(int n, int nc, int J, const double
             double2 wv = wc[row];
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-                if (q < ni) acc[q] = cjfma(Vb[((int64_t)(i0 + q) * nc + c) * n + row], wv, acc[q]);
+                if (q < ni) acc[q] = cjfma(basis.at(p, i0 + q)[row], wv, acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -56,114 +77,122 @@ __global__ void __launch_bounds__(256) k_dots(int n, int nc, int J, const double
                 v.x += red[q][threadIdx.x].x;
                 v.y += red[q][threadIdx.x].y;
             }
-            part[((int64_t)c * J + i0 + threadIdx.x) * nchunk + chunk] = v;
+            part[((int64_t)p * ldp + i0 + threadIdx.x) * nchunk + chunk] = v;
         }
         __syncthreads();
     }
 }
 
-// out[c*ldo + i] = sum over chunks of part (fixed order)
-__global__ void k_dots_final(int nc, int J, int nchunk, const double2 *part, double2 *out, int ldo)
+// out[oidx[p]*ldo + i] = sum over chunks of part (fixed order), i < J[p]
+__global__ void k_dots_final(int k, int ldp, const int *J, int nchunk, const double2 *part, double2 *out, int ldo,
+                             const int *oidx)
 {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nc * J) return;
-    int c = e / J, i = e % J;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= k * ldp) return;
+    const int p = e / ldp, i = e % ldp;
+    if (i >= J[p]) return;
     double2 v = make_double2(0, 0);
-    const double2 *p = part + (int64_t)e * nchunk;
-    for (int q = 0; q < nchunk; ++q) {
-        v.x += p[q].x;
-        v.y += p[q].y;
+    const double2 *q = part + (int64_t)e * nchunk;
+    for (int c = 0; c < nchunk; ++c) {
+        v.x += q[c].x;
+        v.y += q[c].y;
     }
-    out[(int64_t)c * ldo + i] = v;
+    out[(int64_t)oidx[p] * ldo + i] = v;
 }
 
-// w[:, c] -= sum_{i<J} h[c*ldh + i] V_i[:, c]
-__global__ void k_axpy_basis(int n, int nc, int J, const double2 *Vb, const double2 *h, int ldh, double2 *w)
+// out[oidx[p]] = sqrt(max(0, Re sum over chunks of part[p]))   (a 2-norm from k_dots with J = 1)
+__global__ void k_norm_final(int k, int nchunk, const double2 *part, double *out, const int *oidx)
 {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n * nc) return;
-    int row = (int)(e % n), c = (int)(e / n);
-    double2 acc = w[e];
-    for (int i = 0; i < J; ++i) acc = cfms(h[(int64_t)c * ldh + i], Vb[((int64_t)i * nc + c) * n + row], acc);
-    w[e] = acc;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= k) return;
+    double v = 0.0;
+    const double2 *q = part + (int64_t)p * nchunk;
+    for (int c = 0; c < nchunk; ++c) v += q[c].x;
+    out[oidx[p]] = sqrt(fmax(0.0, v));
 }
 
-// x[:, c] += sum_{i<J[c]} y[c*ldy + i] V_i[:, c]
-__global__ void k_update_x(int n, int nc, const int *J, const double2 *Vb, const double2 *yv, int ldy, double2 *x)
+// w_p -= sum_{i<J[p]} h[hidx[p]*ldh + i] basis_i(p)
+__global__ void k_axpy_basis(int n, int k, VRef basis, const int *J, const double2 *h, int ldh, const int *hidx,
+                             VRef w)
 {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n * nc) return;
-    int row = (int)(e % n), c = (int)(e / n);
-    double2 acc = x[e];
-    for (int i = 0; i < J[c]; ++i) acc = cfma(yv[(int64_t)c * ldy + i], Vb[((int64_t)i * nc + c) * n + row], acc);
-    x[e] = acc;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    const int row = (int)(e % n), p = (int)(e / n);
+    double2 *wp = w.at(p);
+    double2 acc = wp[row];
+    const double2 *hp = h + (int64_t)hidx[p] * ldh;
+    for (int i = 0; i < J[p]; ++i) acc = cfms(hp[i], basis.at(p, i)[row], acc);
+    wp[row] = acc;
 }
 
-// v[:, c] = w[:, c] / nrm[c] (0 when nrm[c] = 0)
-__global__ void k_scale(int n, int nc, const double *nrm, const double2 *w, double2 *v)
+// dst[idx[p]*ld + i] += src[idx[p]*ld + i], i < J[p]
+__global__ void k_hfold(int k, int ldp, const int *J, const int *idx, const double2 *src, double2 *dst, int ld)
 {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n * nc) return;
-    int c = (int)(e / n);
-    double s = nrm[c] > 0 ? 1.0 / nrm[c] : 0.0;
-    double2 a = w[e];
-    v[e] = make_double2(a.x * s, a.y * s);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= k * ldp) return;
+    const int p = e / ldp, i = e % ldp;
+    if (i >= J[p]) return;
+    const int64_t o = (int64_t)idx[p] * ld + i;
+    dst[o].x += src[o].x;
+    dst[o].y += src[o].y;
 }
 
-// r = c - r
-__global__ void k_sub_from(int64_t len, const double2 *c, double2 *r)
+// v_p = w_p / nrm[nidx[p]] (0 when the norm is 0)
+__global__ void k_scale(int n, int k, const double *nrm, const int *nidx, VRef w, VRef v)
 {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= len) return;
-    r[e] = make_double2(c[e].x - r[e].x, c[e].y - r[e].y);
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    const int row = (int)(e % n), p = (int)(e / n);
+    const double r = nrm[nidx[p]];
+    const double s = r > 0 ? 1.0 / r : 0.0;
+    const double2 a = w.at(p)[row];
+    v.at(p)[row] = make_double2(a.x * s, a.y * s);
 }
 
-// x += a
-__global__ void k_add_to(int64_t len, const double2 *a, double2 *x)
+// elementwise column ops on packed families: mode 0 dst = a; 1 dst = a - b; 2 dst += a; 3 dst = 0
+__global__ void k_vec(int n, int k, int mode, VRef a, VRef b, VRef dst)
 {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= len) return;
-    x[e] = make_double2(x[e].x + a[e].x, x[e].y + a[e].y);
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    const int row = (int)(e % n), p = (int)(e / n);
+    double2 *d = dst.at(p) + row;
+    if (mode == 3) {
+        *d = make_double2(0, 0);
+        return;
+    }
+    const double2 x = a.at(p)[row];
+    if (mode == 0) *d = x;
+    else if (mode == 1) {
+        const double2 y = b.at(p)[row];
+        *d = make_double2(x.x - y.x, x.y - y.y);
+    } else
+        *d = make_double2(d->x + x.x, d->y + x.y);
 }
 
-// zero the columns whose mask is 0
-__global__ void k_mask_cols(int n, int nc, const int *mask, double2 *v)
-{
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n * nc) return;
-    if (!mask[e / n]) v[e] = make_double2(0, 0);
-}
-
-// dst[c] = sqrt(max(0, Re src[c*lds]))
-__global__ void k_sqrt_re(int nc, const double2 *src, int lds, double *dst)
-{
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < nc) dst[c] = sqrt(fmax(0.0, src[(int64_t)c * lds].x));
-}
-
-// dst[c*ldd + i] += src[c*lds + i], i < J
-__global__ void k_hfold(int nc, int J, const double2 *src, int lds, double2 *dst, int ldd)
-{
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nc * J) return;
-    int c = e / J, i = e % J;
-    dst[(int64_t)c * ldd + i].x += src[(int64_t)c * lds + i].x;
-    dst[(int64_t)c * ldd + i].y += src[(int64_t)c * lds + i].y;
-}
-
-// GMRES small-matrix state per column c (H: (m+1) x m column-major, ld m+1)
+// GMRES small-matrix state per slot c (H: (m+1) x m column-major, ld m+1)
 struct GState {
     double2 *H, *g, *sn, *y, *hj;
     double *cs, *nrm, *res, *wn;
-    int *J, *active;
+    int *J;
 };
 
-// Hessenberg column j of each active column: h[0..j] from hj, h[j+1] = nrm; previous
-// rotations, a new complex Givens rotation with real cosine, residual estimate |g_{j+1}|.
-__global__ void k_givens(int nc, int m, int j, GState s)
+// A new cycle for slot[p]: g = beta e_1 (beta = nrm[slot]), J = 0
+__global__ void k_cycle_init(int k, int m, const int *slot, GState s)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc || !s.active[c]) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= k * (m + 1)) return;
+    const int p = e / (m + 1), i = e % (m + 1), c = slot[p];
+    s.g[(int64_t)c * (m + 1) + i] = make_double2(i == 0 ? s.nrm[c] : 0.0, 0.0);
+    if (i == 0) s.J[c] = 0;
+}
+
+// Hessenberg column j = J[c] of slot c: h[0..j] from hj, h[j+1] = nrm; previous rotations,
+// a new complex Givens rotation with real cosine, residual estimate |g_{j+1}|.
+__global__ void k_givens(int k, int m, const int *slot, GState s)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= k) return;
+    const int c = slot[p], j = s.J[c];
     double2 *H = s.H + (int64_t)c * (m + 1) * m;
     double2 *hj = s.hj + (int64_t)c * (m + 1);
     double2 *g = s.g + (int64_t)c * (m + 1);
@@ -208,15 +237,16 @@ __global__ void k_givens(int nc, int m, int j, GState s)
     s.J[c] = j + 1;
 }
 
-// y = H(1:J,1:J)^{-1} g(1:J) per column (back substitution)
-__global__ void k_trisolve(int nc, int m, GState s)
+// y = H(1:J,1:J)^{-1} g(1:J) for slot[p] (back substitution)
+__global__ void k_trisolve(int k, int m, const int *slot, GState s)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= k) return;
+    const int c = slot[p];
     const double2 *H = s.H + (int64_t)c * (m + 1) * m;
     const double2 *g = s.g + (int64_t)c * (m + 1);
     double2 *y = s.y + (int64_t)c * m;
-    int J = s.J[c];
+    const int J = s.J[c];
     for (int i = J - 1; i >= 0; --i) {
         double2 v = g[i];
         for (int q = i + 1; q < J; ++q) v = cfms(H[i + (int64_t)q * (m + 1)], y[q], v);
@@ -226,351 +256,571 @@ __global__ void k_trisolve(int nc, int m, GState s)
     }
 }
 
+// x_p += sum_{i<J[c]} y_c[i] basis_i(p), c = slot[p]
+__global__ void k_update_x(int n, int k, const int *slot, const int *J, VRef basis, const double2 *yv, int ldy, VRef x)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    const int row = (int)(e % n), p = (int)(e / n), c = slot[p];
+    double2 *xp = x.at(p);
+    double2 acc = xp[row];
+    for (int i = 0; i < J[c]; ++i) acc = cfma(yv[(int64_t)c * ldy + i], basis.at(p, i)[row], acc);
+    xp[row] = acc;
+}
+
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-static cudaError_t apply_op(hm_ctx *h, bool fp32, int op, const double2 *x, double2 *y, int nrhs)
-{
-    return fp32 ? op_apply32(h, op, x, y, nrhs) : op_apply(h, op, x, y, nrhs);
-}
+// ---- the engine ----------------------------------------------------------------------------
+enum SlotState { FREE = 0, OUTER, RESTART, ARNOLDI, INNER_END, DONE };
 
-// Column 2-norms of v (n x nc) -> out (device) and returned to the host.
-static std::vector<double> col_norms(hm_ctx *h, const double2 *v, int nc, double2 *part, double2 *tmp, double *out)
-{
-    const int n = h->plan.n, nchunk = (n + DOT_CHUNK - 1) / DOT_CHUNK;
-    cudaStream_t st = h->stream;
-    HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, v, v, part, nchunk));
-    HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, tmp, 1));
-    HM_LAUNCH(h, K_SMALL, k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, tmp, 1, out));
-    std::vector<double> nv(nc);
-    cudaMemcpyAsync(nv.data(), out, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    return nv;
-}
+struct Slot {
+    int state = FREE;
+    int j = 0, it = 0, it_in = 0, in_max = 0, outer = 0, maxit = 0, status = HM_OK;
+    bool first = false, conv = false, reported = false;
+    double tol = 0, itol = 0, bn = 0, cn = 0, rel = 0;
+};
 
-// Batched GMRES(m) on Eq. 28 for nc <= 64 columns in solve order: c (rhs), x (in/out,
-// starts at zero).  Column c stops at |g_{j+1}| <= tol[c] ||c_c||.  Arnoldi by classical
-// Gram-Schmidt applied twice (the oracle's modified Gram-Schmidt spans the same space up
-// to rounding).  One host synchronisation per Arnoldi step reads the residual estimates.
-static int gmres_batch(hm_ctx *h, bool fp32, const double2 *cvec, double2 *x, int nc, const std::vector<double> &tol,
-                       int m, int maxit, int *iters, double *relres)
-{
-    cudaStream_t st = h->stream;
-    const int n = h->plan.n;
-    const int nchunk = (n + DOT_CHUNK - 1) / DOT_CHUNK;
-    cudaError_t e = cudaSuccess;
-    std::vector<void *> allocs;
-    auto A = [&](void **p, size_t bytes) {
-        cudaError_t r = h->arena.alloc(p, bytes);
-        if (r == cudaSuccess) allocs.push_back(*p);
-        return r;
-    };
-    double2 *Vb, *w, *part, *hcol, *h2, *r;
+struct Engine {
+    hm_ctx *h = nullptr;
+    int S = 0, m = 0, n = 0, nchunk = 0;
+    bool fp32 = false;
+    // per-slot vectors (slot stride n): V, I (original order), FP64 residual, c and x~ (solve order)
+    double2 *B = nullptr, *XO = nullptr, *R = nullptr, *C = nullptr, *XT = nullptr;
+    double2 *Vb = nullptr;                   // Krylov basis: vector i of slot c at (i*S + c) * n
+    double2 *PX = nullptr, *PY = nullptr, *PT = nullptr;   // packed operator operands
+    double2 *part = nullptr, *h2 = nullptr;
+    double *tmp = nullptr;                   // per-slot norms of the control phases
     GState s{};
-    if ((e = A((void **)&Vb, sizeof(double2) * (size_t)n * nc * (m + 1))) ||
-        (e = A((void **)&w, sizeof(double2) * (size_t)n * nc)) ||
-        (e = A((void **)&r, sizeof(double2) * (size_t)n * nc)) ||
-        (e = A((void **)&part, sizeof(double2) * (size_t)nchunk * nc * (m + 1))) ||
-        (e = A((void **)&hcol, sizeof(double2) * (size_t)nc * (m + 1))) ||
-        (e = A((void **)&h2, sizeof(double2) * (size_t)nc * (m + 1))) ||
-        (e = A((void **)&s.H, sizeof(double2) * (size_t)nc * (m + 1) * m)) ||
-        (e = A((void **)&s.g, sizeof(double2) * (size_t)nc * (m + 1))) ||
-        (e = A((void **)&s.sn, sizeof(double2) * (size_t)nc * m)) ||
-        (e = A((void **)&s.y, sizeof(double2) * (size_t)nc * m)) ||
-        (e = A((void **)&s.cs, sizeof(double) * (size_t)nc * m)) ||
-        (e = A((void **)&s.nrm, sizeof(double) * nc)) || (e = A((void **)&s.res, sizeof(double) * nc)) ||
-        (e = A((void **)&s.wn, sizeof(double) * nc)) || (e = A((void **)&s.J, sizeof(int) * nc)) ||
-        (e = A((void **)&s.active, sizeof(int) * nc))) {
-        for (void *p : allocs) h->arena.release(p, 0);
-        h->err = "GMRES workspace allocation failed";
-        return HM_ENOMEM;
+    int *d_idx = nullptr, *h_idx = nullptr;  // index uploads (pinned ring, NIDX regions of S)
+    int *d_iota = nullptr;
+    int ring = 0;
+    std::vector<void *> allocs;
+    std::vector<Slot> sl;
+    static constexpr int NIDX = 24;
+
+    static size_t bytes(int n, int S, int m)
+    {
+        const int nchunk = (n + DOT_CHUNK - 1) / DOT_CHUNK;
+        size_t b = sizeof(double2) * (size_t)n * S * (5 + (m + 1) + 3);
+        b += sizeof(double2) * (size_t)nchunk * S * (m + 1);
+        b += sizeof(double2) * (size_t)S * ((m + 1) * 2 + (m + 1) * m + (m + 1) + 2 * m);
+        b += sizeof(double) * (size_t)S * (m + 5) + sizeof(int) * (size_t)S * (NIDX + 2);
+        return b;
     }
-    s.hj = hcol;
-    std::vector<double> cn = col_norms(h, cvec, nc, part, h2, s.res);
-    std::vector<int> conv(nc, 0), it(nc, 0);
-    std::vector<double> rr(nc, 0.0);
-    for (int c = 0; c < nc; ++c)
-        if (cn[c] == 0.0) conv[c] = 1;
-    int status = HM_OK;
-    bool first = true;
-    while (true) {
-        // r = c - A x (x = 0 on the first cycle): the true residual at every restart
-        if (first)
-            cudaMemcpyAsync(r, cvec, sizeof(double2) * (size_t)n * nc, cudaMemcpyDeviceToDevice, st);
-        else {
-            if ((e = apply_op(h, fp32, 0, x, r, nc))) break;
-            HM_LAUNCH(h, K_VEC, k_sub_from<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>((int64_t)n * nc, cvec, r));
-        }
-        first = false;
-        std::vector<double> beta = col_norms(h, r, nc, part, h2, s.nrm);
-        std::vector<int> act(nc, 0);
-        bool any = false;
-        for (int c = 0; c < nc; ++c) {
-            if (conv[c]) continue;
-            if (beta[c] <= tol[c] * cn[c]) {
-                conv[c] = 1;
-                rr[c] = beta[c] / cn[c];
-                continue;
+
+    cudaError_t open(hm_ctx *hh, int slots, int restart)
+    {
+        h = hh;
+        S = slots;
+        m = restart;
+        n = h->plan.n;
+        nchunk = (n + DOT_CHUNK - 1) / DOT_CHUNK;
+        fp32 = h->opts.precision == 1;
+        sl.assign(S, Slot());
+        cudaError_t e;
+        auto A = [&](void **p, size_t b) {
+            cudaError_t r = h->arena.alloc(p, b);
+            if (r == cudaSuccess) allocs.push_back(*p);
+            return r;
+        };
+        const size_t vs = sizeof(double2) * (size_t)n * S;
+        if ((e = A((void **)&B, vs)) || (e = A((void **)&XO, vs)) || (e = A((void **)&R, vs)) ||
+            (e = A((void **)&C, vs)) || (e = A((void **)&XT, vs)) || (e = A((void **)&Vb, vs * (m + 1))) ||
+            (e = A((void **)&PX, vs)) || (e = A((void **)&PY, vs)) || (e = A((void **)&PT, vs)) ||
+            (e = A((void **)&part, sizeof(double2) * (size_t)nchunk * S * (m + 1))) ||
+            (e = A((void **)&h2, sizeof(double2) * (size_t)S * (m + 1))) ||
+            (e = A((void **)&s.hj, sizeof(double2) * (size_t)S * (m + 1))) ||
+            (e = A((void **)&s.H, sizeof(double2) * (size_t)S * (m + 1) * m)) ||
+            (e = A((void **)&s.g, sizeof(double2) * (size_t)S * (m + 1))) ||
+            (e = A((void **)&s.sn, sizeof(double2) * (size_t)S * m)) ||
+            (e = A((void **)&s.y, sizeof(double2) * (size_t)S * m)) ||
+            (e = A((void **)&s.cs, sizeof(double) * (size_t)S * m)) || (e = A((void **)&s.nrm, sizeof(double) * S)) ||
+            (e = A((void **)&s.res, sizeof(double) * S)) || (e = A((void **)&s.wn, sizeof(double) * S)) ||
+            (e = A((void **)&tmp, sizeof(double) * S)) || (e = A((void **)&s.J, sizeof(int) * S)) ||
+            (e = A((void **)&d_idx, sizeof(int) * (size_t)S * NIDX)) || (e = A((void **)&d_iota, sizeof(int) * S)))
+            return e;
+        if ((e = cudaMallocHost((void **)&h_idx, sizeof(int) * (size_t)S * NIDX))) return e;
+        std::vector<int> io(S);
+        for (int c = 0; c < S; ++c) io[c] = c;
+        if ((e = cudaMemcpyAsync(d_iota, io.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->stream))) return e;
+        // the operator workspace for the widest pack
+        if ((e = ensure_solve_workspace(h, std::min(S, fp32 ? 64 : 16)))) return e;
+        return cudaStreamSynchronize(h->stream);
+    }
+
+    void close()
+    {
+        if (h) cudaStreamSynchronize(h->stream);
+        for (void *p : allocs) h->arena.release(p, 0);
+        allocs.clear();
+        if (h_idx) cudaFreeHost(h_idx);
+        h_idx = nullptr;
+    }
+
+    // copy an index list to the device (a fresh region of the ring; every tick ends synchronised)
+    const int *upload(const std::vector<int> &v)
+    {
+        int *hp = h_idx + (size_t)ring * S, *dp = d_idx + (size_t)ring * S;
+        ring = (ring + 1) % NIDX;
+        std::memcpy(hp, v.data(), sizeof(int) * v.size());
+        cudaMemcpyAsync(dp, hp, sizeof(int) * v.size(), cudaMemcpyHostToDevice, h->stream);
+        return dp;
+    }
+
+    VRef ref(double2 *base, const int *idx, int64_t istep = 0) const { return VRef{base, idx, istep, n}; }
+    VRef packed(double2 *base, int off = 0) const { return VRef{base, d_iota + off, 0, n}; }
+
+    void vec(int mode, int k, VRef a, VRef b, VRef d)
+    {
+        HM_LAUNCH(h, K_VEC, k_vec<<<nblk((int64_t)n * k, 256), 256, 0, h->stream>>>(n, k, mode, a, b, d));
+    }
+
+    cudaError_t op(int code, const double2 *x, double2 *y, int k)
+    {
+        return fp32 ? op_apply32(h, code, x, y, k) : op_apply(h, code, x, y, k);
+    }
+
+    // 2-norms of k packed vectors v -> out[oidx[p]]
+    void norms(int k, VRef v, double *out, const int *oidx)
+    {
+        HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, k), 256, 0, h->stream>>>(n, v, nullptr, v, part, nchunk, 1));
+        HM_LAUNCH(h, K_SMALL, k_norm_final<<<nblk(k, 128), 128, 0, h->stream>>>(k, nchunk, part, out, oidx));
+    }
+
+    cudaError_t fetch(const double *d, std::vector<double> &hv)
+    {
+        hv.resize(S);
+        cudaMemcpyAsync(hv.data(), d, sizeof(double) * S, cudaMemcpyDeviceToHost, h->stream);
+        return cudaStreamSynchronize(h->stream);
+    }
+
+    std::vector<int> in_state(int st) const
+    {
+        std::vector<int> v;
+        for (int c = 0; c < S; ++c)
+            if (sl[c].state == st) v.push_back(c);
+        return v;
+    }
+
+    // take a free slot for the right-hand side V (n entries, original order, host or device
+    // memory); returns the slot, -2 when none is free, -1 on a CUDA error
+    int submit(const double2 *V, double tol, int maxit)
+    {
+        for (int c = 0; c < S; ++c)
+            if (sl[c].state == FREE) {
+                cudaError_t e = cudaMemcpyAsync(B + (size_t)c * n, V, sizeof(double2) * n, cudaMemcpyDefault, h->stream);
+                if (!e) e = cudaMemsetAsync(XO + (size_t)c * n, 0, sizeof(double2) * n, h->stream);
+                if (e) return -1;
+                Slot z;
+                z.state = OUTER;
+                z.tol = tol;
+                z.maxit = maxit;
+                sl[c] = z;
+                return c;
             }
-            if (it[c] >= maxit) {
-                rr[c] = beta[c] / cn[c];
-                continue;
+        return -2;
+    }
+
+    // the inner solve of these slots has ended: fold x~ back (mixed) or form the solution (FP64)
+    cudaError_t inner_end(const std::vector<int> &E)
+    {
+        const int k = (int)E.size();
+        const int *id = upload(E);
+        cudaError_t e;
+        vec(0, k, ref(XT, id), ref(XT, id), packed(PX));
+        if ((e = op(2, PX, PY, k)) || (e = to_orig_order(h, PY, PT, n, k))) return e;
+        vec(fp32 ? 2 : 0, k, packed(PT), packed(PT), ref(XO, id));
+        for (int c : E) {
+            Slot &z = sl[c];
+            if (fp32) {
+                z.outer++;
+                z.state = OUTER;
+            } else {
+                z.state = DONE;
+                z.status = z.conv ? HM_OK : HM_ENOCONV;
             }
-            act[c] = 1;
-            any = true;
         }
-        if (!any) break;
-        cudaMemcpyAsync(s.active, act.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st);
-        HM_LAUNCH(h, K_VEC, k_scale<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.nrm, r, Vb));   // V_0 = r/beta
-        std::vector<double2> g0((size_t)nc * (m + 1), make_double2(0, 0));
-        for (int c = 0; c < nc; ++c) g0[(size_t)c * (m + 1)] = make_double2(beta[c], 0);
-        cudaMemcpyAsync(s.g, g0.data(), sizeof(double2) * g0.size(), cudaMemcpyHostToDevice, st);
-        cudaMemsetAsync(s.J, 0, sizeof(int) * nc, st);
-        std::vector<int> done(nc, 0);
-        for (int c = 0; c < nc; ++c) done[c] = !act[c];
-        std::vector<double> res(nc), wpre(nc), wn(nc);
-        for (int j = 0; j < m; ++j) {
-            double2 *vj = Vb + (size_t)j * nc * n, *vj1 = Vb + (size_t)(j + 1) * nc * n;
-            if ((e = apply_op(h, fp32, 0, vj, w, nc))) break;
-            // ||w|| before orthogonalisation (happy-breakdown reference)
-            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, w, w, part, nchunk));
-            HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1));
-            HM_LAUNCH(h, K_SMALL, k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, s.wn));
-            // CGS2: h = V^H w, w -= V h, twice; coefficients accumulated in hcol
-            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, j + 1, Vb, w, part, nchunk));
-            HM_LAUNCH(h, K_SMALL,
-                      k_dots_final<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, nchunk, part, hcol, m + 1));
-            HM_LAUNCH(h, K_VEC,
-                      k_axpy_basis<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, j + 1, Vb, hcol, m + 1, w));
-            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, j + 1, Vb, w, part, nchunk));
-            HM_LAUNCH(h, K_SMALL,
-                      k_dots_final<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, nchunk, part, h2, m + 1));
-            HM_LAUNCH(h, K_VEC,
-                      k_axpy_basis<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, j + 1, Vb, h2, m + 1, w));
-            HM_LAUNCH(h, K_SMALL, k_hfold<<<nblk(nc * (j + 1), 128), 128, 0, st>>>(nc, j + 1, h2, m + 1, hcol, m + 1));
-            // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
-            HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, nc), 256, 0, st>>>(n, nc, 1, w, w, part, nchunk));
-            HM_LAUNCH(h, K_SMALL, k_dots_final<<<nblk(nc, 128), 128, 0, st>>>(nc, 1, nchunk, part, h2, 1));
-            HM_LAUNCH(h, K_SMALL, k_sqrt_re<<<nblk(nc, 128), 128, 0, st>>>(nc, h2, 1, s.nrm));
-            HM_LAUNCH(h, K_VEC, k_scale<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.nrm, w, vj1));
-            HM_LAUNCH(h, K_SMALL, k_givens<<<nblk(nc, 64), 64, 0, st>>>(nc, m, j, s));
-            cudaMemcpyAsync(res.data(), s.res, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(wpre.data(), s.wn, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(wn.data(), s.nrm, sizeof(double) * nc, cudaMemcpyDeviceToHost, st);
-            if ((e = cudaStreamSynchronize(st))) break;
-            bool all = true;
-            std::vector<int> act2(nc, 0);
-            for (int c = 0; c < nc; ++c) {
-                if (done[c]) continue;
-                it[c]++;
-                bool brk = wn[c] <= 1e-14 * wpre[c];
-                rr[c] = res[c] / cn[c];
-                if (res[c] <= tol[c] * cn[c] || brk) {
-                    done[c] = 1;
-                    conv[c] = 1;
-                } else if (it[c] >= maxit)
-                    done[c] = 1;
-                if (!done[c]) {
-                    all = false;
-                    act2[c] = 1;
+        return cudaGetLastError();
+    }
+
+    // start (FP64) or continue (mixed) the refinement: residual, stopping test, c = D^{-1} L^{-1} r
+    cudaError_t outer(const std::vector<int> &O)
+    {
+        cudaError_t e;
+        std::vector<int> go;
+        if (fp32) {
+            std::vector<int> O0, O1;
+            for (int c : O) (sl[c].outer == 0 ? O0 : O1).push_back(c);
+            if (!O1.empty()) {   // r = V - Z I in FP64
+                const int k = (int)O1.size();
+                const int *id = upload(O1);
+                vec(0, k, ref(XO, id), ref(XO, id), packed(PX));
+                if ((e = z_apply_orig(h, PX, PY, k))) return e;
+                vec(1, k, ref(B, id), packed(PY), ref(R, id));
+            }
+            if (!O0.empty()) {
+                const int *id = upload(O0);
+                vec(0, (int)O0.size(), ref(B, id), ref(B, id), ref(R, id));
+            }
+            const int *id = upload(O);
+            norms((int)O.size(), ref(R, id), tmp, id);
+            std::vector<double> rn;
+            if ((e = fetch(tmp, rn))) return e;
+            for (int c : O) {
+                Slot &z = sl[c];
+                if (z.outer == 0) z.bn = rn[c];
+                z.rel = z.bn > 0 ? rn[c] / z.bn : 0.0;
+                if (z.rel <= z.tol || z.bn == 0.0) {
+                    z.state = DONE;
+                    z.status = HM_OK;
+                } else if (z.it >= z.maxit || z.outer == MAX_OUTER) {
+                    z.state = DONE;
+                    z.status = HM_ENOCONV;
+                } else {
+                    // ask the inner solve for a little more than what is still missing
+                    z.itol = std::min(0.5, std::max(1e-7, 0.3 * z.tol / z.rel));
+                    z.in_max = std::max(z.maxit - z.it, 1);
+                    go.push_back(c);
                 }
             }
-            if (all) break;
-            cudaMemcpyAsync(s.active, act2.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st);
+        } else {
+            go = O;
+            for (int c : O) {
+                sl[c].itol = sl[c].tol;
+                sl[c].in_max = sl[c].maxit;
+            }
         }
-        if (e) break;
-        // x += V y per column (J[c] = steps of this cycle, 0 for columns that sat it out)
-        HM_LAUNCH(h, K_SMALL, k_trisolve<<<nblk(nc, 64), 64, 0, st>>>(nc, m, s));
-        HM_LAUNCH(h, K_VEC, k_update_x<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, s.J, Vb, s.y, m, x));
-        if ((e = cudaStreamSynchronize(st))) break;
-        bool all_done = true;
-        for (int c = 0; c < nc; ++c)
-            if (!conv[c] && it[c] < maxit) all_done = false;
-        if (all_done) break;
-    }
-    for (void *p : allocs) h->arena.release(p, 0);
-    if (e) {
-        h->err = std::string("CUDA error in GMRES: ") + cudaGetErrorString(e);
-        return HM_ECUDA;
-    }
-    int herr = 0;
-    cudaMemcpy(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (herr & ERR_TIMEOUT) {
-        h->err = "device-side wait in a triangular sweep timed out";
-        return HM_ETIMEOUT;
-    }
-    for (int c = 0; c < nc; ++c) {
-        iters[c] = it[c];
-        relres[c] = rr[c];
-        if (!conv[c]) status = HM_ENOCONV;
-    }
-    return status;
-}
-
-// FP64 mode: GMRES on Eq. 28 with the FP64 operator.
-static int solve_fp64(hm_ctx *h, const double2 *dV, int nc, int64_t ldv, double tol, int restart, int maxit,
-                      double2 *dI, int64_t ldi, int *iters, double *relres, double2 *bnew, double2 *cvec, double2 *xt)
-{
-    const int n = h->plan.n;
-    cudaError_t e;
-    if ((e = to_solve_order(h, dV, ldv, bnew, nc)) || (e = op_apply(h, 1, bnew, xt, nc)) ||
-        (e = op_apply(h, 4, xt, cvec, nc))) {
-        h->err = cudaGetErrorString(e);
-        return HM_ECUDA;
-    }
-    cudaMemsetAsync(xt, 0, sizeof(double2) * (size_t)n * nc, h->stream);
-    int s = gmres_batch(h, false, cvec, xt, nc, std::vector<double>(nc, tol), restart, maxit, iters, relres);
-    if (s != HM_OK && s != HM_ENOCONV) return s;
-    if ((e = op_apply(h, 2, xt, bnew, nc)) || (e = to_orig_order(h, bnew, dI, ldi, nc))) {
-        h->err = cudaGetErrorString(e);
-        return HM_ECUDA;
-    }
-    return s;
-}
-
-// Mixed mode: FP64 residual-and-correction loop around the complex-FP32 inner solve.
-static int solve_mixed(hm_ctx *h, const double2 *dV, int nc, int64_t ldv, double tol, int restart, int maxit,
-                       double2 *dI, int64_t ldi, int *iters, double *relres, double2 *bnew, double2 *cvec,
-                       double2 *xt)
-{
-    const int n = h->plan.n, nchunk = (n + DOT_CHUNK - 1) / DOT_CHUNK;
-    cudaStream_t st = h->stream;
-    cudaError_t e = cudaSuccess;
-    double2 *b = nullptr, *xo = nullptr, *r = nullptr, *part = nullptr, *tmp = nullptr;
-    double *nrm = nullptr;
-    int *mask = nullptr;
-    const size_t vec = sizeof(double2) * (size_t)n * nc;
-    if ((e = h->arena.alloc((void **)&b, vec)) || (e = h->arena.alloc((void **)&xo, vec)) ||
-        (e = h->arena.alloc((void **)&r, vec)) || (e = h->arena.alloc((void **)&part, sizeof(double2) * nchunk * nc)) ||
-        (e = h->arena.alloc((void **)&tmp, sizeof(double2) * nc)) || (e = h->arena.alloc((void **)&nrm, sizeof(double) * nc)) ||
-        (e = h->arena.alloc((void **)&mask, sizeof(int) * nc))) {
-        for (void *p : {(void *)b, (void *)xo, (void *)r, (void *)part, (void *)tmp, (void *)nrm, (void *)mask})
-            h->arena.release(p, 0);
-        h->err = "mixed-precision workspace allocation failed";
-        return HM_ENOMEM;
-    }
-    // b: packed copy of V (original order, ld n); xo = 0
-    cudaMemcpy2DAsync(b, sizeof(double2) * n, dV, sizeof(double2) * ldv, sizeof(double2) * n, nc,
-                      cudaMemcpyDeviceToDevice, st);
-    cudaMemsetAsync(xo, 0, vec, st);
-    std::vector<double> bn = col_norms(h, b, nc, part, tmp, nrm);
-    std::vector<int> total(nc, 0), done(nc, 0);
-    std::vector<double> rel(nc, 0.0);
-    int status = HM_OK;
-    const int MAX_OUTER = 40;
-    for (int outer = 0; outer <= MAX_OUTER; ++outer) {
-        // r = b - Z xo in FP64
-        if (outer == 0)
-            cudaMemcpyAsync(r, b, vec, cudaMemcpyDeviceToDevice, st);
-        else {
-            if ((e = z_apply_orig(h, xo, r, nc))) break;
-            HM_LAUNCH(h, K_VEC, k_sub_from<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>((int64_t)n * nc, b, r));
+        if (go.empty()) return cudaSuccess;
+        const int k = (int)go.size();
+        const int *id = upload(go);
+        vec(0, k, ref(fp32 ? R : B, id), ref(B, id), packed(PX));
+        if ((e = to_solve_order(h, PX, n, PY, k)) || (e = op(1, PY, PT, k)) || (e = op(4, PT, PX, k))) return e;
+        vec(0, k, packed(PX), packed(PX), ref(C, id));
+        vec(3, k, packed(PX), packed(PX), ref(XT, id));
+        norms(k, ref(C, id), tmp, id);
+        std::vector<double> cn;
+        if ((e = fetch(tmp, cn))) return e;
+        for (int c : go) {
+            Slot &z = sl[c];
+            z.cn = cn[c];
+            z.it_in = 0;
+            z.first = true;
+            z.conv = false;
+            z.state = RESTART;
         }
-        std::vector<double> rn = col_norms(h, r, nc, part, tmp, nrm);
-        std::vector<int> act(nc, 0);
-        std::vector<double> itol(nc, 0.5);
-        bool any = false;
-        for (int c = 0; c < nc; ++c) {
-            rel[c] = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
-            if (done[c]) continue;
-            if (rel[c] <= tol || bn[c] == 0.0) {
-                done[c] = 1;
+        return cudaSuccess;
+    }
+
+    // true residual c - A x~ at a restart (c itself at the first), stopping test, v_0 = r / beta
+    cudaError_t restart(const std::vector<int> &Rs)
+    {
+        cudaError_t e;
+        std::vector<int> Rn, Rf;
+        for (int c : Rs) {
+            Slot &z = sl[c];
+            if (z.cn == 0.0) {   // zero right-hand side of the inner system
+                z.conv = true;
+                if (!fp32) z.rel = 0.0;
+                z.state = INNER_END;
                 continue;
             }
-            if (total[c] >= maxit || outer == MAX_OUTER) continue;
-            act[c] = 1;
-            any = true;
-            // ask the inner solve for a little more than what is still missing
-            itol[c] = std::min(0.5, std::max(1e-7, 0.3 * tol / rel[c]));
+            (z.first ? Rf : Rn).push_back(c);
         }
-        if (!any) break;
-        int left = maxit;
-        for (int c = 0; c < nc; ++c)
-            if (act[c]) left = std::min(left, maxit - total[c]);
-        cudaMemcpyAsync(mask, act.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st);
-        HM_LAUNCH(h, K_VEC, k_mask_cols<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>(n, nc, mask, r));
-        // inner: c = D^{-1} L^{-1} r (FP32 operators), GMRES on A d~ = c, d = L^{-T} d~
-        if ((e = to_solve_order(h, r, n, bnew, nc)) || (e = op_apply32(h, 1, bnew, xt, nc)) ||
-            (e = op_apply32(h, 4, xt, cvec, nc)))
-            break;
-        cudaMemsetAsync(xt, 0, vec, st);
-        std::vector<int> it(nc, 0);
-        std::vector<double> rr(nc, 0.0);
-        int s = gmres_batch(h, true, cvec, xt, nc, itol, restart, std::max(left, 1), it.data(), rr.data());
-        if (s != HM_OK && s != HM_ENOCONV) {
-            status = s;
-            break;
+        std::vector<int> P(Rn);
+        P.insert(P.end(), Rf.begin(), Rf.end());
+        if (P.empty()) return cudaSuccess;
+        const int k = (int)P.size(), k1 = (int)Rn.size();
+        const int *id = upload(P);
+        if (k1) {
+            vec(0, k1, ref(XT, id), ref(XT, id), packed(PX));
+            if ((e = op(0, PX, PY, k1))) return e;
+            vec(1, k1, ref(C, id), packed(PY), packed(PY));
         }
-        for (int c = 0; c < nc; ++c) total[c] += it[c];
-        if ((e = op_apply32(h, 2, xt, bnew, nc)) || (e = to_orig_order(h, bnew, r, n, nc))) break;
-        HM_LAUNCH(h, K_VEC, k_add_to<<<nblk((int64_t)n * nc, 256), 256, 0, st>>>((int64_t)n * nc, r, xo));
+        if (k > k1) vec(0, k - k1, ref(C, id + k1), ref(C, id + k1), packed(PY, k1));
+        norms(k, packed(PY), s.nrm, id);
+        std::vector<double> beta;
+        if ((e = fetch(s.nrm, beta))) return e;
+        std::vector<int> G, Gp;
+        for (int p = 0; p < k; ++p) {
+            const int c = P[p];
+            Slot &z = sl[c];
+            const double rr = beta[c] / z.cn;
+            if (!fp32) z.rel = rr;
+            if (beta[c] <= z.itol * z.cn) {
+                z.conv = true;
+                z.state = INNER_END;
+            } else if (z.it_in >= z.in_max) {
+                z.state = INNER_END;
+            } else {
+                G.push_back(c);
+                Gp.push_back(p);
+            }
+        }
+        if (G.empty()) return cudaSuccess;
+        const int kg = (int)G.size();
+        const int *gid = upload(G), *gp = upload(Gp);
+        HM_LAUNCH(h, K_VEC,
+                  k_scale<<<nblk((int64_t)n * kg, 256), 256, 0, h->stream>>>(n, kg, s.nrm, gid, ref(PY, gp),
+                                                                              ref(Vb, gid)));
+        HM_LAUNCH(h, K_SMALL, k_cycle_init<<<nblk(kg * (m + 1), 128), 128, 0, h->stream>>>(kg, m, gid, s));
+        for (int c : G) {
+            sl[c].j = 0;
+            sl[c].first = false;
+            sl[c].state = ARNOLDI;
+        }
+        return cudaGetLastError();
     }
-    if (!e && status == HM_OK) {
-        cudaMemcpy2DAsync(dI, sizeof(double2) * ldi, xo, sizeof(double2) * n, sizeof(double2) * n, nc,
-                          cudaMemcpyDeviceToDevice, st);
-        e = cudaStreamSynchronize(st);
+
+    // one Arnoldi step (CGS2) and Givens update for every slot in a cycle
+    cudaError_t arnoldi(const std::vector<int> &Ar)
+    {
+        cudaError_t e;
+        const int k = (int)Ar.size();
+        std::vector<int> Jp(k), vin(k), vout(k);
+        for (int p = 0; p < k; ++p) {
+            const int c = Ar[p], j = sl[c].j;
+            Jp[p] = j + 1;
+            vin[p] = j * S + c;
+            vout[p] = (j + 1) * S + c;
+        }
+        const int *id = upload(Ar), *J = upload(Jp), *vi = upload(vin), *vo = upload(vout);
+        const VRef basis = ref(Vb, id, S), w = packed(PY);
+        cudaStream_t st = h->stream;
+        vec(0, k, ref(Vb, vi), ref(Vb, vi), packed(PX));
+        if ((e = op(0, PX, PY, k))) return e;
+        norms(k, w, s.wn, id);   // ||w|| before orthogonalisation (happy-breakdown reference)
+        // CGS2: h = V^H w, w -= V h, twice; coefficients accumulated in hj
+        HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, k), 256, 0, st>>>(n, basis, J, w, part, nchunk, m + 1));
+        HM_LAUNCH(h, K_SMALL,
+                  k_dots_final<<<nblk(k * (m + 1), 128), 128, 0, st>>>(k, m + 1, J, nchunk, part, s.hj, m + 1, id));
+        HM_LAUNCH(h, K_VEC,
+                  k_axpy_basis<<<nblk((int64_t)n * k, 256), 256, 0, st>>>(n, k, basis, J, s.hj, m + 1, id, w));
+        HM_LAUNCH(h, K_DOTS, k_dots<<<dim3(nchunk, k), 256, 0, st>>>(n, basis, J, w, part, nchunk, m + 1));
+        HM_LAUNCH(h, K_SMALL,
+                  k_dots_final<<<nblk(k * (m + 1), 128), 128, 0, st>>>(k, m + 1, J, nchunk, part, h2, m + 1, id));
+        HM_LAUNCH(h, K_VEC, k_axpy_basis<<<nblk((int64_t)n * k, 256), 256, 0, st>>>(n, k, basis, J, h2, m + 1, id, w));
+        HM_LAUNCH(h, K_SMALL, k_hfold<<<nblk(k * (m + 1), 128), 128, 0, st>>>(k, m + 1, J, id, h2, s.hj, m + 1));
+        // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
+        norms(k, w, s.nrm, id);
+        HM_LAUNCH(h, K_VEC, k_scale<<<nblk((int64_t)n * k, 256), 256, 0, st>>>(n, k, s.nrm, id, w, ref(Vb, vo)));
+        HM_LAUNCH(h, K_SMALL, k_givens<<<nblk(k, 64), 64, 0, st>>>(k, m, id, s));
+        std::vector<double> res(S), wpre(S), wn(S);
+        cudaMemcpyAsync(res.data(), s.res, sizeof(double) * S, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(wpre.data(), s.wn, sizeof(double) * S, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(wn.data(), s.nrm, sizeof(double) * S, cudaMemcpyDeviceToHost, st);
+        if ((e = cudaStreamSynchronize(st))) return e;
+        std::vector<int> F;
+        for (int c : Ar) {
+            Slot &z = sl[c];
+            z.it++;
+            z.it_in++;
+            const bool brk = wn[c] <= 1e-14 * wpre[c];
+            if (!fp32) z.rel = res[c] / z.cn;
+            if (res[c] <= z.itol * z.cn || brk) {
+                z.conv = true;
+                z.state = INNER_END;
+                F.push_back(c);
+            } else if (z.it_in >= z.in_max) {
+                z.state = INNER_END;
+                F.push_back(c);
+            } else if (z.j + 1 == m) {
+                z.state = RESTART;
+                F.push_back(c);
+            } else
+                z.j++;
+        }
+        if (F.empty()) return cudaSuccess;
+        // end of the cycle: x~ += V y
+        const int kf = (int)F.size();
+        const int *fid = upload(F);
+        HM_LAUNCH(h, K_SMALL, k_trisolve<<<nblk(kf, 64), 64, 0, st>>>(kf, m, fid, s));
+        HM_LAUNCH(h, K_VEC,
+                  k_update_x<<<nblk((int64_t)n * kf, 256), 256, 0, st>>>(n, kf, fid, s.J, ref(Vb, fid, S), s.y, m,
+                                                                          ref(XT, fid)));
+        return cudaGetLastError();
     }
-    for (void *p : {(void *)b, (void *)xo, (void *)r, (void *)part, (void *)tmp, (void *)nrm, (void *)mask})
-        h->arena.release(p, 0);
-    if (e) {
-        h->err = std::string("CUDA error in the refinement loop: ") + cudaGetErrorString(e);
+
+    // one tick: every occupied slot advances by one step; slots that finished are appended to fin
+    int tick(std::vector<int> &fin)
+    {
+        cudaError_t e = cudaSuccess;
+        std::vector<int> L;
+        if (!(L = in_state(INNER_END)).empty() && (e = inner_end(L))) return fail(e);
+        if (!(L = in_state(OUTER)).empty() && (e = outer(L))) return fail(e);
+        if (!(L = in_state(RESTART)).empty() && (e = restart(L))) return fail(e);
+        if (!(L = in_state(ARNOLDI)).empty() && (e = arnoldi(L))) return fail(e);
+        // slots that reached INNER_END in this tick with FP64 finish now (no further operator)
+        if (!fp32 && !(L = in_state(INNER_END)).empty() && (e = inner_end(L))) return fail(e);
+        if ((e = cudaStreamSynchronize(h->stream))) return fail(e);
+        int herr = 0;
+        cudaMemcpy(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (herr & ERR_TIMEOUT) {
+            h->err = "device-side wait in a triangular sweep timed out";
+            return HM_ETIMEOUT;
+        }
+        for (int c = 0; c < S; ++c)
+            if (sl[c].state == DONE && !sl[c].reported) {
+                sl[c].reported = true;
+                fin.push_back(c);
+            }
+        return HM_OK;
+    }
+
+    int fail(cudaError_t e)
+    {
+        h->err = std::string("CUDA error in the GMRES engine: ") + cudaGetErrorString(e);
         return HM_ECUDA;
     }
-    if (status != HM_OK) return status;
-    for (int c = 0; c < nc; ++c) {
-        iters[c] = total[c];
-        relres[c] = rel[c];
-        if (!done[c]) status = HM_ENOCONV;
+
+    int active() const
+    {
+        int a = 0;
+        for (const Slot &z : sl) a += (z.state != FREE && z.state != DONE);
+        return a;
     }
-    return status;
-}
+};
 
 int gmres_solve(hm_ctx *h, const double2 *dV, int nrhs, int64_t ldv, double tol, int restart, int maxit, double2 *dI,
                 int64_t ldi, int *iters, double *relres)
 {
-    const int n = h->plan.n;
-    // columns solved in lockstep per batch: the FP32 operator takes 64 per sweep launch
-    const int BATCH = h->opts.precision == 1 ? 64 : 16;
-    cudaStream_t st = h->stream;
-    double2 *bnew = nullptr, *cvec = nullptr, *xt = nullptr;
-    int status = HM_OK;
+    // slots of the engine: the FP32 operator takes 64 columns per sweep launch, the FP64 one 16
+    const int width = h->opts.precision == 1 ? 64 : 16;
+    Engine E;
     cudaError_t e;
-    const int nb = std::min(nrhs, BATCH);
-    if ((e = h->arena.alloc((void **)&bnew, sizeof(double2) * (size_t)n * nb)) ||
-        (e = h->arena.alloc((void **)&cvec, sizeof(double2) * (size_t)n * nb)) ||
-        (e = h->arena.alloc((void **)&xt, sizeof(double2) * (size_t)n * nb))) {
-        h->arena.release(bnew, 0);
-        h->arena.release(cvec, 0);
-        h->err = "solve workspace allocation failed";
-        return HM_ENOMEM;
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    if ((e = E.open(h, std::min(nrhs, width), restart))) {
+        E.close();
+        h->err = std::string("solve workspace: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA;
     }
-    cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
-    for (int c0 = 0; c0 < nrhs; c0 += BATCH) {
-        const int nc = std::min(BATCH, nrhs - c0);
-        int s = (h->opts.precision == 1)
-                    ? solve_mixed(h, dV + c0 * ldv, nc, ldv, tol, restart, maxit, dI + c0 * ldi, ldi, iters + c0,
-                                  relres + c0, bnew, cvec, xt)
-                    : solve_fp64(h, dV + c0 * ldv, nc, ldv, tol, restart, maxit, dI + c0 * ldi, ldi, iters + c0,
-                                 relres + c0, bnew, cvec, xt);
-        if (s == HM_ENOCONV) status = HM_ENOCONV;
-        else if (s != HM_OK) {
+    const int n = h->plan.n;
+    std::vector<int> col(E.S, -1);
+    int next = 0, done = 0, status = HM_OK;
+    while (done < nrhs && status != HM_ECUDA && status != HM_ETIMEOUT) {
+        while (next < nrhs) {
+            const int c = E.submit(dV + (size_t)next * ldv, tol, maxit);
+            if (c == -2) break;
+            if (c < 0) {
+                status = E.fail(cudaGetLastError());
+                break;
+            }
+            col[c] = next++;
+        }
+        if (status == HM_ECUDA) break;
+        std::vector<int> fin;
+        const int s = E.tick(fin);
+        if (s != HM_OK) {
             status = s;
             break;
         }
+        for (int c : fin) {
+            cudaMemcpyAsync(dI + (size_t)col[c] * ldi, E.XO + (size_t)c * n, sizeof(double2) * n,
+                            cudaMemcpyDeviceToDevice, h->stream);
+            iters[col[c]] = E.sl[c].it;
+            relres[col[c]] = E.sl[c].rel;
+            if (E.sl[c].status != HM_OK) status = E.sl[c].status;
+            E.sl[c] = Slot();
+            ++done;
+        }
     }
-    if (status != HM_ECUDA && (e = cudaStreamSynchronize(st))) {
-        status = HM_ECUDA;
-        h->err = cudaGetErrorString(e);
-    }
-    int herr = 0;
-    cudaMemcpy(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if ((status == HM_OK || status == HM_ENOCONV) && (herr & ERR_TIMEOUT)) {
-        h->err = "device-side wait in a triangular sweep timed out";
-        status = HM_ETIMEOUT;
-    }
-    h->arena.release(bnew, 0);
-    h->arena.release(cvec, 0);
-    h->arena.release(xt, 0);
+    if ((e = cudaStreamSynchronize(h->stream)) && status != HM_ECUDA) status = E.fail(e);
+    E.close();
     return status;
 }
 
 }  // namespace hm
+
+// ---- continuous-batching C-ABI ----------------------------------------------------------------
+struct hm_batch_s {
+    hm_ctx *h = nullptr;
+    hm::Engine E;
+};
+
+extern "C" {
+
+int hm_batch_bytes(hm_handle h, int32_t slots, int32_t restart, int64_t *bytes)
+{
+    if (!h || slots < 1 || slots > 1024 || restart < 1 || !bytes) return HM_EINVAL;
+    *bytes = (int64_t)hm::Engine::bytes(h->plan.n ? h->plan.n : h->n, slots, restart);
+    return HM_OK;
+}
+
+int hm_batch_open(hm_handle h, int32_t slots, int32_t restart, hm_batch *out)
+{
+    if (!h || !out || slots < 1 || slots > 1024 || restart < 1) return HM_EINVAL;
+    *out = nullptr;
+    if (!h->setup_done || h->batch_open) {
+        h->err = h->batch_open ? "a batch is already open on this handle" : "batch before precond_setup";
+        return HM_ESTATE;
+    }
+    cudaSetDevice(h->dev);
+    hm_batch b = new hm_batch_s;
+    b->h = h;
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    cudaError_t e = b->E.open(h, slots, restart);
+    if (e) {
+        b->E.close();
+        delete b;
+        h->err = std::string("batch workspace: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA;
+    }
+    h->batch_open = true;
+    *out = b;
+    return HM_OK;
+}
+
+int hm_batch_submit(hm_batch b, const hm_c128 *V, double tol, int32_t maxit, int32_t *slot)
+{
+    if (!b || !V || !slot || maxit < 0 || !(tol >= 0)) return HM_EINVAL;
+    cudaSetDevice(b->h->dev);
+    const int c = b->E.submit((const double2 *)V, tol, maxit);
+    *slot = c;
+    if (c == -2) return HM_EBUSY;
+    if (c < 0) return b->E.fail(cudaGetLastError());
+    return HM_OK;
+}
+
+int hm_batch_step(hm_batch b, int32_t *finished, int32_t *nfinished, int32_t *nactive)
+{
+    if (!b || !finished || !nfinished) return HM_EINVAL;
+    cudaSetDevice(b->h->dev);
+    std::vector<int> fin;
+    const int s = b->E.tick(fin);
+    for (size_t i = 0; i < fin.size(); ++i) finished[i] = fin[i];
+    *nfinished = (int32_t)fin.size();
+    if (nactive) *nactive = b->E.active();
+    return s;
+}
+
+int hm_batch_result(hm_batch b, int32_t slot, hm_c128 *I, int32_t *iters, double *relres)
+{
+    if (!b || slot < 0 || slot >= b->E.S || !I) return HM_EINVAL;
+    hm::Slot &z = b->E.sl[slot];
+    if (z.state != hm::DONE) {
+        b->h->err = "hm_batch_result: the slot holds no finished solve";
+        return HM_ESTATE;
+    }
+    cudaSetDevice(b->h->dev);
+    const int n = b->E.n;
+    cudaError_t e = cudaMemcpyAsync(I, b->E.XO + (size_t)slot * n, sizeof(double2) * n, cudaMemcpyDefault,
+                                    b->h->stream);
+    if (!e) e = cudaStreamSynchronize(b->h->stream);
+    if (e) return b->E.fail(e);
+    if (iters) *iters = z.it;
+    if (relres) *relres = z.rel;
+    const int st = z.status;
+    z = hm::Slot();
+    return st;
+}
+
+int hm_batch_close(hm_batch b)
+{
+    if (!b) return HM_EINVAL;
+    cudaSetDevice(b->h->dev);
+    b->E.close();
+    b->h->batch_open = false;
+    delete b;
+    return HM_OK;
+}
+
+}  // extern "C"

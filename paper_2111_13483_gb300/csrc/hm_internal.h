@@ -148,6 +148,7 @@ struct hm_ctx {
     float2 *d_W32 = nullptr, *d_Ad32 = nullptr, *d_Dinv32 = nullptr, *d_farU32 = nullptr, *d_farV32 = nullptr;
     float2 *d_t32 = nullptr, *d_s32 = nullptr, *d_work32 = nullptr;
     int t32_cols = 0;
+    bool batch_open = false;   // an hm_batch holds this handle
 };
 
 // Launch wrapper: counts every launch by kernel class and, when profiling is on, brackets

@@ -15,8 +15,9 @@ import numpy as np
 from . import build as _build
 
 HM_OK, HM_EINVAL, HM_ENOMEM, HM_ESINGULAR, HM_ENOCONV, HM_ETIMEOUT, HM_ECUDA, HM_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+HM_EBUSY = -8
 _NAMES = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_ESINGULAR", -4: "HM_ENOCONV", -5: "HM_ETIMEOUT",
-          -6: "HM_ECUDA", -7: "HM_ESTATE"}
+          -6: "HM_ECUDA", -7: "HM_ESTATE", -8: "HM_EBUSY"}
 
 OP_A, OP_LINV, OP_LTINV, OP_ZF, OP_DINV, OP_Z = 0, 1, 2, 3, 4, 5
 
@@ -56,7 +57,8 @@ class hm_stats(ctypes.Structure):
 EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_device", "hmat_stats",
            "hm_last_error", "hmat_destroy", "hm_get_order", "hm_get_fill", "hm_get_block", "hm_apply",
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
-           "hm_far_apply_noalloc", "hm_get_fill_ranks"]
+           "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
+           "hm_batch_step", "hm_batch_result", "hm_batch_close"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -101,6 +103,12 @@ def load(build_if_missing=True):
     L.hm_get_profile.argtypes = [vp, ctypes.c_int32, _i64p, _i64p, _f64p]
     L.hm_far_apply_noalloc.argtypes = [vp, vp, vp, ctypes.c_int32]
     L.hm_get_fill_ranks.argtypes = [vp, _i32p]
+    L.hm_batch_bytes.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, _i64p]
+    L.hm_batch_open.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)]
+    L.hm_batch_submit.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int32, _i32p]
+    L.hm_batch_step.argtypes = [vp, _i32p, _i32p, _i32p]
+    L.hm_batch_result.argtypes = [vp, ctypes.c_int32, vp, _i32p, _f64p]
+    L.hm_batch_close.argtypes = [vp]
     _lib = L
     return L
 
@@ -308,3 +316,70 @@ def hm_get_fill_ranks(h):
     out = np.zeros(max(1, len(idx)), dtype=np.int32)
     h.check(load().hm_get_fill_ranks(h.ptr, _p(out, _i32p)), "hm_get_fill_ranks")
     return out[:len(idx)]
+
+
+class Batch:
+    """Continuous-batching slot engine over one handle (hm_batch_* in the header).
+
+    ``submit(V)`` places a right-hand side (complex128 (n,), original order; numpy or a torch
+    CUDA tensor) in a free slot and returns the slot (None when all are occupied);
+    ``step()`` advances every occupied slot by one GMRES step and returns the slots that
+    finished; ``result(slot)`` returns (I, iters, relres, status) and frees the slot."""
+
+    def __init__(self, h, slots, restart=30):
+        self.h, self.slots, self.restart = h, slots, restart
+        p = ctypes.c_void_p()
+        h.check(load().hm_batch_open(h.ptr, slots, restart, ctypes.byref(p)), "hm_batch_open")
+        self.ptr = p
+        self._fin = np.zeros(slots, dtype=np.int32)
+        self._keep = {}
+
+    @staticmethod
+    def bytes(h, slots, restart=30):
+        b = ctypes.c_int64()
+        h.check(load().hm_batch_bytes(h.ptr, slots, restart, ctypes.byref(b)), "hm_batch_bytes")
+        return b.value
+
+    def submit(self, V, tol=1e-4, maxit=5000):
+        if hasattr(V, "data_ptr"):
+            ptr, keep = V.data_ptr(), V
+        else:
+            keep = np.ascontiguousarray(V, dtype=np.complex128)
+            ptr = keep.ctypes.data
+        slot = ctypes.c_int32()
+        code = load().hm_batch_submit(self.ptr, ptr, tol, maxit, ctypes.byref(slot))
+        if code == HM_EBUSY:
+            return None
+        self.h.check(code, "hm_batch_submit")
+        return slot.value
+
+    def step(self):
+        nf, na = ctypes.c_int32(), ctypes.c_int32()
+        self.h.check(load().hm_batch_step(self.ptr, _p(self._fin, _i32p), ctypes.byref(nf), ctypes.byref(na)),
+                     "hm_batch_step")
+        self.active = na.value
+        return self._fin[:nf.value].tolist()
+
+    def result(self, slot, out=None):
+        """out: optional torch CUDA complex128 tensor (n,) to receive I on the device."""
+        it, rr = ctypes.c_int32(), ctypes.c_double()
+        if out is not None:
+            code = load().hm_batch_result(self.ptr, slot, out.data_ptr(), ctypes.byref(it), ctypes.byref(rr))
+            I = out
+        else:
+            I = np.zeros(self.h.n, dtype=np.complex128)
+            code = load().hm_batch_result(self.ptr, slot, I.ctypes.data, ctypes.byref(it), ctypes.byref(rr))
+        if code not in (HM_OK, HM_ENOCONV):
+            self.h.check(code, "hm_batch_result")
+        return I, it.value, rr.value, code
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().hm_batch_close(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
