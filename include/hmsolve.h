@@ -194,7 +194,9 @@ int hm_get_fill_ranks(hm_handle h, int32_t *rank);
  *   op 2: y = L^{-T} x     (Eq. 24, the right scalings);
  *   op 3: y = Z_F x        (far field, Eq. 11);
  *   op 4: y = D^{-1} x     (Eq. 28 preconditioner solve);
- *   op 5: y = Z x          (near + far, ORIGINAL order; the refinement residual operator).
+ *   op 5: y = Z x          (near + far, ORIGINAL order; the refinement residual operator);
+ *   ops 8-12: ops 0-4 with the complex-FP32 factors and arithmetic of the mixed-precision
+ *       inner solve (x and y stay complex FP64); precision 1 handles only (else HM_ESTATE).
  * x and y must not overlap.
  */
 int hm_apply(hm_handle h, int32_t op, const void *dx, void *dy, int32_t nrhs);

@@ -194,6 +194,10 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
         (e = upload(h, &h->d_far_c1, h->far_c1)) || (e = upload(h, &h->d_far_rank, h->far_rank)) ||
         (e = upload(h, &h->d_far_uoff, h->far_uoff)) || (e = upload(h, &h->d_far_voff, h->far_voff)) ||
         (e = upload(h, &h->d_far_toff, F.toff)) || (e = upload(h, &h->d_far_item, F.item_blk)) ||
+        (e = upload(h, &h->d_p1_lo, F.p1_lo)) || (e = upload(h, &h->d_p1_hi, F.p1_hi)) ||
+        (e = upload(h, &h->d_p1_ptr, F.p1_ptr)) || (e = upload(h, &h->d_p1_off, F.p1_off)) ||
+        (e = upload(h, &h->d_p1_ld, F.p1_ld)) || (e = upload(h, &h->d_p1_rank, F.p1_rank)) ||
+        (e = upload(h, &h->d_p1_row, F.p1_row)) || (e = upload(h, &h->d_p1_isv, F.p1_isv)) ||
         (e = upload(h, &h->d_flptr, F.lptr)) ||
         (e = upload(h, &h->d_flent, F.lent)) || (e = upload(h, &h->d_nptr, F.nptr)) ||
         (e = upload(h, &h->d_nent, F.nent)) || (e = upload(h, &h->d_leaf_ptr, h->leaf_ptr)) ||
@@ -458,14 +462,19 @@ int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, 
 
 int hm_apply(hm_handle h, int32_t op, const void *dx, void *dy, int32_t nrhs)
 {
-    if (!h || !dx || !dy || nrhs < 1 || op < 0 || op > 5) return HM_EINVAL;
+    if (!h || !dx || !dy || nrhs < 1 || op < 0 || op > 12 || (op > 5 && op < 8)) return HM_EINVAL;
     if (op != 3 && op != 5 && !h->setup_done) {
         h->err = "hm_apply: operator needs precond_setup";
+        return HM_ESTATE;
+    }
+    if (op >= 8 && h->opts.precision != 1) {
+        h->err = "hm_apply: the complex-FP32 operators exist for precision 1 handles only";
         return HM_ESTATE;
     }
     cudaSetDevice(h->dev);
     cudaError_t e;
     if (op == 5) e = hm::z_apply_orig(h, (const double2 *)dx, (double2 *)dy, nrhs);
+    else if (op >= 8) e = hm::op_apply32(h, op - 8, (const double2 *)dx, (double2 *)dy, nrhs);
     else e = op_apply(h, op, (const double2 *)dx, (double2 *)dy, nrhs);
     if (!e) e = cudaStreamSynchronize(h->stream);
     if (e) return cuda_fail(h, e, "hm_apply");

@@ -2,178 +2,252 @@
 //
 // Z_F is stored once per admissible pair (rows r-range, columns c-range, r before c): a
 // low-rank block U V^T or a dense block B; the mirrored block is its transpose.  u is given
-// in cluster order; v is written in solve order.
+// in cluster order with the right-hand sides interleaved (u[i * nrhs + r]); v is written
+// in solve order, column-major.
 //
-// Phase 1 (k_far_rank): one warp per (low-rank block b, rank column l) computes
-//     t_b[l] = V_b[:, l]^T u[c-range],  s_b[l] = U_b[:, l]^T u[r-range]
-// for a group of right-hand sides, loading each factor entry once per group.
-// Phase 2 (k_far_gather): one CTA per leaf; its eight warps take the leaf's list of covering
-// far blocks round robin (low-rank row side U_b t_b, column side V_b s_b, dense row side
-// B u, dense column side B^T u), each warp accumulating partial sums for the leaf's rows,
-// which are then added in warp order.  The arithmetic order is fixed, so results are
-// deterministic and do not depend on how many right-hand sides share the launch.
+// Phase 1 (k_far_t): the rank vectors t_b = V_b^T u[c-range] and s_b = U_b^T u[r-range].
+// Factor columns that contract over the same index range are stacked (up to 64 per task),
+// so one CTA stages each 64-row piece of u once for all of them and runs a register-tiled
+// product (tile.cuh); t and s are stored interleaved like u.
+// Phase 2 (k_far_y): one CTA per leaf accumulates, in the order of the leaf's list of
+// covering far blocks, U_b t_b (row side), V_b s_b (column side), B u (dense row side) and
+// B^T u (dense column side) for the leaf's rows; the list is cut into contraction segments
+// of at most 64 that are staged in shared memory in chunks.  Every output sums its terms in
+// one fixed order, so results are deterministic and do not depend on how many right-hand
+// sides share the launch.
 #include "cplx.cuh"
 #include "hm_internal.h"
+#include "tile.cuh"
 
 namespace hm {
 
-constexpr int FAR_RB = 8;    // right-hand sides per register group
-constexpr int FAR_G = 8;     // warps (incidence groups) per leaf CTA
+namespace {
+constexpr int SEG = 64;   // longest staged contraction segment
+}
 
-template <class T>
-__global__ void __launch_bounds__(256) k_far_rank(int64_t tlen, const int *item_blk, const int64_t *toff,
-                                                  const int *r0, const int *r1, const int *c0, const int *c1,
-                                                  const int64_t *uoff, const int64_t *voff, const T *U, const T *V,
-                                                  const T *u, int n, int nrhs, T *t, T *s)
+template <class T, int TR, int TC, int NT>
+__global__ void __launch_bounds__(256) k_far_t(const int *task_lo, const int *task_hi, const int *task_ptr,
+                                               const int64_t *item_off, const int *item_ld, const int *item_rank,
+                                               const int *item_row, const int *item_isv, const T *U, const T *V,
+                                               const T *u, int nrhs, T *t, T *s)
 {
-    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (item >= tlen) return;
-    const int b = item_blk[item];
-    const int l = (int)(item - toff[b]);
-    const int m = r1[b] - r0[b], nc = c1[b] - c0[b];
-    const T *Vl = V + voff[b] + (int64_t)l * nc;
-    const T *Ul = U + uoff[b] + (int64_t)l * m;
-    for (int rb = 0; rb < nrhs; rb += FAR_RB) {
-        const int nr = min(FAR_RB, nrhs - rb);
-        const T *uc = u + c0[b] + (int64_t)rb * n, *ur = u + r0[b] + (int64_t)rb * n;
-        T a1[FAR_RB], a2[FAR_RB];
-#pragma unroll
-        for (int q = 0; q < FAR_RB; ++q) a1[q] = a2[q] = czero(T());
-        for (int i = lane; i < nc; i += 32) {
-            const T v = Vl[i];
-#pragma unroll
-            for (int q = 0; q < FAR_RB; ++q)
-                if (q < nr) a1[q] = cfma(v, uc[i + (int64_t)q * n], a1[q]);
-        }
-        for (int i = lane; i < m; i += 32) {
-            const T v = Ul[i];
-#pragma unroll
-            for (int q = 0; q < FAR_RB; ++q)
-                if (q < nr) a2[q] = cfma(v, ur[i + (int64_t)q * n], a2[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < FAR_RB; ++q) {
-            if (q >= nr) break;
-            T x1 = a1[q], x2 = a2[q];
-            for (int w = 16; w > 0; w >>= 1) {
-                x1.x += __shfl_xor_sync(0xffffffffu, x1.x, w);
-                x1.y += __shfl_xor_sync(0xffffffffu, x1.y, w);
-                x2.x += __shfl_xor_sync(0xffffffffu, x2.x, w);
-                x2.y += __shfl_xor_sync(0xffffffffu, x2.y, w);
+    extern __shared__ unsigned char smraw[];
+    T *buf = (T *)smraw;
+    __shared__ int s_item[64], s_l[64];
+    __shared__ int s_R;
+    const int task = blockIdx.x;
+    const int lo = task_lo[task], hi = task_hi[task], i0 = task_ptr[task], i1 = task_ptr[task + 1];
+    if (threadIdx.x == 0) {
+        int R = 0;
+        for (int it = i0; it < i1; ++it)
+            for (int l = 0; l < item_rank[it] && R < 64; ++l, ++R) {
+                s_item[R] = it;
+                s_l[R] = l;
             }
-            if (lane == 0) {
-                t[item + (int64_t)(rb + q) * tlen] = x1;
-                s[item + (int64_t)(rb + q) * tlen] = x2;
-            }
+        s_R = R;
+    }
+    __syncthreads();
+    const int R = s_R;
+    const int nrt = (R + TR - 1) / TR, ntiles = nrt * ((nrhs + TC - 1) / TC);
+    const int ldw = stage_ldw(R, TR), ldr = stage_ldr(nrhs, TC);
+    Tile<T, TR, TC, NT> acc;
+    tile_load(acc, (const T *)nullptr, 0, 0, R, nrhs, nrt, ntiles);
+    for (int c0 = lo; c0 < hi; c0 += SEG) {
+        const int ch = min(SEG, hi - c0);
+        T *Ws = buf, *Ys = buf + ch * ldw;
+        for (int e = threadIdx.x; e < ch * R; e += blockDim.x) {
+            const int qq = e % ch, rr = e / ch, it = s_item[rr];
+            const T *F = (item_isv[it] ? V : U) + item_off[it] + (int64_t)s_l[rr] * item_ld[it];
+            Ws[qq * ldw + rr] = F[c0 - lo + qq];
         }
+        const T *uc = u + (int64_t)c0 * nrhs;
+        for (int e = threadIdx.x; e < ch * nrhs; e += blockDim.x) {
+            const int qq = e / nrhs, r = e % nrhs;
+            Ys[qq * ldr + r] = uc[e];
+        }
+        __syncthreads();
+        tile_mac<false>(acc, Ws, ldw, Ys, ldr, 1, ch, nrt, ntiles);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt) {
+        const int tile = threadIdx.x + tt * blockDim.x;
+        const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int c = 0; c < TC; ++c)
+                if (tile < ntiles && row0 + a < R && r0 + c < nrhs) {
+                    const int it = s_item[row0 + a];
+                    T *dst = item_isv[it] ? t : s;
+                    dst[(int64_t)(item_row[it] + s_l[row0 + a]) * nrhs + r0 + c] = acc.v[tt][a][c];
+                }
     }
 }
 
+// Contraction source of one incidence entry of leaf rows [a, a + ni): coefficient
+// F(i, k) = Fb[i * fi + k * fk] and vector Y(k, r) = Yb[k * nrhs + r], k < K.
+template <class T> struct FarSeg {
+    const T *Fb, *Yb;
+    int64_t fi, fk;
+    int K;
+};
+
 template <class T>
-__global__ void __launch_bounds__(256) k_far_gather(int nl, const int *leaf_ptr, const int *lptr, const int *lent,
-                                                    const int *r0, const int *r1, const int *c0, const int *c1,
-                                                    const int *rank, const int64_t *uoff, const int64_t *voff,
-                                                    const int64_t *toff, const T *U, const T *V, const T *t,
-                                                    const T *s, const T *u, const int *cl2new, int n, int nrhs, T *y,
-                                                    int64_t tlen)
+__device__ __forceinline__ FarSeg<T> far_seg(int ent, int a, const int *r0, const int *r1, const int *c0,
+                                             const int *c1, const int *rank, const int64_t *uoff,
+                                             const int64_t *voff, const int64_t *toff, const T *U, const T *V,
+                                             const T *t, const T *s, const T *u, int nrhs)
+{
+    const int b = ent >> 2, kind = ent & 3;
+    const int m = r1[b] - r0[b], nc = c1[b] - c0[b];
+    FarSeg<T> g;
+    if (kind == 0) {          // low rank, leaf in the row range: U_b t_b
+        g.Fb = U + uoff[b] + (a - r0[b]);
+        g.fi = 1;
+        g.fk = m;
+        g.Yb = t + toff[b] * nrhs;
+        g.K = rank[b];
+    } else if (kind == 1) {   // low rank, leaf in the column range: V_b s_b
+        g.Fb = V + voff[b] + (a - c0[b]);
+        g.fi = 1;
+        g.fk = nc;
+        g.Yb = s + toff[b] * nrhs;
+        g.K = rank[b];
+    } else if (kind == 2) {   // dense, row side: B u[c-range]
+        g.Fb = U + uoff[b] + (a - r0[b]);
+        g.fi = 1;
+        g.fk = m;
+        g.Yb = u + (int64_t)c0[b] * nrhs;
+        g.K = nc;
+    } else {                  // dense, column side: B^T u[r-range]
+        g.Fb = U + uoff[b] + (int64_t)(a - c0[b]) * m;
+        g.fi = m;
+        g.fk = 1;
+        g.Yb = u + (int64_t)r0[b] * nrhs;
+        g.K = m;
+    }
+    return g;
+}
+
+template <class T, int TR, int TC, int NT>
+__global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, const int *lptr, const int *lent,
+                                               const int *r0, const int *r1, const int *c0, const int *c1,
+                                               const int *rank, const int64_t *uoff, const int64_t *voff,
+                                               const int64_t *toff, const T *U, const T *V, const T *t,
+                                               const T *s, const T *u, const int *cl2new, int n, int nrhs, T *y,
+                                               int budget)
 {
     extern __shared__ unsigned char smraw[];
-    T *part = (T *)smraw;                       // [FAR_G][64][FAR_RB]
+    T *buf = (T *)smraw;
     const int l = blockIdx.x;
     if (l >= nl) return;
     const int a = leaf_ptr[l], ni = leaf_ptr[l + 1] - a;
-    const int on = cl2new[a];
-    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p0 = lptr[l], p1 = lptr[l + 1];
-    for (int rb = 0; rb < nrhs; rb += FAR_RB) {
-        const int nr = min(FAR_RB, nrhs - rb);
-        for (int i0 = 0; i0 < ni; i0 += 32) {
-            const int i = i0 + lane;
-            const bool act = i < ni;
-            T acc[FAR_RB];
-#pragma unroll
-            for (int q = 0; q < FAR_RB; ++q) acc[q] = czero(T());
-            for (int p = p0 + g; p < p1; p += FAR_G) {
-                const int ent = lent[p], b = ent >> 2, kind = ent & 3;
-                const int m = r1[b] - r0[b], nc = c1[b] - c0[b];
-                if (!act) continue;
-                if (kind <= 1) {
-                    const int rk = rank[b];
-                    const int ld = kind == 0 ? m : nc;
-                    const T *F = (kind == 0 ? U + uoff[b] + (a - r0[b]) : V + voff[b] + (a - c0[b])) + i;
-                    const T *tb = (kind == 0 ? t : s) + toff[b] + (int64_t)rb * tlen;
-                    for (int k = 0; k < rk; ++k) {
-                        const T f = F[(int64_t)k * ld];
-#pragma unroll
-                        for (int q = 0; q < FAR_RB; ++q)
-                            if (q < nr) acc[q] = cfma(f, tb[k + (int64_t)q * tlen], acc[q]);
-                    }
-                } else if (kind == 2) {
-                    const T *B = U + uoff[b] + (a - r0[b]) + i;
-                    const T *uc = u + c0[b] + (int64_t)rb * n;
-                    for (int k = 0; k < nc; ++k) {
-                        const T f = B[(int64_t)k * m];
-#pragma unroll
-                        for (int q = 0; q < FAR_RB; ++q)
-                            if (q < nr) acc[q] = cfma(f, uc[k + (int64_t)q * n], acc[q]);
-                    }
-                } else {
-                    const T *B = U + uoff[b] + (int64_t)((a - c0[b]) + i) * m;
-                    const T *ur = u + r0[b] + (int64_t)rb * n;
-                    for (int k = 0; k < m; ++k) {
-                        const T f = B[k];
-#pragma unroll
-                        for (int q = 0; q < FAR_RB; ++q)
-                            if (q < nr) acc[q] = cfma(f, ur[k + (int64_t)q * n], acc[q]);
-                    }
+    const int nrt = (ni + TR - 1) / TR, ntiles = nrt * ((nrhs + TC - 1) / TC);
+    const int ldw = stage_ldw(ni, TR), ldr = stage_ldr(nrhs, TC);
+    Tile<T, TR, TC, NT> acc;
+    tile_load(acc, (const T *)nullptr, 0, 0, ni, nrhs, nrt, ntiles);
+    const int p1 = lptr[l + 1];
+    int p = lptr[l], k0 = 0;
+    while (p < p1) {
+        // one chunk: segments (entry, [k0, k0 + len)) while they fit the budget
+        int used = 0, pp = p, kk = k0;
+        for (int nseg = 0; pp < p1 && nseg < 32;) {
+            const FarSeg<T> g = far_seg(lent[pp], a, r0, r1, c0, c1, rank, uoff, voff, toff, U, V, t, s, u, nrhs);
+            if (kk >= g.K) {   // entry done (or empty)
+                ++pp;
+                kk = 0;
+                continue;
+            }
+            const int len = min(SEG, g.K - kk);
+            const int need = stage_need(ni, len, nrhs, TR, TC);
+            if (nseg > 0 && used + need > budget) break;
+            T *Ws = buf + used, *Ys = Ws + len * ldw;
+            if (g.fi == 1)
+                for (int e = threadIdx.x; e < len * ni; e += blockDim.x) {
+                    const int i = e % ni, q = e / ni;
+                    Ws[q * ldw + i] = g.Fb[i + (int64_t)(kk + q) * g.fk];
                 }
+            else
+                for (int e = threadIdx.x; e < len * ni; e += blockDim.x) {
+                    const int q = e % len, i = e / len;
+                    Ws[q * ldw + i] = g.Fb[(int64_t)i * g.fi + kk + q];
+                }
+            const T *yb = g.Yb + (int64_t)kk * nrhs;
+            for (int e = threadIdx.x; e < len * nrhs; e += blockDim.x) {
+                const int q = e / nrhs, r = e % nrhs;
+                Ys[q * ldr + r] = yb[e];
             }
-            if (act) {
-#pragma unroll
-                for (int q = 0; q < FAR_RB; ++q) part[(g * 64 + i) * FAR_RB + q] = acc[q];
-            }
+            used += need;
+            ++nseg;
+            kk += len;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < ni * nr; e += blockDim.x) {
-            const int i = e % ni, q = e / ni;
-            T v = part[i * FAR_RB + q];
-            for (int gg = 1; gg < FAR_G; ++gg) {
-                const T w = part[(gg * 64 + i) * FAR_RB + q];
-                v.x += w.x;
-                v.y += w.y;
+        // replay the chunk's segments in order
+        int off = 0;
+        while (p != pp || k0 != kk) {
+            const FarSeg<T> g = far_seg(lent[p], a, r0, r1, c0, c1, rank, uoff, voff, toff, U, V, t, s, u, nrhs);
+            if (k0 >= g.K) {
+                ++p;
+                k0 = 0;
+                continue;
             }
-            y[on + i + (int64_t)(rb + q) * n] = v;
+            const int len = min(SEG, g.K - k0);
+            tile_mac<false>(acc, buf + off, ldw, buf + off + len * ldw, ldr, 1, len, nrt, ntiles);
+            off += stage_need(ni, len, nrhs, TR, TC);
+            k0 += len;
         }
         __syncthreads();
     }
+    tile_store(acc, y + cl2new[a], 1, n, ni, nrhs, nrt, ntiles);
 }
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+namespace {
+template <class T> struct FarLaunch {
+    hm_ctx *h;
+    const T *U, *V;
+    T *t, *s;
+    const T *ucl;
+    T *y;
+    int nrhs;
+    template <int TR, int TC, int NT> cudaError_t run(int maxw)
+    {
+        const FarPlan &F = h->fplan;
+        const int n = h->plan.n;
+        const int budget = stage_need(64, SEG, nrhs, TR, TC);
+        const size_t smem = sizeof(T) * (size_t)budget;
+        static bool attr = false;   // one per instantiation
+        if (!attr) {
+            const int smax = (int)(sizeof(T) * (size_t)stage_need(64, SEG, maxw, TR, TC));
+            cudaError_t e;
+            if ((e = cudaFuncSetAttribute(k_far_t<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)) ||
+                (e = cudaFuncSetAttribute(k_far_y<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)))
+                return e;
+            attr = true;
+        }
+        const int ntask = (int)F.p1_lo.size();
+        if (ntask > 0)
+            HM_LAUNCH(h, K_FAR1,
+                      (k_far_t<T, TR, TC, NT><<<ntask, 256, smem, h->stream>>>(
+                          h->d_p1_lo, h->d_p1_hi, h->d_p1_ptr, h->d_p1_off, h->d_p1_ld, h->d_p1_rank, h->d_p1_row,
+                          h->d_p1_isv, U, V, ucl, nrhs, t, s)));
+        HM_LAUNCH(h, K_FAR2,
+                  (k_far_y<T, TR, TC, NT><<<h->nl, 256, smem, h->stream>>>(
+                      h->nl, h->d_leaf_ptr, h->d_flptr, h->d_flent, h->d_far_r0, h->d_far_r1, h->d_far_c0,
+                      h->d_far_c1, h->d_far_rank, h->d_far_uoff, h->d_far_voff, h->d_far_toff, U, V, t, s, ucl,
+                      h->d_cl2new, n, nrhs, y, budget)));
+        return cudaGetLastError();
+    }
+};
+}  // namespace
+
 template <class T>
 cudaError_t far_product(hm_ctx *h, const T *U, const T *V, T *t, T *s, const T *ucl, T *y, int nrhs)
 {
-    const FarPlan &F = h->fplan;
-    const int n = h->plan.n;
-    const int smem = (int)(sizeof(T) * FAR_G * 64 * FAR_RB);
-    static bool attr = false;   // one per instantiation
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_far_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e) return e;
-        attr = true;
-    }
-    if (F.nf > 0 && F.tlen > 0)
-        HM_LAUNCH(h, K_FAR1,
-                  k_far_rank<T><<<nblk(F.tlen * 32, 256), 256, 0, h->stream>>>(
-                      F.tlen, h->d_far_item, h->d_far_toff, h->d_far_r0, h->d_far_r1, h->d_far_c0, h->d_far_c1,
-                      h->d_far_uoff, h->d_far_voff, U, V, ucl, n, nrhs, t, s));
-    HM_LAUNCH(h, K_FAR2,
-              k_far_gather<T><<<h->nl, 32 * FAR_G, sizeof(T) * FAR_G * 64 * FAR_RB, h->stream>>>(
-                  h->nl, h->d_leaf_ptr, h->d_flptr, h->d_flent, h->d_far_r0, h->d_far_r1, h->d_far_c0, h->d_far_c1,
-                  h->d_far_rank, h->d_far_uoff, h->d_far_voff, h->d_far_toff, U, V, t, s, ucl, h->d_cl2new, n, nrhs,
-                  y, F.tlen));
-    return cudaGetLastError();
+    FarLaunch<T> f{h, U, V, t, s, ucl, y, nrhs};
+    return tile_dispatch<T>(nrhs, f);
 }
 
 template cudaError_t far_product<double2>(hm_ctx *, const double2 *, const double2 *, double2 *, double2 *,

@@ -86,6 +86,11 @@ struct FarPlan {
     int64_t tlen = 0;                 // sum of ranks
     std::vector<int64_t> toff;        // per block: offset of its rank vectors
     std::vector<int> item_blk;        // rank item e (toff[b] <= e < toff[b+1]) -> block b
+    // rank-vector tasks: factor columns contracting over one index range [p1_lo, p1_hi),
+    // at most 64 per task; items p1_ptr[t]..p1_ptr[t+1]: factor V (isv) or U at p1_off with
+    // column stride p1_ld, p1_rank columns, output rows p1_row.. of t (isv) or s
+    std::vector<int> p1_lo, p1_hi, p1_ptr, p1_ld, p1_rank, p1_row, p1_isv;
+    std::vector<int64_t> p1_off;
     // near-field incidence lists (cluster order) for Z_N products: per leaf l, entries
     // (b << 1 | side), side 0 = l is the row leaf t, 1 = l is the column leaf s (t != s)
     std::vector<int> nptr, nent;
@@ -121,6 +126,9 @@ struct hm_ctx {
     int *d_far_r0 = nullptr, *d_far_r1 = nullptr, *d_far_c0 = nullptr, *d_far_c1 = nullptr, *d_far_rank = nullptr;
     int64_t *d_far_uoff = nullptr, *d_far_voff = nullptr, *d_far_toff = nullptr;
     int *d_flptr = nullptr, *d_flent = nullptr, *d_nptr = nullptr, *d_nent = nullptr, *d_far_item = nullptr;
+    int *d_p1_lo = nullptr, *d_p1_hi = nullptr, *d_p1_ptr = nullptr, *d_p1_ld = nullptr, *d_p1_rank = nullptr,
+        *d_p1_row = nullptr, *d_p1_isv = nullptr;
+    int64_t *d_p1_off = nullptr;
     int *d_leaf_ptr = nullptr, *d_perm = nullptr;
     int *d_new2cl = nullptr, *d_cl2new = nullptr, *d_new2orig = nullptr, *d_pos = nullptr;
     // device: plan

@@ -21,6 +21,7 @@
 
 #include "cplx.cuh"
 #include "hm_internal.h"
+#include "tile.cuh"
 
 namespace hm {
 
@@ -57,33 +58,23 @@ __device__ bool wait_ready(const int *flags, int k, int epoch, int *err)
     return true;
 }
 
-__device__ __forceinline__ void publish(int *flags, int i, int epoch)
-{
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) atomicExch(flags + i, epoch);
-}
 
 // Dependencies finishing last (the final TAIL entries of a list) are taken one per chunk,
 // so that the chain's critical path never carries more than one block product.
 constexpr int TAIL = 4;
-// Threads that share one output in a single-block chunk (the inner sum split in SPLIT
-// contiguous parts, added in a fixed order).
-constexpr int SPLIT = 4;
 
 // Next chunk [p, q) of a dependency list walked from p towards pend (step +1 or -1): blocks
-// are added while their staged entries (coefficient block + vector block) fit the budget;
-// each of the last TAIL dependencies forms a chunk of its own.
-__device__ __forceinline__ int next_chunk(int p, int pend, int step, const int *dep, const int *size, int nrow,
+// are added while their staged entries fit the budget; each of the last TAIL dependencies
+// forms a chunk of its own.
+template <int TR, int TC>
+__device__ __forceinline__ int next_chunk(int p, int pend, int step, const int *dep, const int *size, int no,
                                           int nrhs, int budget)
 {
     const int tail0 = pend - TAIL * step;   // first position of the tail
     if ((step > 0 && p >= tail0) || (step < 0 && p <= tail0)) return p + step;
-    const int last = tail0;
     int q = p, used = 0, cnt = 0;
-    while (q != last && cnt < 16) {
-        const int nk = size[dep[q]];
-        const int need = nk * nrow + nk * nrhs;
+    while (q != tail0 && cnt < 16) {
+        const int need = stage_need(no, size[dep[q]], nrhs, TR, TC);
         if (cnt > 0 && used + need > budget) break;
         used += need;
         ++cnt;
@@ -92,188 +83,121 @@ __device__ __forceinline__ int next_chunk(int p, int pend, int step, const int *
     return q;
 }
 
-// acc[row + r*nrow] -= sum_q w[q*ldw + row] * y[q + r*len] for one staged block, every output
-// shared by SPLIT consecutive lanes that each sum a contiguous part of q; the parts are
-// combined as (p0 + p1) + (p2 + p3).  blockDim.x must be a multiple of 32.
-template <class T>
-__device__ __forceinline__ void single_block(T *acc, const T *w, int ldw, const T *y, int len, int nrow, int nrhs)
+// One block row of a sweep (Eqs. 23, 24): out = x_o - sum over the dependency list of
+// M_b y_b, with M_b = W_ko^T (forward, W_ko at Wsrc, nc x no column-major) or W_oj
+// (backward, no x nc column-major).  The CTA stages each chunk's coefficient blocks before
+// waiting on the chunk's ready flags, then the vector blocks, then runs the tile products.
+template <class T, int TR, int TC, int NT, bool FWD>
+__device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, const int *boff, const int *lptr,
+                                          const int *lidx, const int *lcol, const int64_t *coff, const T *W,
+                                          const T *x, T *y, int n, int nrhs, int budget, int *flags, int epoch,
+                                          int *err, T *buf)
 {
-    const int total = nrow * nrhs * SPLIT;
-    for (int base = 0; base < total; base += blockDim.x) {
-        const int e2 = base + threadIdx.x;
-        const bool act = e2 < total;
-        const int e = e2 / SPLIT, part = e2 % SPLIT;
-        T v = czero(T());
-        if (act) {
-            const int row = e % nrow, r = e / nrow;
-            const int q0 = part * len / SPLIT, q1 = (part + 1) * len / SPLIT;
-            const T *wr = w + row, *yr = y + r * len;
-            for (int q = q0; q < q1; ++q) v = cfma(wr[q * ldw], yr[q], v);
+    const int o = boff[o_blk];
+    const int nrt = (no + TR - 1) / TR, ntiles = nrt * ((nrhs + TC - 1) / TC);
+    const int ldw = stage_ldw(no, TR);
+    Tile<T, TR, TC, NT> acc;
+    tile_load(acc, x + o, 1, n, no, nrhs, nrt, ntiles);
+    // forward: list ascending over [lptr[o], lptr[o+1]); backward: descending
+    const int pa = FWD ? lptr[o_blk] : lptr[o_blk + 1] - 1, pend = FWD ? lptr[o_blk + 1] : lptr[o_blk] - 1;
+    const int step = FWD ? 1 : -1;
+    for (int p = pa; p != pend;) {
+        const int q = next_chunk<TR, TC>(p, pend, step, lidx, size, no, nrhs, budget);
+        // stage the coefficient blocks (static data) before waiting
+        int off = 0;
+        for (int b = p; b != q; b += step) {
+            const int k = lidx[b], nc = size[k];
+            T *Ws = buf + off;
+            if (FWD) {   // W_ko: nc x no at coff[k] + lcol*nc; M(row, qq) = W_ko(qq, row)
+                const T *src = W + coff[k] + (int64_t)lcol[b] * nc;
+                for (int e = threadIdx.x; e < nc * no; e += blockDim.x) {
+                    const int qq = e % nc, row = e / nc;
+                    Ws[qq * ldw + row] = src[e];
+                }
+            } else {     // W_oj: no x nc at coff[o] + lcol*no; M(row, qq) = W_oj(row, qq)
+                const T *src = W + coff[o_blk] + (int64_t)lcol[b] * no;
+                for (int e = threadIdx.x; e < nc * no; e += blockDim.x) {
+                    const int row = e % no, qq = e / no;
+                    Ws[qq * ldw + row] = src[e];
+                }
+            }
+            off += stage_need(no, nc, nrhs, TR, TC);
         }
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
-        if (act && part == 0) {
-            acc[e].x -= v.x;
-            acc[e].y -= v.y;
+        if (threadIdx.x == 0)
+            for (int b = p; b != q; b += step) wait_ready(flags, lidx[b], epoch, err);
+        __syncthreads();
+        off = 0;
+        for (int b = p; b != q; b += step) {
+            const int k = lidx[b], nc = size[k], ok = boff[k];
+            T *Ys = buf + off + nc * ldw;
+            for (int e = threadIdx.x; e < nc * nrhs; e += blockDim.x) {
+                const int qq = e % nc, r = e / nc;
+                Ys[r * nc + qq] = ldcg(y + ok + qq + (int64_t)r * n);
+            }
+            off += stage_need(no, nc, nrhs, TR, TC);
         }
+        __syncthreads();
+        off = 0;
+        for (int b = p; b != q; b += step) {
+            const int nc = size[lidx[b]];
+            tile_mac<true>(acc, buf + off, ldw, buf + off + nc * ldw, 1, nc, nc, nrt, ntiles);
+            off += stage_need(no, nc, nrhs, TR, TC);
+        }
+        __syncthreads();
+        p = q;
+    }
+    tile_store(acc, y + o, 1, n, no, nrhs, nrt, ntiles);
+    // publish: the barrier orders every thread's stores before thread 0's fence and flag
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(flags + o_blk, epoch);
     }
 }
 
 }  // namespace
 
 // y = L^{-1} x : y_i = x_i - sum_{k < i, i in S_k} W_ki^T y_k   (Eq. 23)
-template <class T>
+template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, const int *boff, const int *rptr,
                                                    const int *ridx, const int *rcol, const int64_t *coff,
                                                    const T *W, const T *x, T *y, int n, int nrhs, int budget,
                                                    int *flags, int epoch, int *ticket, int *err)
 {
     extern __shared__ unsigned char smraw[];
-    T *acc = (T *)smraw;                 // ni x nrhs
-    T *buf = acc + 64 * nrhs;            // staged chunk: W blocks (transposed) then y blocks
     __shared__ int s_i;
     if (threadIdx.x == 0) s_i = atomicAdd(ticket, 1);
     __syncthreads();
     const int i = s_i;
     if (i >= nb) return;
-    const int ni = size[i], o = boff[i];
-    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
-        const int c = e % ni, r = e / ni;
-        acc[e] = x[o + c + (int64_t)r * n];
-    }
-    const int p0 = rptr[i], p1 = rptr[i + 1];
-    for (int p = p0; p < p1;) {
-        const int q = next_chunk(p, p1, 1, ridx, size, ni, nrhs, budget);
-        // stage the coefficient blocks (static data) before waiting
-        int off = 0;
-        for (int b = p; b < q; ++b) {
-            const int k = ridx[b], nk = size[k];
-            const T *Wki = W + coff[k] + (int64_t)rcol[b] * nk;   // nk x ni, column-major
-            for (int e = threadIdx.x; e < nk * ni; e += blockDim.x) {
-                const int qq = e % nk, c = e / nk;
-                buf[off + qq * ni + c] = Wki[e];
-            }
-            off += nk * ni;
-        }
-        if (threadIdx.x == 0)
-            for (int b = p; b < q; ++b) wait_ready(flags, ridx[b], epoch, err);
-        __syncthreads();
-        const int yoff0 = off;
-        for (int b = p; b < q; ++b) {
-            const int k = ridx[b], nk = size[k], ok = boff[k];
-            for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
-                const int qq = e % nk, r = e / nk;
-                buf[off + e] = ldcg(y + ok + qq + (int64_t)r * n);
-            }
-            off += nk * nrhs;
-        }
-        __syncthreads();
-        if (p >= p1 - TAIL)   // a tail singleton (decided by position only: batch invariant)
-            single_block(acc, buf, ni, buf + yoff0, size[ridx[p]], ni, nrhs);
-        else
-        for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
-            const int c = e % ni, r = e / ni;
-            T s = acc[e];
-            int wo = 0, yo = yoff0;
-            for (int b = p; b < q; ++b) {
-                const int nk = size[ridx[b]];
-                const T *wb = buf + wo + c;
-                const T *yb = buf + yo + r * nk;
-                for (int qq = 0; qq < nk; ++qq) s = cfms(wb[qq * ni], yb[qq], s);
-                wo += nk * ni;
-                yo += nk * nrhs;
-            }
-            acc[e] = s;
-        }
-        __syncthreads();
-        p = q;
-    }
-    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
-        const int c = e % ni, r = e / ni;
-        y[o + c + (int64_t)r * n] = acc[e];
-    }
-    publish(flags, i, epoch);
+    sweep_row<T, TR, TC, NT, true>(i, size[i], size, boff, rptr, ridx, rcol, coff, W, x, y, n, nrhs, budget, flags,
+                                   epoch, err, (T *)smraw);
 }
 
 // y = L^{-T} x : y_k = x_k - sum_{j in S_k} W_kj y_j   (Eq. 24); j walked downwards
-template <class T>
+template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, const int *boff, const int *sptr,
                                                    const int *sidx, const int *srow, const int64_t *coff,
                                                    const T *W, const T *x, T *y, int n, int nrhs, int budget,
                                                    int *flags, int epoch, int *ticket, int *err)
 {
     extern __shared__ unsigned char smraw[];
-    T *acc = (T *)smraw;                 // nk x nrhs
-    T *buf = acc + 64 * nrhs;
     __shared__ int s_k;
     if (threadIdx.x == 0) s_k = nb - 1 - atomicAdd(ticket, 1);
     __syncthreads();
     const int k = s_k;
     if (k < 0) return;
-    const int nk = size[k], o = boff[k];
-    for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
-        const int rw = e % nk, r = e / nk;
-        acc[e] = x[o + rw + (int64_t)r * n];
-    }
-    const int pend = sptr[k] - 1;
-    for (int p = sptr[k + 1] - 1; p > pend;) {
-        const int q = next_chunk(p, pend, -1, sidx, size, nk, nrhs, budget);
-        int off = 0;
-        for (int b = p; b > q; --b) {
-            const int nj = size[sidx[b]];
-            const T *Wkj = W + coff[k] + (int64_t)srow[b] * nk;     // nk x nj, column-major
-            for (int e = threadIdx.x; e < nk * nj; e += blockDim.x) buf[off + e] = Wkj[e];
-            off += nk * nj;
-        }
-        if (threadIdx.x == 0)
-            for (int b = p; b > q; --b) wait_ready(flags, sidx[b], epoch, err);
-        __syncthreads();
-        const int yoff0 = off;
-        for (int b = p; b > q; --b) {
-            const int j = sidx[b], nj = size[j], oj = boff[j];
-            for (int e = threadIdx.x; e < nj * nrhs; e += blockDim.x) {
-                const int c = e % nj, r = e / nj;
-                buf[off + e] = ldcg(y + oj + c + (int64_t)r * n);
-            }
-            off += nj * nrhs;
-        }
-        __syncthreads();
-        if (p <= pend + TAIL)   // a tail singleton (decided by position only: batch invariant)
-            single_block(acc, buf, nk, buf + yoff0, size[sidx[p]], nk, nrhs);
-        else
-        for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
-            const int rw = e % nk, r = e / nk;
-            T s = acc[e];
-            int wo = 0, yo = yoff0;
-            for (int b = p; b > q; --b) {
-                const int nj = size[sidx[b]];
-                const T *wb = buf + wo + rw;
-                const T *yb = buf + yo + r * nj;
-                for (int c = 0; c < nj; ++c) s = cfms(wb[c * nk], yb[c], s);
-                wo += nk * nj;
-                yo += nj * nrhs;
-            }
-            acc[e] = s;
-        }
-        __syncthreads();
-        p = q;
-    }
-    for (int e = threadIdx.x; e < nk * nrhs; e += blockDim.x) {
-        const int rw = e % nk, r = e / nk;
-        y[o + rw + (int64_t)r * n] = acc[e];
-    }
-    publish(flags, k, epoch);
+    sweep_row<T, TR, TC, NT, false>(k, size[k], size, boff, sptr, sidx, srow, coff, W, x, y, n, nrhs, budget, flags,
+                                    epoch, err, (T *)smraw);
 }
 
-// dst[i + r*n] = src[idx[i] + r*n]
+// dst[i*nrhs + r] = src[idx[i] + r*n]   (right-hand sides interleaved)
 template <class T>
-__global__ void k_gather(int n, int nrhs, const int *idx, const T *src, T *dst)
+__global__ void k_gather_il(int n, int nrhs, const int *idx, const T *src, T *dst)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)n * nrhs) return;
-    int i = (int)(e % n), r = (int)(e / n);
+    int i = (int)(e / nrhs), r = (int)(e % nrhs);
     dst[e] = src[idx[i] + (int64_t)r * n];
 }
 
@@ -365,11 +289,11 @@ __global__ void __launch_bounds__(128) k_near_mv(int nl, const int *leaf_ptr, co
             const double2 *B = near + near_off[b];
             if (side == 0) {   // row l = t: sum_c B[i, c] u_s[c]
                 const int ms = leaf_ptr[s + 1] - leaf_ptr[s];
-                const double2 *us = u + leaf_ptr[s] + (int64_t)r * n;
-                for (int c = 0; c < ms; ++c) acc = cfma(B[i + (int64_t)c * mt], us[c], acc);
+                const double2 *us = u + (int64_t)leaf_ptr[s] * nrhs + r;
+                for (int c = 0; c < ms; ++c) acc = cfma(B[i + (int64_t)c * mt], us[(int64_t)c * nrhs], acc);
             } else {           // row l = s (t != s): sum_q B[q, i] u_t[q]
-                const double2 *ut = u + leaf_ptr[t] + (int64_t)r * n;
-                for (int q = 0; q < mt; ++q) acc = cfma(B[q + (int64_t)i * mt], ut[q], acc);
+                const double2 *ut = u + (int64_t)leaf_ptr[t] * nrhs + r;
+                for (int q = 0; q < mt; ++q) acc = cfma(B[q + (int64_t)i * mt], ut[(int64_t)q * nrhs], acc);
             }
         }
         y[on + i + (int64_t)r * n] = acc;
@@ -393,48 +317,63 @@ static OpData<float2> data32(hm_ctx *h)
     return {h->d_W32, h->d_Ad32, h->d_Dinv32, h->d_farU32, h->d_farV32, h->d_t32, h->d_s32, h->d_work32};
 }
 
-// Widest column batch one sweep launch takes (wider requests are split into slices); the
-// shared memory of a sweep CTA (accumulator + one staged 64-row block and its vector block)
-// then allows two CTAs per SM, so the resident CTAs cover the ~band of pending block rows.
+// Widest column batch one sweep launch takes (wider requests are split into slices).
 template <class T> static int max_cols() { return sizeof(T) == 16 ? 16 : 64; }
-template <class T> static int sweep_budget(int nrhs) { return 4096 + 64 * nrhs; }
 
-template <class T>
-static size_t sweep_smem(int nrhs)
+// Register tile per width: (TR, TC, NT) = (1, 1, 1) up to 4 columns, (2, 2, 1) up to 16,
+// (2, 4, 2) up to 64 (complex FP32 only); 256 threads cover every output tile of a 64-row
+// block.  The shared memory of a CTA holds one chunk: at least one 64 x 64 coefficient
+// block with its vector block.
+template <class T, int TR, int TC, int NT>
+static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs, int ep,
+                               int maxw)
 {
-    return sizeof(T) * (size_t)(64 * nrhs + sweep_budget<T>(nrhs));
+    Plan &P = h->plan;
+    const int budget = stage_need(64, 64, nrhs, TR, TC);
+    const size_t smem = sizeof(T) * (size_t)budget;
+    static bool attr = false;
+    if (!attr) {
+        const int smax = (int)(sizeof(T) * (size_t)stage_need(64, 64, maxw, TR, TC));
+        cudaFuncSetAttribute(k_sweep_fwd<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        cudaFuncSetAttribute(k_sweep_bwd<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        attr = true;
+    }
+    if (forward)
+        HM_LAUNCH(h, K_SWEEP_FWD,
+                  (k_sweep_fwd<T, TR, TC, NT><<<P.nb, 256, smem, h->stream>>>(
+                      P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs,
+                      budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+    else
+        HM_LAUNCH(h, K_SWEEP_BWD,
+                  (k_sweep_bwd<T, TR, TC, NT><<<P.nb, 256, smem, h->stream>>>(
+                      P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs,
+                      budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+    return cudaGetLastError();
 }
 
 template <class T>
 static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs)
 {
-    Plan &P = h->plan;
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_ticket, 0, sizeof(int), h->stream))) return e;
     const int ep = ++h->epoch;
-    const size_t smem = sweep_smem<T>(nrhs);
-    const int budget = sweep_budget<T>(nrhs);
-    if (forward)
-        HM_LAUNCH(h, K_SWEEP_FWD,
-                  k_sweep_fwd<T><<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx,
-                                                                 h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs, budget,
-                                                                 h->d_flags, ep, h->d_ticket, h->d_err));
-    else
-        HM_LAUNCH(h, K_SWEEP_BWD,
-                  k_sweep_bwd<T><<<P.nb, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx,
-                                                                 h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs, budget,
-                                                                 h->d_flags, ep, h->d_ticket, h->d_err));
-    return cudaGetLastError();
+    if (nrhs <= 4) return sweep_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, ep, 4);
+    if constexpr (sizeof(T) == 16) return sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, ep, 16);
+    else {
+        if (nrhs <= 16) return sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, ep, 16);
+        return sweep_shape<T, 2, 4, 2>(h, d, forward, x, y, nrhs, ep, 64);
+    }
 }
 
-// y (solve order) = Z_F x (solve order); ucl receives the cluster-order copy of x
+// y (solve order) = Z_F x (solve order); ucl receives the cluster-order copy of x with the
+// right-hand sides interleaved (ucl[i*nrhs + r])
 template <class T>
 static cudaError_t far_apply(hm_ctx *h, const OpData<T> &d, const T *x, T *y, int nrhs, T *ucl)
 {
     Plan &P = h->plan;
     FarPlan &F = h->fplan;
     const int n = P.n;
-    HM_LAUNCH(h, K_PERMUTE, k_gather<T><<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_cl2new, x,
+    HM_LAUNCH(h, K_PERMUTE, k_gather_il<T><<<nblk((int64_t)n * nrhs, 256), 256, 0, h->stream>>>(n, nrhs, h->d_cl2new, x,
                                                                                             ucl));
     (void)F;
     cudaError_t e = far_product<T>(h, d.U, d.V, d.t, d.s, ucl, y, nrhs);
@@ -456,9 +395,6 @@ static cudaError_t diag(hm_ctx *h, const OpData<T> &d, int mode, const T *x, con
 template <class T>
 static void set_attrs()
 {
-    const int smax = (int)sweep_smem<T>(max_cols<T>());
-    cudaFuncSetAttribute(k_sweep_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-    cudaFuncSetAttribute(k_sweep_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     cudaFuncSetAttribute(k_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * 128 * 64));
 }
 

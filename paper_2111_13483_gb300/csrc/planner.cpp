@@ -3,6 +3,8 @@
 // coefficients (Sec. 3.3, Figs. 3b-7b), storage layout and the far-field incidence lists.
 // Integer work only; every floating-point step runs on the device.
 #include <algorithm>
+#include <array>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <numeric>
@@ -365,6 +367,57 @@ void plan_far(hm_ctx *h)
     for (int l = 0; l < nl; ++l) F.nptr[l + 1] = F.nptr[l] + (int)nl_lists[l].size();
     F.nent.clear();
     for (int l = 0; l < nl; ++l) F.nent.insert(F.nent.end(), nl_lists[l].begin(), nl_lists[l].end());
+    // rank-vector tasks: group the factor columns by the range they contract over
+    // (V_b over the column range for t_b, U_b over the row range for s_b), 64 per task,
+    // larger tasks first
+    std::map<std::pair<int, int>, std::vector<std::array<int64_t, 5>>> by_range;
+    for (int b = 0; b < nf; ++b) {
+        const int rk = h->far_rank[b];
+        if (rk <= 0) continue;
+        const int m = h->far_r1[b] - h->far_r0[b], c = h->far_c1[b] - h->far_c0[b];
+        for (int l0 = 0; l0 < rk; l0 += 64) {
+            const int64_t cols = std::min(64, rk - l0);
+            by_range[{h->far_c0[b], h->far_c1[b]}].push_back({h->far_voff[b] + l0 * c, c, cols, F.toff[b] + l0, 1});
+            by_range[{h->far_r0[b], h->far_r1[b]}].push_back({h->far_uoff[b] + l0 * m, m, cols, F.toff[b] + l0, 0});
+        }
+    }
+    struct Task {
+        int lo, hi;
+        std::vector<std::array<int64_t, 5>> items;
+    };
+    std::vector<Task> tasks;
+    for (auto &kv : by_range) {
+        Task cur{kv.first.first, kv.first.second, {}};
+        int R = 0;
+        for (auto &it : kv.second) {
+            if (R + it[2] > 64) {
+                tasks.push_back(cur);
+                cur.items.clear();
+                R = 0;
+            }
+            cur.items.push_back(it);
+            R += (int)it[2];
+        }
+        if (!cur.items.empty()) tasks.push_back(cur);
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [](const Task &x, const Task &y) {
+        return (int64_t)(x.hi - x.lo) * (int64_t)x.items.size() > (int64_t)(y.hi - y.lo) * (int64_t)y.items.size();
+    });
+    F.p1_lo.clear(), F.p1_hi.clear(), F.p1_ld.clear(), F.p1_rank.clear(), F.p1_row.clear(), F.p1_isv.clear();
+    F.p1_off.clear();
+    F.p1_ptr.assign(1, 0);
+    for (const Task &tk : tasks) {
+        F.p1_lo.push_back(tk.lo);
+        F.p1_hi.push_back(tk.hi);
+        for (auto &it : tk.items) {
+            F.p1_off.push_back(it[0]);
+            F.p1_ld.push_back((int)it[1]);
+            F.p1_rank.push_back((int)it[2]);
+            F.p1_row.push_back((int)it[3]);
+            F.p1_isv.push_back((int)it[4]);
+        }
+        F.p1_ptr.push_back((int)F.p1_off.size());
+    }
     F.entries = 0;
     for (int b = 0; b < nf; ++b) {
         int64_t m = h->far_r1[b] - h->far_r0[b], c = h->far_c1[b] - h->far_c0[b];

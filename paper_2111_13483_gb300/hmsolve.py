@@ -20,6 +20,7 @@ _NAMES = {0: "HM_OK", -1: "HM_EINVAL", -2: "HM_ENOMEM", -3: "HM_ESINGULAR", -4: 
           -6: "HM_ECUDA", -7: "HM_ESTATE", -8: "HM_EBUSY"}
 
 OP_A, OP_LINV, OP_LTINV, OP_ZF, OP_DINV, OP_Z = 0, 1, 2, 3, 4, 5
+OP32 = 8   # OP32 + op (op 0-4): the complex-FP32 operator of a precision 1 handle
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
