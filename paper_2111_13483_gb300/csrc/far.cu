@@ -55,16 +55,15 @@ __global__ void __launch_bounds__(256) k_far_t(const int *task_lo, const int *ta
     for (int c0 = lo; c0 < hi; c0 += SEG) {
         const int ch = min(SEG, hi - c0);
         T *Ws = buf, *Ys = buf + ch * ldw;
-        for (int e = threadIdx.x; e < ch * R; e += blockDim.x) {
-            const int qq = e % ch, rr = e / ch, it = s_item[rr];
-            const T *F = (item_isv[it] ? V : U) + item_off[it] + (int64_t)s_l[rr] * item_ld[it];
-            Ws[qq * ldw + rr] = F[c0 - lo + qq];
-        }
+        stage_copy(
+            ch * R,
+            [&](int e) {
+                const int rr = e / ch, it = s_item[rr];
+                return ((item_isv[it] ? V : U) + item_off[it] + (int64_t)s_l[rr] * item_ld[it])[c0 - lo + e % ch];
+            },
+            [&](int e, T v) { Ws[(e % ch) * ldw + e / ch] = v; });
         const T *uc = u + (int64_t)c0 * nrhs;
-        for (int e = threadIdx.x; e < ch * nrhs; e += blockDim.x) {
-            const int qq = e / nrhs, r = e % nrhs;
-            Ys[qq * ldr + r] = uc[e];
-        }
+        stage_copy(ch * nrhs, [&](int e) { return uc[e]; }, [&](int e, T v) { Ys[(e / nrhs) * ldr + e % nrhs] = v; });
         __syncthreads();
         tile_mac<false>(acc, Ws, ldw, Ys, ldr, 1, ch, nrt, ntiles);
         __syncthreads();
@@ -164,20 +163,14 @@ __global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, cons
             if (nseg > 0 && used + need > budget) break;
             T *Ws = buf + used, *Ys = Ws + len * ldw;
             if (g.fi == 1)
-                for (int e = threadIdx.x; e < len * ni; e += blockDim.x) {
-                    const int i = e % ni, q = e / ni;
-                    Ws[q * ldw + i] = g.Fb[i + (int64_t)(kk + q) * g.fk];
-                }
+                stage_copy(len * ni, [&](int e) { return g.Fb[e % ni + (int64_t)(kk + e / ni) * g.fk]; },
+                           [&](int e, T v) { Ws[(e / ni) * ldw + e % ni] = v; });
             else
-                for (int e = threadIdx.x; e < len * ni; e += blockDim.x) {
-                    const int q = e % len, i = e / len;
-                    Ws[q * ldw + i] = g.Fb[(int64_t)i * g.fi + kk + q];
-                }
+                stage_copy(len * ni, [&](int e) { return g.Fb[(int64_t)(e / len) * g.fi + kk + e % len]; },
+                           [&](int e, T v) { Ws[(e % len) * ldw + e / len] = v; });
             const T *yb = g.Yb + (int64_t)kk * nrhs;
-            for (int e = threadIdx.x; e < len * nrhs; e += blockDim.x) {
-                const int q = e / nrhs, r = e % nrhs;
-                Ys[q * ldr + r] = yb[e];
-            }
+            stage_copy(len * nrhs, [&](int e) { return yb[e]; },
+                       [&](int e, T v) { Ys[(e / nrhs) * ldr + e % nrhs] = v; });
             used += need;
             ++nseg;
             kk += len;

@@ -110,16 +110,12 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
             T *Ws = buf + off;
             if (FWD) {   // W_ko: nc x no at coff[k] + lcol*nc; M(row, qq) = W_ko(qq, row)
                 const T *src = W + coff[k] + (int64_t)lcol[b] * nc;
-                for (int e = threadIdx.x; e < nc * no; e += blockDim.x) {
-                    const int qq = e % nc, row = e / nc;
-                    Ws[qq * ldw + row] = src[e];
-                }
+                stage_copy(nc * no, [&](int e) { return src[e]; },
+                           [&](int e, T v) { Ws[(e % nc) * ldw + e / nc] = v; });
             } else {     // W_oj: no x nc at coff[o] + lcol*no; M(row, qq) = W_oj(row, qq)
                 const T *src = W + coff[o_blk] + (int64_t)lcol[b] * no;
-                for (int e = threadIdx.x; e < nc * no; e += blockDim.x) {
-                    const int row = e % no, qq = e / no;
-                    Ws[qq * ldw + row] = src[e];
-                }
+                stage_copy(nc * no, [&](int e) { return src[e]; },
+                           [&](int e, T v) { Ws[(e / no) * ldw + e % no] = v; });
             }
             off += stage_need(no, nc, nrhs, TR, TC);
         }
@@ -130,10 +126,8 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
         for (int b = p; b != q; b += step) {
             const int k = lidx[b], nc = size[k], ok = boff[k];
             T *Ys = buf + off + nc * ldw;
-            for (int e = threadIdx.x; e < nc * nrhs; e += blockDim.x) {
-                const int qq = e % nc, r = e / nc;
-                Ys[r * nc + qq] = ldcg(y + ok + qq + (int64_t)r * n);
-            }
+            stage_copy(nc * nrhs, [&](int e) { return ldcg(y + ok + e % nc + (int64_t)(e / nc) * n); },
+                       [&](int e, T v) { Ys[e] = v; });
             off += stage_need(no, nc, nrhs, TR, TC);
         }
         __syncthreads();
@@ -151,7 +145,7 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicExch(flags + o_blk, epoch);
+        *(volatile int *)(flags + o_blk) = epoch;
     }
 }
 

@@ -97,6 +97,25 @@ __device__ __forceinline__ void tile_mac(Tile<T, TR, TC, NT> &acc, const T *Ws, 
     }
 }
 
+// Staging copy dst(e) = src(e) for e < count over the CTA's threads, SB loads in flight per
+// thread before their stores (a plain loop would wait for each load before the next).
+template <int SB = 8, class Ld, class St> __device__ __forceinline__ void stage_copy(int count, Ld &&ld, St &&st)
+{
+    for (int e0 = threadIdx.x; e0 < count; e0 += SB * blockDim.x) {
+        decltype(ld(0)) v[SB];
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < count) v[u] = ld(e);
+        }
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < count) st(e, v[u]);
+        }
+    }
+}
+
 // Tile shape for a column count: (1, 1, 1) up to 4 columns, (2, 2, 1) up to 16, (2, 4, 2) up
 // to 64 (complex FP32); with 256 threads every output tile of a 64-row block is covered.
 // Dispatches f.template run<TR, TC, NT>(maxw) with maxw the widest count of the shape.
