@@ -220,7 +220,7 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
     if ((e = h->arena.alloc((void **)&h->d_err, sizeof(int))) ||
         (e = h->arena.alloc((void **)&h->d_ticket, sizeof(int))) ||
         (e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream)) ||
-        (h->opts.precision == 1 && (e = make_fp32_copies(h, false))) || (e = cudaStreamSynchronize(h->stream))) {
+        (h->opts.precision == 1 && (e = make_fp32_copies(h))) || (e = cudaStreamSynchronize(h->stream))) {
         int s = cuda_fail(h, e, "hmat_create");
         h->arena.release_all();
         if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -238,13 +238,18 @@ int precond_setup(hm_handle h)
     h->setup_done = false;
     Plan &P = h->plan;
     cudaError_t e;
-    if (!h->d_W) {
-        if ((e = h->arena.alloc((void **)&h->d_W, sizeof(double2) * P.coef_entries)) ||
-            (e = h->arena.alloc((void **)&h->d_Ad, sizeof(double2) * P.diag_entries)) ||
-            (e = h->arena.alloc((void **)&h->d_Dinv, sizeof(double2) * P.diag_entries)))
+    const bool mixed = h->opts.precision == 1;
+    if (!h->d_Dinv) {   // factors: FP64, or FP32 (with D_k^{-1} in both) for the mixed setup
+        if ((e = h->arena.alloc((void **)&h->d_Dinv, sizeof(double2) * P.diag_entries)) ||
+            (mixed ? ((e = h->arena.alloc((void **)&h->d_W32, sizeof(float2) * P.coef_entries)) ||
+                      (e = h->arena.alloc((void **)&h->d_Ad32, sizeof(float2) * P.diag_entries)) ||
+                      (e = h->arena.alloc((void **)&h->d_Dinv32, sizeof(float2) * P.diag_entries)))
+                   : ((e = h->arena.alloc((void **)&h->d_W, sizeof(double2) * P.coef_entries)) ||
+                      (e = h->arena.alloc((void **)&h->d_Ad, sizeof(double2) * P.diag_entries)))))
             return cuda_fail(h, e, "precond_setup allocation");
     }
-    if ((e = h->arena.alloc((void **)&h->d_A, sizeof(double2) * P.coef_entries)))
+    if ((e = mixed ? h->arena.alloc((void **)&h->d_A32, sizeof(float2) * P.coef_entries)
+                   : h->arena.alloc((void **)&h->d_A, sizeof(double2) * P.coef_entries)))
         return cuda_fail(h, e, "precond_setup workspace");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -253,7 +258,6 @@ int precond_setup(hm_handle h)
     int bad = -1;
     e = setup_run(h, &bad);
     if (!e && bad < 0) e = compress_run(h);
-    if (!e && bad < 0 && h->opts.precision == 1) e = make_fp32_copies(h, true);
     cudaEventRecord(e1, h->stream);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -261,7 +265,9 @@ int precond_setup(hm_handle h)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->arena.release(h->d_A, 0);
+    h->arena.release(h->d_A32, 0);
     h->d_A = nullptr;
+    h->d_A32 = nullptr;
     if (e) return cuda_fail(h, e, "precond_setup");
     if (bad >= 0) {
         h->err = "pivot block D_" + std::to_string(bad) + " (solve order; leaf " + std::to_string(P.order[bad]) +
@@ -417,23 +423,35 @@ int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out)
     const Plan &P = h->plan;
     if (k < 0 || k >= P.nb || what < 0 || what > 3) return HM_EINVAL;
     cudaSetDevice(h->dev);
-    const double2 *src;
+    const bool mixed = h->opts.precision == 1;
+    const void *src;
     size_t cnt;
+    bool f32 = false;
     int64_t nk = P.size[k];
     if (what == 0) {
-        src = h->d_Ad + P.doff[k];
+        src = mixed ? (const void *)(h->d_Ad32 + P.doff[k]) : (const void *)(h->d_Ad + P.doff[k]);
+        f32 = mixed;
         cnt = nk * nk;
     } else if (what == 1) {
         src = h->d_Dinv + P.doff[k];
         cnt = nk * nk;
     } else {
-        src = h->d_W + P.coff[k];
+        src = mixed ? (const void *)(h->d_W32 + P.coff[k]) : (const void *)(h->d_W + P.coff[k]);
+        f32 = mixed;
         cnt = (size_t)nk * P.M[k];
     }
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(out, src, sizeof(double2) * cnt, cudaMemcpyDeviceToHost, h->stream)) ||
+    if (!f32) {
+        if ((e = cudaMemcpyAsync(out, src, sizeof(double2) * cnt, cudaMemcpyDeviceToHost, h->stream)) ||
+            (e = cudaStreamSynchronize(h->stream)))
+            return cuda_fail(h, e, "hm_get_block");
+        return HM_OK;
+    }
+    std::vector<float2> tmp(cnt);   // FP32 factors of the mixed setup, widened on the host
+    if ((e = cudaMemcpyAsync(tmp.data(), src, sizeof(float2) * cnt, cudaMemcpyDeviceToHost, h->stream)) ||
         (e = cudaStreamSynchronize(h->stream)))
         return cuda_fail(h, e, "hm_get_block");
+    for (size_t i = 0; i < cnt; ++i) out[i] = hm_c128{(double)tmp[i].x, (double)tmp[i].y};
     return HM_OK;
 }
 
@@ -469,6 +487,10 @@ int hm_apply(hm_handle h, int32_t op, const void *dx, void *dy, int32_t nrhs)
     }
     if (op >= 8 && h->opts.precision != 1) {
         h->err = "hm_apply: the complex-FP32 operators exist for precision 1 handles only";
+        return HM_ESTATE;
+    }
+    if (h->opts.precision == 1 && (op <= 2 || op == 4)) {
+        h->err = "hm_apply: a precision 1 handle keeps complex-FP32 factors (ops 8-12)";
         return HM_ESTATE;
     }
     cudaSetDevice(h->dev);

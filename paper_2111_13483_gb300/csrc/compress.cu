@@ -39,7 +39,7 @@ __device__ __forceinline__ float2 conjd(float2 a) { return make_float2(a.x, -a.y
 
 template <class TC>
 __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, const int *fill_k, const int *size,
-                                                  const int *sidx, const int *srow, const int64_t *coff, double2 *W,
+                                                  const int *sidx, const int *srow, const int64_t *coff, TC *W,
                                                   double tol, int *rank_out)
 {
     typedef typename Real<TC>::type R;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
     if (f >= nfill) return;
     const int e = fill_e[f], k = fill_k[f];
     const int m = size[k], n = size[sidx[e]];
-    double2 *Wb = W + coff[k] + (int64_t)srow[e] * m;   // m x n, column-major, ld m
+    TC *Wb = W + coff[k] + (int64_t)srow[e] * m;   // m x n, column-major, ld m
     __shared__ R s_part[8];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const bool tr = m < n;                       // A = W^H (rows nr = n, columns nc = m)
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
     R fro2 = 0;
     for (int x = threadIdx.x; x < m * n; x += blockDim.x) {
         const int r = x % m, c = x / m;
-        const TC w = cconv<TC>(Wb[x]);
+        const TC w = Wb[x];
         fro2 += w.x * w.x + w.y * w.y;
         if (tr) A[r * 64 + c] = conjd(w);
         else A[c * 64 + r] = w;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
                 acc = tr ? cfma(V[o * 64 + row], conjd(A[o * 64 + c]), acc)
                          : cfma(A[o * 64 + row], conjd(V[o * 64 + c]), acc);
             }
-            Wb[x] = cwiden(acc);
+            Wb[x] = acc;
         }
     }
     if (threadIdx.x == 0) rank_out[f] = r;
@@ -207,11 +207,12 @@ cudaError_t compress_run(hm_ctx *h)
             return e;
         attr = true;
     }
-    // FP64 Jacobi for the FP64 path (the oracle's rank decisions); FP32 rotations in mixed mode
+    // FP64 Jacobi on the FP64 factors (the oracle's rank decisions); FP32 on the FP32 factors
+    // of the mixed-precision setup
     if (h->opts.precision == 1)
         HM_LAUNCH(h, K_COMPRESS,
                   k_compress<float2><<<nfill, 256, smem32, h->stream>>>(nfill, h->d_fill_e, h->d_fill_k, h->d_size,
-                                                                        h->d_sidx, h->d_srow, h->d_coff, h->d_W,
+                                                                        h->d_sidx, h->d_srow, h->d_coff, h->d_W32,
                                                                         h->opts.fill_tol, h->d_fill_rank));
     else
         HM_LAUNCH(h, K_COMPRESS,

@@ -136,7 +136,8 @@ struct hm_ctx {
     int64_t *d_coff = nullptr, *d_doff = nullptr;
     int *d_rptr = nullptr, *d_ridx = nullptr, *d_rcol = nullptr;
     // device: setup outputs / workspace
-    double2 *d_A = nullptr;      // stacked columns workspace (scratch during setup)
+    double2 *d_A = nullptr;      // stacked columns workspace (scratch during setup; FP64 setup)
+    float2 *d_A32 = nullptr;     // the same for the mixed-precision setup
     double2 *d_Ad = nullptr;     // diagonal blocks workspace -> D_k after setup
     double2 *d_W = nullptr;      // coefficient panels W_k (uncompressed)
     double2 *d_Dinv = nullptr;   // D_k^{-1}
@@ -152,7 +153,8 @@ struct hm_ctx {
     int t_cols = 0;
     double2 *d_work = nullptr;               // operator scratch vectors
     int work_cols = 0;
-    // complex-FP32 copies for the mixed-precision inner operator
+    // complex-FP32 factors of the mixed-precision setup (D_k, W, D_k^{-1}; D_k^{-1} is also
+    // kept in FP64 in d_Dinv) and FP32 copies of the far factors for the inner operator
     float2 *d_W32 = nullptr, *d_Ad32 = nullptr, *d_Dinv32 = nullptr, *d_farU32 = nullptr, *d_farV32 = nullptr;
     float2 *d_t32 = nullptr, *d_s32 = nullptr, *d_work32 = nullptr;
     int t32_cols = 0;
@@ -184,7 +186,7 @@ cudaError_t setup_run(hm_ctx *h, int *bad_block);
 cudaError_t compress_run(hm_ctx *h);
 cudaError_t op_apply(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
 cudaError_t op_apply32(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
-cudaError_t make_fp32_copies(hm_ctx *h, bool factors);
+cudaError_t make_fp32_copies(hm_ctx *h);
 cudaError_t to_solve_order(hm_ctx *h, const double2 *src, int64_t lds, double2 *dst, int nrhs);
 cudaError_t to_orig_order(hm_ctx *h, const double2 *src, double2 *dst, int64_t ldd, int nrhs);
 cudaError_t z_apply_orig(hm_ctx *h, const double2 *x, double2 *y, int nrhs);

@@ -436,8 +436,8 @@ cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs)
     return cudaSuccess;
 }
 
-// Complex FP32 copies of the far factors (at create) and of the factors (after setup).
-cudaError_t make_fp32_copies(hm_ctx *h, bool factors)
+// Complex FP32 copies of the far factors for the mixed-precision inner operator (at create).
+cudaError_t make_fp32_copies(hm_ctx *h)
 {
     cudaError_t e;
     auto narrow = [&](const double2 *src, float2 **dst, size_t len) -> cudaError_t {
@@ -447,14 +447,8 @@ cudaError_t make_fp32_copies(hm_ctx *h, bool factors)
             HM_LAUNCH(h, K_VEC, k_narrow<<<nblk((int64_t)len, 256), 256, 0, h->stream>>>((int64_t)len, src, *dst));
         return cudaGetLastError();
     };
-    if (!factors) {
-        if ((e = narrow(h->d_farU, &h->d_farU32, (size_t)h->farU_len))) return e;
-        return narrow(h->d_farV, &h->d_farV32, (size_t)h->farV_len);
-    }
-    const Plan &P = h->plan;
-    if ((e = narrow(h->d_W, &h->d_W32, (size_t)P.coef_entries))) return e;
-    if ((e = narrow(h->d_Ad, &h->d_Ad32, (size_t)P.diag_entries))) return e;
-    return narrow(h->d_Dinv, &h->d_Dinv32, (size_t)P.diag_entries);
+    if ((e = narrow(h->d_farU, &h->d_farU32, (size_t)h->farU_len))) return e;
+    return narrow(h->d_farV, &h->d_farV32, (size_t)h->farV_len);
 }
 
 template <class T>

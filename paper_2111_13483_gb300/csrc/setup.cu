@@ -11,12 +11,17 @@
 //   Dinv + doff[k]      D_k^{-1} for the Eq. 28 preconditioner.
 // Step k: pivot inverse (one CTA), panel (M_k/64 CTAs), Schur updates
 // A_ij -= A_ik W_kj for i >= j in S_k (Eq. 19; one CTA per block pair, diagonal blocks
-// in full; FP32 products in the mixed-precision setup).  Stream order gives the step
-// dependencies.
+// in full).  Stream order gives the step dependencies.
+//
+// S is the storage and arithmetic type of A, the diagonal blocks and W: complex FP64, or
+// complex FP32 in the mixed-precision setup, where the pivot blocks are still inverted in
+// FP64 (their inverse is kept in FP64 and as an FP32 copy for the panels and the inner
+// operator) and everything else stays FP32, so no step converts between the two.
 #include <cstdio>
 
 #include "cplx.cuh"
 #include "hm_internal.h"
+#include "tile.cuh"
 
 namespace hm {
 
@@ -34,10 +39,11 @@ __device__ __forceinline__ int find_row(const int *sptr, const int *sidx, const 
 }
 
 // Near-field blocks (cluster leaves t <= s) into the solve-order workspace.
+template <class S>
 __global__ void k_scatter_near(int n_near, const int *near_t, const int *near_s, const int64_t *near_off,
                                const double2 *near, const int *leaf_ptr, const int *pos, const int *sptr,
                                const int *sidx, const int *srow, const int *M, const int64_t *coff,
-                               const int64_t *doff, double2 *A, double2 *Ad, int *err)
+                               const int64_t *doff, S *A, S *Ad, int *err)
 {
     int b = blockIdx.x;
     if (b >= n_near) return;
@@ -45,7 +51,7 @@ __global__ void k_scatter_near(int n_near, const int *near_t, const int *near_s,
     int m = leaf_ptr[t + 1] - leaf_ptr[t], n = leaf_ptr[s + 1] - leaf_ptr[s];
     const double2 *B = near + near_off[b];
     int i = pos[t], j = pos[s];
-    double2 *dst;
+    S *dst;
     int ld;
     bool tr;
     if (i == j) {
@@ -67,30 +73,35 @@ __global__ void k_scatter_near(int n_near, const int *near_t, const int *near_s,
     }
     for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
         int rr = e % m, cc = e / m;
-        double2 v = B[e];
+        const S v = cconv<S>(B[e]);
         if (!tr) dst[rr + (int64_t)cc * ld] = v;
         else dst[cc + (int64_t)rr * ld] = v;
     }
 }
 
 // In-place Gauss-Jordan inverse with partial pivoting (largest modulus, lowest row on
-// ties) of D_k = Ad[k]; result to Dinv[k].  err <- k+1 on a singular pivot.
-__global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, const int64_t *doff, const double2 *Ad,
-                                                       double2 *Dinv, int *err)
+// ties) of D_k = Ad[k], in FP64 whatever S is; result to Dinv[k] (and its FP32 copy when
+// Dinv32 is given).  err <- k+1 on a singular pivot.  Per column: one warp finds the pivot;
+// one pass forms the scaled pivot row and the pivot column and moves the old row c into
+// the pivot's row; one pass eliminates (four fused multiply-adds per entry) and writes the
+// new row c.
+template <class S>
+__global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, const int64_t *doff, const S *Ad,
+                                                       double2 *Dinv, float2 *Dinv32, int *err)
 {
     extern __shared__ double2 sm[];
     const int n = size[k];
     const int ld = n + 1;                      // padded
     double2 *a = sm;                           // n x ld, row-major a[r*ld + c]
     double2 *rowc = sm + n * ld;               // n: pivot row after scaling
-    double2 *colc = rowc + n;                  // n: pivot column before the update
+    double2 *colc = rowc + n;                  // n: pivot column (rows after the interchange)
     __shared__ int piv[64];
     __shared__ int s_p;
     __shared__ double2 s_d;
-    const double2 *D = Ad + doff[k];
+    const S *D = Ad + doff[k];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int r = e % n, c = e / n;
-        a[r * ld + c] = D[e];
+        a[r * ld + c] = cwiden(D[e]);
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
@@ -123,37 +134,30 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, c
         }
         __syncthreads();
         const int p = s_p;
-        if (p != c)
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                double2 t = a[c * ld + j];
-                a[c * ld + j] = a[p * ld + j];
-                a[p * ld + j] = t;
-            }
-        __syncthreads();
         const double2 d = s_d;
+        // rows c and p interchanged: the new row c is the old row p
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            rowc[j] = (j == c) ? d : cmul(a[c * ld + j], d);
-            colc[j] = a[j * ld + c];
+            const double2 ap = a[p * ld + j];
+            rowc[j] = (j == c) ? d : cmul(ap, d);
+            colc[j] = a[(j == p ? c : j) * ld + c];
+            if (p != c) a[p * ld + j] = a[c * ld + j];
         }
         __syncthreads();
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            int r = e / n, j = e % n;
-            if (r == c) continue;
-            double2 f = colc[r];
-            double2 rc = rowc[j];
+            const int r = e / n, j = e % n;
             double2 nv;
-            if (j == c) {
-                nv = cmul(f, d);
-                nv.x = -nv.x;
-                nv.y = -nv.y;
-            } else {
-                double2 cur = a[r * ld + j];
-                nv = make_double2(cur.x - (f.x * rc.x - f.y * rc.y), cur.y - (f.x * rc.y + f.y * rc.x));
+            if (r == c) nv = rowc[j];
+            else {
+                const double2 f = colc[r];
+                if (j == c) nv = make_double2(-(f.x * d.x - f.y * d.y), -(f.x * d.y + f.y * d.x));
+                else {
+                    const double2 cur = a[r * ld + j], rc = rowc[j];
+                    nv.x = fma(-f.x, rc.x, fma(f.y, rc.y, cur.x));
+                    nv.y = fma(-f.x, rc.y, fma(-f.y, rc.x, cur.y));
+                }
             }
             a[r * ld + j] = nv;
         }
-        __syncthreads();
-        for (int j = threadIdx.x; j < n; j += blockDim.x) a[c * ld + j] = rowc[j];
         __syncthreads();
     }
     // undo the row interchanges as column interchanges, last first
@@ -168,24 +172,28 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, c
         __syncthreads();
     }
     double2 *out = Dinv + doff[k];
+    float2 *out32 = Dinv32 ? Dinv32 + doff[k] : nullptr;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int r = e % n, c = e / n;
-        out[e] = a[r * ld + c];
+        const double2 v = a[r * ld + c];
+        out[e] = v;
+        if (out32) out32[e] = make_float2((float)v.x, (float)v.y);
     }
 }
 
-// W_k[:, c0:c0+64] = D_k^{-1} (A_col_k[c0:c0+64, :])^T
+// W_k[:, c0:c0+64] = D_k^{-1} (A_col_k[c0:c0+64, :])^T in S arithmetic
+template <class S>
 __global__ void __launch_bounds__(256) k_panel(int k, const int *size, const int *M, const int64_t *coff,
-                                               const int64_t *doff, const double2 *Dinv, const double2 *A, double2 *W)
+                                               const int64_t *doff, const S *Dinv, const S *A, S *W)
 {
-    extern __shared__ double2 psm[];
-    double2 *dinv = psm;              // dinv[r*65 + q] = D_k^{-1}[r, q]
-    double2 *ac = psm + 64 * 65;      // ac[q*65 + col] = A_col[c0+col, q]
+    extern __shared__ unsigned char psraw[];
+    S *dinv = (S *)psraw;             // dinv[r*65 + q] = D_k^{-1}[r, q]
+    S *ac = dinv + 64 * 65;           // ac[q*65 + col] = A_col[c0+col, q]
     const int n = size[k], Mk = M[k];
     const int c0 = blockIdx.x * 64;
     const int nc = min(64, Mk - c0);
-    const double2 *Di = Dinv + doff[k];
-    const double2 *Ac = A + coff[k];
+    const S *Di = Dinv + doff[k];
+    const S *Ac = A + coff[k];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int r = e % n, q = e / n;
         dinv[r * 65 + q] = Di[e];
@@ -195,47 +203,42 @@ __global__ void __launch_bounds__(256) k_panel(int k, const int *size, const int
         ac[q * 65 + col] = Ac[(c0 + col) + (int64_t)q * Mk];
     }
     __syncthreads();
-    double2 *Wk = W + coff[k];
+    S *Wk = W + coff[k];
     for (int e = threadIdx.x; e < n * nc; e += blockDim.x) {
         int r = e % n, col = e / n;
-        double2 acc = make_double2(0, 0);
+        S acc = czero(S());
         for (int q = 0; q < n; ++q) acc = cfma(dinv[r * 65 + q], ac[q * 65 + col], acc);
         Wk[r + (int64_t)(c0 + col) * n] = acc;
     }
 }
 
-// Schur updates of step k (Eq. 19): one CTA per pair (a >= b) of S_k, A_ij -= A_ik W_kj.
-// TC is the arithmetic type: double2 (FP64 setup) or float2 (mixed-precision setup: FP32
-// products of the FP64-stored blocks, subtracted in FP64).  A 16 x 16 thread grid covers
-// the output block with up to 4 x 4 outputs per thread; every loop runs over the block's
-// actual rows and columns, so no issue slot is spent on padding.
-// C (ni x nj) -= A (ni x nk) W (nk x nj) on a 16U x 16U tile: thread (tx, ty) owns rows
-// tx + 16u and columns ty + 16v (u, v < U).  The shared tiles are zero-padded to the tile
-// size, so every thread runs the same unpredicated FMA sequence; padded outputs are dropped.
-template <class TC, int QC, int U>
-__device__ __forceinline__ void update_tile(TC (*As)[65], TC (*Ws)[65], const double2 *Aik, int Mk, const double2 *Wkj,
-                                            int nk, int ni, int nj, double2 *C, int ldc)
+// Schur updates of step k (Eq. 19): one CTA per pair (a >= b) of S_k, A_ij -= A_ik W_kj,
+// in S arithmetic.  C (ni x nj) -= A (ni x nk) W (nk x nj) on a 16U x 16U tile: thread
+// (tx, ty) owns rows tx + 16u and columns ty + 16v (u, v < U).  The shared tiles are
+// zero-padded to the tile size, so every thread runs the same unpredicated FMA sequence;
+// padded outputs are dropped.
+template <class S, int QC, int U>
+__device__ __forceinline__ void update_tile(S (*As)[65], S (*Ws)[65], const S *Aik, int Mk, const S *Wkj, int nk,
+                                            int ni, int nj, S *C, int ldc)
 {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     constexpr int TS = 16 * U;
-    TC acc[U][U];
+    S acc[U][U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < U; ++v) acc[u][v] = czero(TC());
+        for (int v = 0; v < U; ++v) acc[u][v] = czero(S());
     for (int q0 = 0; q0 < nk; q0 += QC) {
         const int nq = min(QC, nk - q0);
-        for (int e = threadIdx.x; e < TS * nq; e += blockDim.x) {
-            const int r = e % TS, q = e / TS;
-            As[q][r] = r < ni ? cconv<TC>(Aik[r + (int64_t)(q0 + q) * Mk]) : czero(TC());
-        }
-        for (int e = threadIdx.x; e < nq * TS; e += blockDim.x) {
-            const int q = e % nq, c = e / nq;
-            Ws[q][c] = c < nj ? cconv<TC>(Wkj[(q0 + q) + (int64_t)c * nk]) : czero(TC());
-        }
+        stage_copy<4>(
+            TS * nq, [&](int e) { return e % TS < ni ? Aik[e % TS + (int64_t)(q0 + e / TS) * Mk] : czero(S()); },
+            [&](int e, S v) { As[e / TS][e % TS] = v; });
+        stage_copy<4>(
+            nq * TS, [&](int e) { return e / nq < nj ? Wkj[(q0 + e % nq) + (int64_t)(e / nq) * nk] : czero(S()); },
+            [&](int e, S v) { Ws[e % nq][e / nq] = v; });
         __syncthreads();
         for (int q = 0; q < nq; ++q) {
-            TC av[U], wv[U];
+            S av[U], wv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) av[u] = As[q][tx + 16 * u];
 #pragma unroll
@@ -253,27 +256,26 @@ __device__ __forceinline__ void update_tile(TC (*As)[65], TC (*Ws)[65], const do
         for (int v = 0; v < U; ++v) {
             const int r = tx + 16 * u, c = ty + 16 * v;
             if (r < ni && c < nj) {
-                double2 *p = C + r + (int64_t)c * ldc;
-                const double2 d = cwiden(acc[u][v]);
-                double2 o = *p;
-                o.x -= d.x;
-                o.y -= d.y;
+                S *p = C + r + (int64_t)c * ldc;
+                S o = *p;
+                o.x -= acc[u][v].x;
+                o.y -= acc[u][v].y;
                 *p = o;
             }
         }
 }
 
-template <class TC>
+template <class S>
 __global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, const int *sptr, const int *sidx,
                                                 const int *srow, const int *M, const int64_t *coff,
-                                                const int64_t *doff, const double2 *W, double2 *A, double2 *Ad)
+                                                const int64_t *doff, const S *W, S *A, S *Ad)
 {
-    constexpr int QC = sizeof(TC) == 16 ? 16 : 32;
-    __shared__ TC As[QC][65];   // As[q][r] = A_ik[r, q0+q]
-    __shared__ TC Ws[QC][65];   // Ws[q][c] = W_kj[q0+q, c]
-    // triangular index -> (a, b), a >= b
-    long t = blockIdx.x;
-    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    constexpr int QC = sizeof(S) == 16 ? 16 : 32;
+    __shared__ S As[QC][65];   // As[q][r] = A_ik[r, q0+q]
+    __shared__ S Ws[QC][65];   // Ws[q][c] = W_kj[q0+q, c]
+    // triangular index -> (a, b), a >= b (integer arithmetic only)
+    const long t = blockIdx.x;
+    int a = (int)sqrtf(2.0f * (float)t);
     while ((long)(a + 1) * (a + 2) / 2 <= t) ++a;
     while ((long)a * (a + 1) / 2 > t) --a;
     int b = (int)(t - (long)a * (a + 1) / 2);
@@ -282,9 +284,9 @@ __global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, 
     const int i = sidx[e0 + a], j = sidx[e0 + b];
     const int nk = size[k], ni = size[i], nj = size[j];
     const int Mk = M[k];
-    const double2 *Aik = A + coff[k] + srow[e0 + a];                 // ld Mk
-    const double2 *Wkj = W + coff[k] + (int64_t)srow[e0 + b] * nk;   // ld nk
-    double2 *C;
+    const S *Aik = A + coff[k] + srow[e0 + a];                 // ld Mk
+    const S *Wkj = W + coff[k] + (int64_t)srow[e0 + b] * nk;   // ld nk
+    S *C;
     int ldc;
     if (i == j) {
         C = Ad + doff[i];
@@ -296,51 +298,47 @@ __global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, 
         ldc = M[j];
     }
     if (ni <= 32 && nj <= 32)
-        update_tile<TC, QC, 2>(As, Ws, Aik, Mk, Wkj, nk, ni, nj, C, ldc);
+        update_tile<S, QC, 2>(As, Ws, Aik, Mk, Wkj, nk, ni, nj, C, ldc);
     else
-        update_tile<TC, QC, 4>(As, Ws, Aik, Mk, Wkj, nk, ni, nj, C, ldc);
+        update_tile<S, QC, 4>(As, Ws, Aik, Mk, Wkj, nk, ni, nj, C, ldc);
 }
 
-cudaError_t setup_run(hm_ctx *h, int *bad_block)
+template <class S>
+static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *Dinv32, int *bad_block)
 {
     Plan &P = h->plan;
     cudaStream_t st = h->stream;
     cudaError_t e;
     *bad_block = -1;
-    if ((e = cudaMemsetAsync(h->d_A, 0, sizeof(double2) * P.coef_entries, st))) return e;
-    if ((e = cudaMemsetAsync(h->d_Ad, 0, sizeof(double2) * P.diag_entries, st))) return e;
+    if ((e = cudaMemsetAsync(A, 0, sizeof(S) * P.coef_entries, st))) return e;
+    if ((e = cudaMemsetAsync(Ad, 0, sizeof(S) * P.diag_entries, st))) return e;
     if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st))) return e;
-    HM_LAUNCH(h, K_SCATTER, k_scatter_near<<<(int)h->near_t.size(), 128, 0, st>>>((int)h->near_t.size(), h->d_near_t, h->d_near_s,
-                                                          h->d_near_off, h->d_near, h->d_leaf_ptr, h->d_pos,
-                                                          h->d_sptr, h->d_sidx, h->d_srow, h->d_M, h->d_coff,
-                                                          h->d_doff, h->d_A, h->d_Ad, h->d_err));
+    HM_LAUNCH(h, K_SCATTER,
+              k_scatter_near<S><<<(int)h->near_t.size(), 128, 0, st>>>(
+                  (int)h->near_t.size(), h->d_near_t, h->d_near_s, h->d_near_off, h->d_near, h->d_leaf_ptr, h->d_pos,
+                  h->d_sptr, h->d_sidx, h->d_srow, h->d_M, h->d_coff, h->d_doff, A, Ad, h->d_err));
     if ((e = cudaGetLastError())) return e;
     const size_t inv_smem = sizeof(double2) * (64 * 65 + 128);
-    const size_t panel_smem = sizeof(double2) * (2 * 64 * 65);
-    if ((e = cudaFuncSetAttribute(k_pivot_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem)))
+    const size_t panel_smem = sizeof(S) * (2 * 64 * 65);
+    if ((e = cudaFuncSetAttribute(k_pivot_inverse<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem)))
+    if ((e = cudaFuncSetAttribute(k_panel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem)))
         return e;
     for (int k = 0; k < P.nb; ++k) {
         int nk = P.size[k];
-        HM_LAUNCH(h, K_PIVOT, k_pivot_inverse<<<1, 256, sizeof(double2) * (nk * (nk + 1) + 2 * nk), st>>>(k, h->d_size, h->d_doff, h->d_Ad,
-                                                                               h->d_Dinv, h->d_err));
+        HM_LAUNCH(h, K_PIVOT,
+                  k_pivot_inverse<S><<<1, 256, sizeof(double2) * (nk * (nk + 1) + 2 * nk), st>>>(
+                      k, h->d_size, h->d_doff, Ad, h->d_Dinv, Dinv32, h->d_err));
         int ns = P.sptr[k + 1] - P.sptr[k];
         if (ns > 0) {
             int Mk = P.M[k];
-            HM_LAUNCH(h, K_PANEL, k_panel<<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff, h->d_Dinv, h->d_A,
-                                                   h->d_W));
+            HM_LAUNCH(h, K_PANEL,
+                      k_panel<S><<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff,
+                                                                          DinvS, A, W));
             long nt = (long)ns * (ns + 1) / 2;
-            if (h->opts.precision == 1)
-                HM_LAUNCH(h, K_UPDATE,
-                          k_update<float2><<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx,
-                                                                         h->d_srow, h->d_M, h->d_coff, h->d_doff,
-                                                                         h->d_W, h->d_A, h->d_Ad));
-            else
-                HM_LAUNCH(h, K_UPDATE,
-                          k_update<double2><<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx,
-                                                                          h->d_srow, h->d_M, h->d_coff, h->d_doff,
-                                                                          h->d_W, h->d_A, h->d_Ad));
+            HM_LAUNCH(h, K_UPDATE,
+                      k_update<S><<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx, h->d_srow,
+                                                                h->d_M, h->d_coff, h->d_doff, W, A, Ad));
         }
         if ((e = cudaGetLastError())) return e;
     }
@@ -350,6 +348,13 @@ cudaError_t setup_run(hm_ctx *h, int *bad_block)
     if (herr == 0x7fffffff) return cudaErrorInvalidValue;   // plan / pattern mismatch
     if (herr > 0) *bad_block = herr - 1;
     return cudaSuccess;
+}
+
+cudaError_t setup_run(hm_ctx *h, int *bad_block)
+{
+    if (h->opts.precision == 1)
+        return setup_typed<float2>(h, h->d_A32, h->d_Ad32, h->d_W32, h->d_Dinv32, h->d_Dinv32, bad_block);
+    return setup_typed<double2>(h, h->d_A, h->d_Ad, h->d_W, h->d_Dinv, nullptr, bad_block);
 }
 
 }  // namespace hm
