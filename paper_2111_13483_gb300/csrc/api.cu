@@ -198,6 +198,8 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
         (e = upload(h, &h->d_p1_ptr, F.p1_ptr)) || (e = upload(h, &h->d_p1_off, F.p1_off)) ||
         (e = upload(h, &h->d_p1_ld, F.p1_ld)) || (e = upload(h, &h->d_p1_rank, F.p1_rank)) ||
         (e = upload(h, &h->d_p1_row, F.p1_row)) || (e = upload(h, &h->d_p1_isv, F.p1_isv)) ||
+        (e = upload(h, &h->d_seg_ptr, F.seg_ptr)) || (e = upload(h, &h->d_segs, F.segs)) ||
+        (e = upload(h, &h->d_seg_kcum, F.seg_kcum)) || (e = upload(h, &h->d_part_ptr, F.part_ptr)) ||
         (e = upload(h, &h->d_flptr, F.lptr)) ||
         (e = upload(h, &h->d_flent, F.lent)) || (e = upload(h, &h->d_nptr, F.nptr)) ||
         (e = upload(h, &h->d_nent, F.nent)) || (e = upload(h, &h->d_leaf_ptr, h->leaf_ptr)) ||

@@ -11,8 +11,10 @@
 // product (tile.cuh); t and s are stored interleaved like u.
 // Phase 2 (k_far_y): one CTA per leaf accumulates, in the order of the leaf's list of
 // covering far blocks, U_b t_b (row side), V_b s_b (column side), B u (dense row side) and
-// B^T u (dense column side) for the leaf's rows; the list is cut into contraction segments
-// of at most 64 that are staged in shared memory in chunks.  Every output sums its terms in
+// B^T u (dense column side) for the leaf's rows; the host plan cuts the list into
+// contraction segments of at most 32, which are staged in shared memory in chunks.  Each
+// leaf's list is split into FAR_PARTS consecutive parts of about equal length, one CTA each
+// (so that the uneven leaves spread over all SMs); k_far_sum adds the parts in order.  Every output sums its terms in
 // one fixed order, so results are deterministic and do not depend on how many right-hand
 // sides share the launch.
 #include "cplx.cuh"
@@ -20,6 +22,8 @@
 #include "tile.cuh"
 
 namespace hm {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 namespace {
 constexpr int SEG = 64;   // longest staged contraction segment
@@ -84,118 +88,106 @@ __global__ void __launch_bounds__(256) k_far_t(const int *task_lo, const int *ta
     }
 }
 
-// Contraction source of one incidence entry of leaf rows [a, a + ni): coefficient
-// F(i, k) = Fb[i * fi + k * fk] and vector Y(k, r) = Yb[k * nrhs + r], k < K.
-template <class T> struct FarSeg {
-    const T *Fb, *Yb;
-    int64_t fi, fk;
-    int K;
-};
-
-template <class T>
-__device__ __forceinline__ FarSeg<T> far_seg(int ent, int a, const int *r0, const int *r1, const int *c0,
-                                             const int *c1, const int *rank, const int64_t *uoff,
-                                             const int64_t *voff, const int64_t *toff, const T *U, const T *V,
-                                             const T *t, const T *s, const T *u, int nrhs)
+// Phase 2: one CTA per leaf over the leaf's segments (FarSegD, list order, len <= 32).
+// Consecutive segments form a chunk while their summed length fits half the staging buffer;
+// the chunk's coefficient rows and vector rows are stacked into one contraction, so a
+// single tile product per chunk keeps every output's order (segment by segment, k
+// ascending).  Chunks are copied with cp.async by one warp per segment into the two halves
+// of the buffer in turn, so the copy of the next chunk overlaps the product of the current.
+template <class T> __device__ __forceinline__ void cp_async_el(T *dst, const T *src)
 {
-    const int b = ent >> 2, kind = ent & 3;
-    const int m = r1[b] - r0[b], nc = c1[b] - c0[b];
-    FarSeg<T> g;
-    if (kind == 0) {          // low rank, leaf in the row range: U_b t_b
-        g.Fb = U + uoff[b] + (a - r0[b]);
-        g.fi = 1;
-        g.fk = m;
-        g.Yb = t + toff[b] * nrhs;
-        g.K = rank[b];
-    } else if (kind == 1) {   // low rank, leaf in the column range: V_b s_b
-        g.Fb = V + voff[b] + (a - c0[b]);
-        g.fi = 1;
-        g.fk = nc;
-        g.Yb = s + toff[b] * nrhs;
-        g.K = rank[b];
-    } else if (kind == 2) {   // dense, row side: B u[c-range]
-        g.Fb = U + uoff[b] + (a - r0[b]);
-        g.fi = 1;
-        g.fk = m;
-        g.Yb = u + (int64_t)c0[b] * nrhs;
-        g.K = nc;
-    } else {                  // dense, column side: B^T u[r-range]
-        g.Fb = U + uoff[b] + (int64_t)(a - c0[b]) * m;
-        g.fi = m;
-        g.fk = 1;
-        g.Yb = u + (int64_t)r0[b] * nrhs;
-        g.K = m;
-    }
-    return g;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 template <class T, int TR, int TC, int NT>
-__global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, const int *lptr, const int *lent,
-                                               const int *r0, const int *r1, const int *c0, const int *c1,
-                                               const int *rank, const int64_t *uoff, const int64_t *voff,
-                                               const int64_t *toff, const T *U, const T *V, const T *t,
-                                               const T *s, const T *u, const int *cl2new, int n, int nrhs, T *y,
-                                               int budget)
+__global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, const int *part_ptr, const int *kcum,
+                                               const FarSegD *segs, const T *U, const T *V, const T *t, const T *s,
+                                               const T *u, const int *cl2new, int n, int nrhs, T *part, int budget)
 {
     extern __shared__ unsigned char smraw[];
-    T *buf = (T *)smraw;
-    const int l = blockIdx.x;
+    const int l = blockIdx.x / FAR_PARTS, pp = blockIdx.x % FAR_PARTS;
     if (l >= nl) return;
     const int a = leaf_ptr[l], ni = leaf_ptr[l + 1] - a;
     const int nrt = (ni + TR - 1) / TR, ntiles = nrt * ((nrhs + TC - 1) / TC);
     const int ldw = stage_ldw(ni, TR), ldr = stage_ldr(nrhs, TC);
+    const int half = budget / 2, kmax = half / (ldw + ldr);   // >= 32 for ni <= 64
+    T *const bufs[2] = {(T *)smraw, (T *)smraw + half};
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     Tile<T, TR, TC, NT> acc;
     tile_load(acc, (const T *)nullptr, 0, 0, ni, nrhs, nrt, ntiles);
-    const int p1 = lptr[l + 1];
-    int p = lptr[l], k0 = 0;
-    while (p < p1) {
-        // one chunk: segments (entry, [k0, k0 + len)) while they fit the budget
-        int used = 0, pp = p, kk = k0;
-        for (int nseg = 0; pp < p1 && nseg < 32;) {
-            const FarSeg<T> g = far_seg(lent[pp], a, r0, r1, c0, c1, rank, uoff, voff, toff, U, V, t, s, u, nrhs);
-            if (kk >= g.K) {   // entry done (or empty)
-                ++pp;
-                kk = 0;
-                continue;
+    const int w1 = part_ptr[blockIdx.x + 1];
+    // segments [p, p + count) of the chunk starting at p: those whose stacked length fits kmax
+    auto chunk_count = [&](int p) {
+        const int q = p + threadIdx.x;
+        const bool fit = q < w1 && kcum[q + 1] - kcum[p] <= kmax;
+        return __syncthreads_count(fit);
+    };
+    auto stage = [&](int p, int cnt, T *buf) {
+        const int k0 = kcum[p];
+        T *Wst = buf, *Yst = buf + kmax * ldw;
+        for (int q = wp; q < cnt; q += nwarp) {
+            const FarSegD g = segs[p + q];
+            const int kb = kcum[p + q] - k0;
+            const T *F = ((g.src & 1) ? V : U) + g.foff;
+            const int ys = g.src >> 1;
+            const T *Yb = (ys == 0 ? t : (ys == 1 ? s : u)) + g.yrow * nrhs;
+            for (int k = 0; k < g.len; ++k) {
+                for (int i = lane; i < ni; i += 32)
+                    cp_async_el(Wst + (kb + k) * ldw + i, F + (int64_t)i * g.fi + (int64_t)k * g.fk);
+                for (int r = lane; r < nrhs; r += 32) cp_async_el(Yst + (kb + k) * ldr + r, Yb + (int64_t)k * nrhs + r);
             }
-            const int len = min(SEG, g.K - kk);
-            const int need = stage_need(ni, len, nrhs, TR, TC);
-            if (nseg > 0 && used + need > budget) break;
-            T *Ws = buf + used, *Ys = Ws + len * ldw;
-            if (g.fi == 1)
-                stage_copy(len * ni, [&](int e) { return g.Fb[e % ni + (int64_t)(kk + e / ni) * g.fk]; },
-                           [&](int e, T v) { Ws[(e / ni) * ldw + e % ni] = v; });
-            else
-                stage_copy(len * ni, [&](int e) { return g.Fb[(int64_t)(e / len) * g.fi + kk + e % len]; },
-                           [&](int e, T v) { Ws[(e % len) * ldw + e / len] = v; });
-            const T *yb = g.Yb + (int64_t)kk * nrhs;
-            stage_copy(len * nrhs, [&](int e) { return yb[e]; },
-                       [&](int e, T v) { Ys[(e / nrhs) * ldr + e % nrhs] = v; });
-            used += need;
-            ++nseg;
-            kk += len;
         }
-        __syncthreads();
-        // replay the chunk's segments in order
-        int off = 0;
-        while (p != pp || k0 != kk) {
-            const FarSeg<T> g = far_seg(lent[p], a, r0, r1, c0, c1, rank, uoff, voff, toff, U, V, t, s, u, nrhs);
-            if (k0 >= g.K) {
-                ++p;
-                k0 = 0;
-                continue;
-            }
-            const int len = min(SEG, g.K - k0);
-            tile_mac<false>(acc, buf + off, ldw, buf + off + len * ldw, ldr, 1, len, nrt, ntiles);
-            off += stage_need(ni, len, nrhs, TR, TC);
-            k0 += len;
+        cp_async_commit();
+        return kcum[p + cnt] - k0;
+    };
+    int p = part_ptr[blockIdx.x];
+    if (p < w1) {
+        int cnt = chunk_count(p), klen = stage(p, cnt, bufs[0]);
+        for (int it = 0;; ++it) {
+            const int pn = p + cnt;
+            int cntn = 0, klenn = 0;
+            if (pn < w1) {
+                cntn = chunk_count(pn);
+                klenn = stage(pn, cntn, bufs[(it + 1) & 1]);
+                cp_async_wait<1>();
+            } else
+                cp_async_wait<0>();
+            __syncthreads();
+            T *buf = bufs[it & 1];
+            tile_mac<false>(acc, buf, ldw, buf + kmax * ldw, ldr, 1, klen, nrt, ntiles);
+            __syncthreads();
+            if (pn >= w1) break;
+            p = pn;
+            cnt = cntn;
+            klen = klenn;
         }
-        __syncthreads();
     }
-    tile_store(acc, y + cl2new[a], 1, n, ni, nrhs, nrt, ntiles);
+    tile_store(acc, part + (size_t)pp * n * nrhs + cl2new[a], 1, n, ni, nrhs, nrt, ntiles);
 }
 
-static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+// y = sum of the FAR_PARTS partial products, added in part order
+template <class T> __global__ void k_far_sum(int64_t len, const T *part, T *y)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    T v = part[e];
+    for (int p = 1; p < FAR_PARTS; ++p) {
+        const T w = part[p * len + e];
+        v.x += w.x;
+        v.y += w.y;
+    }
+    y[e] = v;
+}
+
 
 namespace {
 template <class T> struct FarLaunch {
@@ -226,11 +218,13 @@ template <class T> struct FarLaunch {
                       (k_far_t<T, TR, TC, NT><<<ntask, 256, smem, h->stream>>>(
                           h->d_p1_lo, h->d_p1_hi, h->d_p1_ptr, h->d_p1_off, h->d_p1_ld, h->d_p1_rank, h->d_p1_row,
                           h->d_p1_isv, U, V, ucl, nrhs, t, s)));
+        T *part = (T *)h->d_farpart;
         HM_LAUNCH(h, K_FAR2,
-                  (k_far_y<T, TR, TC, NT><<<h->nl, 256, smem, h->stream>>>(
-                      h->nl, h->d_leaf_ptr, h->d_flptr, h->d_flent, h->d_far_r0, h->d_far_r1, h->d_far_c0,
-                      h->d_far_c1, h->d_far_rank, h->d_far_uoff, h->d_far_voff, h->d_far_toff, U, V, t, s, ucl,
-                      h->d_cl2new, n, nrhs, y, budget)));
+                  (k_far_y<T, TR, TC, NT><<<h->nl * FAR_PARTS, 256, smem, h->stream>>>(
+                      h->nl, h->d_leaf_ptr, h->d_part_ptr, h->d_seg_kcum, h->d_segs, U, V, t, s, ucl, h->d_cl2new,
+                      n, nrhs, part, budget)));
+        const int64_t len = (int64_t)n * nrhs;
+        HM_LAUNCH(h, K_FAR2, k_far_sum<T><<<nblk(len, 256), 256, 0, h->stream>>>(len, part, y));
         return cudaGetLastError();
     }
 };

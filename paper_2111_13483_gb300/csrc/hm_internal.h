@@ -79,6 +79,16 @@ struct Plan {
 
 // far-field incidence lists (cluster order): per leaf l, entries (b << 2 | kind), kind
 // 0 = low-rank row side, 1 = low-rank column side, 2 = dense row side, 3 = dense column side
+// One contraction segment of a leaf's far-field rows (phase 2 of the far product):
+// F(i, k) = Fbase[foff + i * fi + k * fk] (Fbase = U, or V when src & 1), and
+// Y(k, r) = Ybase[(yrow + k) * nrhs + r] (Ybase = t, s, u for src >> 1 = 0, 1, 2), k < len.
+struct FarSegD {
+    int64_t foff, yrow;
+    int fi, fk, len, src;
+};
+
+constexpr int FAR_PARTS = 4;
+
 struct FarPlan {
     int nf = 0;
     int64_t entries = 0;
@@ -91,6 +101,13 @@ struct FarPlan {
     // column stride p1_ld, p1_rank columns, output rows p1_row.. of t (isv) or s
     std::vector<int> p1_lo, p1_hi, p1_ptr, p1_ld, p1_rank, p1_row, p1_isv;
     std::vector<int64_t> p1_off;
+    // phase-2 segments per leaf: seg_ptr[l]..seg_ptr[l+1] in the order of the leaf's list
+    // (len <= 32 each); seg_kcum[q] = sum of len over the segments before q
+    std::vector<int> seg_ptr, seg_kcum;
+    std::vector<FarSegD> segs;
+    // each leaf's segments in FAR_PARTS consecutive parts of about equal contraction length:
+    // part (l, p) covers segments part_ptr[l*FAR_PARTS + p] .. part_ptr[l*FAR_PARTS + p + 1]
+    std::vector<int> part_ptr;
     // near-field incidence lists (cluster order) for Z_N products: per leaf l, entries
     // (b << 1 | side), side 0 = l is the row leaf t, 1 = l is the column leaf s (t != s)
     std::vector<int> nptr, nent;
@@ -129,6 +146,8 @@ struct hm_ctx {
     int *d_p1_lo = nullptr, *d_p1_hi = nullptr, *d_p1_ptr = nullptr, *d_p1_ld = nullptr, *d_p1_rank = nullptr,
         *d_p1_row = nullptr, *d_p1_isv = nullptr;
     int64_t *d_p1_off = nullptr;
+    int *d_seg_ptr = nullptr, *d_seg_kcum = nullptr, *d_part_ptr = nullptr;
+    hm::FarSegD *d_segs = nullptr;
     int *d_leaf_ptr = nullptr, *d_perm = nullptr;
     int *d_new2cl = nullptr, *d_cl2new = nullptr, *d_new2orig = nullptr, *d_pos = nullptr;
     // device: plan
@@ -152,6 +171,8 @@ struct hm_ctx {
     double2 *d_t = nullptr, *d_s = nullptr;  // far rank vectors (per rhs column)
     int t_cols = 0;
     double2 *d_work = nullptr;               // operator scratch vectors
+    void *d_farpart = nullptr;               // far-field partial sums (FAR_PARTS x n x nrhs)
+    size_t farpart_bytes = 0;
     int work_cols = 0;
     // complex-FP32 factors of the mixed-precision setup (D_k, W, D_k^{-1}; D_k^{-1} is also
     // kept in FP64 in d_Dinv) and FP32 copies of the far factors for the inner operator

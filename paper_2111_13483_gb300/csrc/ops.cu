@@ -410,6 +410,14 @@ cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs)
         if ((e = h->arena.alloc((void **)&h->d_s, sizeof(double2) * tl * nrhs))) return e;
         h->t_cols = nrhs;
     }
+    const size_t fpb = (size_t)FAR_PARTS * n * nrhs * sizeof(double2);
+    if (h->farpart_bytes < fpb) {
+        if (h->d_farpart) h->arena.release(h->d_farpart, 0);
+        h->d_farpart = nullptr;
+        h->farpart_bytes = 0;
+        if ((e = h->arena.alloc(&h->d_farpart, fpb))) return e;
+        h->farpart_bytes = fpb;
+    }
     if (h->work_cols < 3 * nrhs) {
         if (h->d_work) h->arena.release(h->d_work, 0);
         h->d_work = nullptr;

@@ -367,6 +367,53 @@ void plan_far(hm_ctx *h)
     for (int l = 0; l < nl; ++l) F.nptr[l + 1] = F.nptr[l] + (int)nl_lists[l].size();
     F.nent.clear();
     for (int l = 0; l < nl; ++l) F.nent.insert(F.nent.end(), nl_lists[l].begin(), nl_lists[l].end());
+    // phase-2 segments: every list entry of leaf l cut into contraction pieces of <= 32
+    F.seg_ptr.assign(nl + 1, 0);
+    F.segs.clear();
+    for (int l = 0; l < nl; ++l) {
+        const int a = h->leaf_ptr[l];
+        for (int p = F.lptr[l]; p < F.lptr[l + 1]; ++p) {
+            const int b = F.lent[p] >> 2, kind = F.lent[p] & 3;
+            const int64_t m = h->far_r1[b] - h->far_r0[b], c = h->far_c1[b] - h->far_c0[b];
+            FarSegD g{};
+            int K;
+            if (kind == 0) {
+                g = {h->far_uoff[b] + (a - h->far_r0[b]), F.toff[b], 1, (int)m, 0, 0};
+                K = h->far_rank[b];
+            } else if (kind == 1) {
+                g = {h->far_voff[b] + (a - h->far_c0[b]), F.toff[b], 1, (int)c, 0, 1 | (1 << 1)};
+                K = h->far_rank[b];
+            } else if (kind == 2) {
+                g = {h->far_uoff[b] + (a - h->far_r0[b]), h->far_c0[b], 1, (int)m, 0, 2 << 1};
+                K = (int)c;
+            } else {
+                g = {h->far_uoff[b] + (int64_t)(a - h->far_c0[b]) * m, h->far_r0[b], (int)m, 1, 0, 2 << 1};
+                K = (int)m;
+            }
+            for (int k0 = 0; k0 < K; k0 += 32) {
+                FarSegD q = g;
+                q.foff += (int64_t)k0 * g.fk;
+                q.yrow += k0;
+                q.len = std::min(32, K - k0);
+                F.segs.push_back(q);
+            }
+        }
+        F.seg_ptr[l + 1] = (int)F.segs.size();
+    }
+    F.seg_kcum.assign(F.segs.size() + 1, 0);
+    for (size_t q = 0; q < F.segs.size(); ++q) F.seg_kcum[q + 1] = F.seg_kcum[q] + F.segs[q].len;
+    F.part_ptr.assign((size_t)nl * FAR_PARTS + 1, 0);
+    for (int l = 0; l < nl; ++l) {
+        const int b = F.seg_ptr[l], e = F.seg_ptr[l + 1];
+        const int64_t K = F.seg_kcum[e] - F.seg_kcum[b];
+        int q = b;
+        for (int p = 0; p < FAR_PARTS; ++p) {
+            F.part_ptr[(size_t)l * FAR_PARTS + p] = q;
+            const int64_t target = K * (p + 1) / FAR_PARTS;
+            while (q < e && F.seg_kcum[q] - F.seg_kcum[b] < target) ++q;
+        }
+    }
+    F.part_ptr[(size_t)nl * FAR_PARTS] = (int)F.segs.size();
     // rank-vector tasks: group the factor columns by the range they contract over
     // (V_b over the column range for t_b, U_b over the row range for s_b), 64 per task,
     // larger tasks first
