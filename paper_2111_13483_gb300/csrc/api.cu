@@ -378,6 +378,7 @@ void hmat_destroy(hm_handle h)
     cudaSetDevice(h->dev);
     cudaStreamSynchronize(h->stream);
     h->prof.destroy();
+    sweep_tune_release(h);
     h->arena.release_all();
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;

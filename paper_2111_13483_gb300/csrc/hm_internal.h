@@ -113,6 +113,16 @@ struct FarPlan {
     std::vector<int> nptr, nent;
 };
 
+// Online choice of the number of independent column groups of a sweep launch, per
+// precision, direction and width class: candidates are timed on real calls (every
+// candidate computes the same result) and the fastest per column is kept.
+constexpr int SWEEP_GMAX = 4;
+struct SweepTune {
+    int ncand = 0, trial = 0, best = 0;
+    int cand[3] = {0, 0, 0}, width[3] = {0, 0, 0};
+    cudaEvent_t ev[6] = {};
+};
+
 }  // namespace hm
 
 // ---- the handle -------------------------------------------------------------------------
@@ -180,6 +190,7 @@ struct hm_ctx {
     float2 *d_t32 = nullptr, *d_s32 = nullptr, *d_work32 = nullptr;
     int t32_cols = 0;
     bool batch_open = false;   // an hm_batch holds this handle
+    hm::SweepTune sweep_tune[2][2][5];   // [FP32][forward][width class]
 };
 
 // Launch wrapper: counts every launch by kernel class and, when profiling is on, brackets
@@ -214,6 +225,7 @@ cudaError_t z_apply_orig(hm_ctx *h, const double2 *x, double2 *y, int nrhs);
 template <class T>
 cudaError_t far_product(hm_ctx *h, const T *U, const T *V, T *t, T *s, const T *ucl, T *y, int nrhs);
 cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs);
+void sweep_tune_release(hm_ctx *h);
 int gmres_solve(hm_ctx *h, const double2 *dV, int nrhs, int64_t ldv, double tol, int restart, int maxit,
                 double2 *dI, int64_t ldi, int *iters, double *relres);
 }  // namespace hm

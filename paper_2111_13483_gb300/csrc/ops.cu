@@ -151,38 +151,43 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
 
 }  // namespace
 
+// The columns are split into G groups of gw (the last may be narrower), each an independent
+// chain with its own ready flags; ticket t takes block t / G (in sweep order) of group t % G.
+
 // y = L^{-1} x : y_i = x_i - sum_{k < i, i in S_k} W_ki^T y_k   (Eq. 23)
 template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, const int *boff, const int *rptr,
                                                    const int *ridx, const int *rcol, const int64_t *coff,
-                                                   const T *W, const T *x, T *y, int n, int nrhs, int budget,
-                                                   int *flags, int epoch, int *ticket, int *err)
+                                                   const T *W, const T *x, T *y, int n, int nrhs, int G, int gw,
+                                                   int budget, int *flags, int epoch, int *ticket, int *err)
 {
     extern __shared__ unsigned char smraw[];
-    __shared__ int s_i;
-    if (threadIdx.x == 0) s_i = atomicAdd(ticket, 1);
+    __shared__ int s_t;
+    if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
-    const int i = s_i;
+    const int i = s_t / G, g = s_t % G;
     if (i >= nb) return;
-    sweep_row<T, TR, TC, NT, true>(i, size[i], size, boff, rptr, ridx, rcol, coff, W, x, y, n, nrhs, budget, flags,
-                                   epoch, err, (T *)smraw);
+    const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
+    sweep_row<T, TR, TC, NT, true>(i, size[i], size, boff, rptr, ridx, rcol, coff, W, x + (int64_t)c0 * n,
+                                   y + (int64_t)c0 * n, n, nc, budget, flags + g * nb, epoch, err, (T *)smraw);
 }
 
 // y = L^{-T} x : y_k = x_k - sum_{j in S_k} W_kj y_j   (Eq. 24); j walked downwards
 template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, const int *boff, const int *sptr,
                                                    const int *sidx, const int *srow, const int64_t *coff,
-                                                   const T *W, const T *x, T *y, int n, int nrhs, int budget,
-                                                   int *flags, int epoch, int *ticket, int *err)
+                                                   const T *W, const T *x, T *y, int n, int nrhs, int G, int gw,
+                                                   int budget, int *flags, int epoch, int *ticket, int *err)
 {
     extern __shared__ unsigned char smraw[];
-    __shared__ int s_k;
-    if (threadIdx.x == 0) s_k = nb - 1 - atomicAdd(ticket, 1);
+    __shared__ int s_t;
+    if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
-    const int k = s_k;
+    const int k = nb - 1 - s_t / G, g = s_t % G;
     if (k < 0) return;
-    sweep_row<T, TR, TC, NT, false>(k, size[k], size, boff, sptr, sidx, srow, coff, W, x, y, n, nrhs, budget, flags,
-                                    epoch, err, (T *)smraw);
+    const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
+    sweep_row<T, TR, TC, NT, false>(k, size[k], size, boff, sptr, sidx, srow, coff, W, x + (int64_t)c0 * n,
+                                    y + (int64_t)c0 * n, n, nc, budget, flags + g * nb, epoch, err, (T *)smraw);
 }
 
 // dst[i*nrhs + r] = src[idx[i] + r*n]   (right-hand sides interleaved)
@@ -314,16 +319,16 @@ static OpData<float2> data32(hm_ctx *h)
 // Widest column batch one sweep launch takes (wider requests are split into slices).
 template <class T> static int max_cols() { return sizeof(T) == 16 ? 16 : 64; }
 
-// Register tile per width: (TR, TC, NT) = (1, 1, 1) up to 4 columns, (2, 2, 1) up to 16,
-// (2, 4, 2) up to 64 (complex FP32 only); 256 threads cover every output tile of a 64-row
-// block.  The shared memory of a CTA holds one chunk: at least one 64 x 64 coefficient
-// block with its vector block.
+// Register tile per group width: (TR, TC, NT) = (1, 1, 1) up to 4 columns, (2, 2, 1) up
+// to 16, (2, 4, 2) up to 64 (complex FP32 only); 256 threads cover every output tile of a
+// 64-row block.  The shared memory of a CTA holds one chunk: at least one 64 x 64
+// coefficient block with its vector block.
 template <class T, int TR, int TC, int NT>
-static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs, int ep,
-                               int maxw)
+static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs, int G,
+                               int gw, int ep, int maxw)
 {
     Plan &P = h->plan;
-    const int budget = stage_need(64, 64, nrhs, TR, TC);
+    const int budget = stage_need(64, 64, gw, TR, TC);
     const size_t smem = sizeof(T) * (size_t)budget;
     static bool attr = false;
     if (!attr) {
@@ -332,17 +337,64 @@ static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, cons
         cudaFuncSetAttribute(k_sweep_bwd<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         attr = true;
     }
+    const unsigned grid = (unsigned)(P.nb * G);
     if (forward)
         HM_LAUNCH(h, K_SWEEP_FWD,
-                  (k_sweep_fwd<T, TR, TC, NT><<<P.nb, 256, smem, h->stream>>>(
-                      P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs,
-                      budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+                  (k_sweep_fwd<T, TR, TC, NT><<<grid, 256, smem, h->stream>>>(
+                      P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs, G,
+                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
     else
         HM_LAUNCH(h, K_SWEEP_BWD,
-                  (k_sweep_bwd<T, TR, TC, NT><<<P.nb, 256, smem, h->stream>>>(
-                      P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs,
-                      budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+                  (k_sweep_bwd<T, TR, TC, NT><<<grid, 256, smem, h->stream>>>(
+                      P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs, G,
+                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
     return cudaGetLastError();
+}
+
+static int width_class(int w) { return w <= 4 ? 0 : w <= 8 ? 1 : w <= 16 ? 2 : w <= 32 ? 3 : 4; }
+
+// Number of column groups for a sweep of nrhs columns: the tuned choice of the width class,
+// or the next untried candidate (then *tu / *slot let the caller time the launch).
+static int sweep_groups(hm_ctx *h, bool fp32, bool forward, int nrhs, SweepTune **tu, int *slot)
+{
+    SweepTune &t = h->sweep_tune[fp32][forward][width_class(nrhs)];
+    *tu = nullptr;
+    if (t.best) return t.best;
+    if (t.ncand == 0)
+        for (int G = 1; G <= SWEEP_GMAX; G *= 2)
+            if (G == 1 || (nrhs + G - 1) / G >= 4) t.cand[t.ncand++] = G;
+    if (t.ncand == 1) return t.best = 1;
+    if (t.trial < t.ncand) {
+        if (!t.ev[0])
+            for (cudaEvent_t &e : t.ev) cudaEventCreate(&e);
+        *tu = &t;
+        *slot = t.trial;
+        t.width[t.trial] = nrhs;
+        return t.cand[t.trial++];
+    }
+    // every candidate has run once: keep the fastest per column
+    float best = 0;
+    for (int c = 0; c < t.ncand; ++c) {
+        float ms = 0;
+        cudaEventSynchronize(t.ev[2 * c + 1]);
+        cudaEventElapsedTime(&ms, t.ev[2 * c], t.ev[2 * c + 1]);
+        ms /= (float)t.width[c];
+        if (c == 0 || ms < best) {
+            best = ms;
+            t.best = t.cand[c];
+        }
+    }
+    for (cudaEvent_t &e : t.ev) cudaEventDestroy(e), e = nullptr;
+    return t.best;
+}
+
+void sweep_tune_release(hm_ctx *h)
+{
+    for (auto &a : h->sweep_tune)
+        for (auto &b : a)
+            for (SweepTune &t : b)
+                for (cudaEvent_t &e : t.ev)
+                    if (e) cudaEventDestroy(e), e = nullptr;
 }
 
 template <class T>
@@ -351,12 +403,19 @@ static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_ticket, 0, sizeof(int), h->stream))) return e;
     const int ep = ++h->epoch;
-    if (nrhs <= 4) return sweep_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, ep, 4);
-    if constexpr (sizeof(T) == 16) return sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, ep, 16);
+    SweepTune *tu;
+    int slot = 0;
+    const int G = sweep_groups(h, sizeof(T) == 8, forward, nrhs, &tu, &slot);
+    const int gw = (nrhs + G - 1) / G;
+    if (tu) cudaEventRecord(tu->ev[2 * slot], h->stream);
+    if (gw <= 4) e = sweep_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
+    else if constexpr (sizeof(T) == 16) e = sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
     else {
-        if (nrhs <= 16) return sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, ep, 16);
-        return sweep_shape<T, 2, 4, 2>(h, d, forward, x, y, nrhs, ep, 64);
+        if (gw <= 16) e = sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
+        else e = sweep_shape<T, 2, 4, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 64);
     }
+    if (tu) cudaEventRecord(tu->ev[2 * slot + 1], h->stream);
+    return e;
 }
 
 // y (solve order) = Z_F x (solve order); ucl receives the cluster-order copy of x with the
@@ -397,8 +456,8 @@ cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs)
     cudaError_t e;
     const int n = h->plan.n;
     if (!h->d_flags) {
-        if ((e = h->arena.alloc((void **)&h->d_flags, sizeof(int) * h->plan.nb))) return e;
-        if ((e = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->plan.nb, h->stream))) return e;
+        if ((e = h->arena.alloc((void **)&h->d_flags, sizeof(int) * h->plan.nb * SWEEP_GMAX))) return e;
+        if ((e = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->plan.nb * SWEEP_GMAX, h->stream))) return e;
         h->epoch = 0;
     }
     const size_t tl = std::max<int64_t>(1, h->fplan.tlen);
