@@ -232,6 +232,18 @@ int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, 
  */
 int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
 
+/*
+ * Schedule of the block-triangular sweeps (Eqs. 23, 24): the right-hand-side columns of a
+ * launch are split into `groups` (1, 2 or 4) independent chains, and `kind` selects how a
+ * chain is computed: 1 = one CTA per block row; 2 = one CTA per two consecutive block rows;
+ * 3 = one chain CTA walks all block rows adding the dependencies of the last four rows
+ * from shared memory, while one helper CTA per block row adds all older dependencies.
+ * Every schedule gives bitwise the same result.  (0, 0) -- the default -- lets the library
+ * time the candidates on its first calls of each width and keep the fastest.  Kinds 2 and
+ * 3 apply to groups of at most 16 columns (kind 1 otherwise).  HM_EINVAL for other values.
+ */
+int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind);
+
 /* ---- continuous batching (serving) ---------------------------------------------------- */
 
 /*

@@ -211,6 +211,12 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
         (e = upload(h, &h->d_M, P.M)) || (e = upload(h, &h->d_coff, P.coff)) || (e = upload(h, &h->d_doff, P.doff)) ||
         (e = upload(h, &h->d_rptr, P.rptr)) || (e = upload(h, &h->d_ridx, P.ridx)) ||
         (e = upload(h, &h->d_rcol, P.rcol)) || (e = upload(h, &h->d_fill_e, P.fill_e)) ||
+        (e = upload(h, &h->d_xptr[0], P.xptr[0])) || (e = upload(h, &h->d_xdep[0], P.xdep[0])) ||
+        (e = upload(h, &h->d_xoff[0], P.xoff[0])) || (e = upload(h, &h->d_xint[0], P.xint[0])) ||
+        (e = upload(h, &h->d_xptr[1], P.xptr[1])) || (e = upload(h, &h->d_xdep[1], P.xdep[1])) ||
+        (e = upload(h, &h->d_xoff[1], P.xoff[1])) || (e = upload(h, &h->d_xint[1], P.xint[1])) ||
+        (e = upload(h, &h->d_rec[0], P.rec[0])) || (e = upload(h, &h->d_reccol[0], P.reccol[0])) ||
+        (e = upload(h, &h->d_rec[1], P.rec[1])) || (e = upload(h, &h->d_reccol[1], P.reccol[1])) ||
         (e = upload(h, &h->d_fill_k, P.fill_k))) {
         int s = cuda_fail(h, e, "hmat_create upload");
         std::fprintf(stderr, "hmat_create: %s\n", h->err.c_str());
@@ -455,6 +461,19 @@ int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out)
         (e = cudaStreamSynchronize(h->stream)))
         return cuda_fail(h, e, "hm_get_block");
     for (size_t i = 0; i < cnt; ++i) out[i] = hm_c128{(double)tmp[i].x, (double)tmp[i].y};
+    return HM_OK;
+}
+
+int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind)
+{
+    if (!h) return HM_EINVAL;
+    if (groups == 0 && kind == 0) {
+        h->sweep_fixed = 0;
+        return HM_OK;
+    }
+    if ((groups != 1 && groups != 2 && groups != 4) || (kind != 1 && kind != SWEEP_SR && kind != 3))
+        return HM_EINVAL;
+    h->sweep_fixed = groups | (kind << 4);
     return HM_OK;
 }
 

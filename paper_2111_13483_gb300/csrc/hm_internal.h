@@ -49,6 +49,9 @@ struct Prof {
 };
 
 // ---- host plan: solve order, symbolic fill, storage layout ---------------------------
+constexpr int SWEEP_SR = 2;   // blocks per super-row of the sweeps
+constexpr int SWEEP_T = 4;    // recent dependencies handled by the chain CTA
+
 struct Plan {
     int nb = 0, n = 0;
     std::vector<int> order;      // block p -> leaf
@@ -71,14 +74,23 @@ struct Plan {
     // fill-in blocks (Sec. 3.4): entries e of sidx whose pair (k, S_k[e]) is not a near pair
     std::vector<int> fill_e;     // entry index into sidx
     std::vector<int> fill_k;     // its block row k
+    // super-rows of SWEEP_SR consecutive blocks in sweep order (index 0 forward, 1 backward):
+    // xptr/xdep = the union of the members' dependency blocks outside the super-row, in the
+    // order the sweep adds them; xoff[e * SWEEP_SR + s] = column of member s's coefficient
+    // block in the dependency's panel (forward) or of the dependency's block in member s's
+    // panel (backward), -1 if the pair has none; xint[(r * SWEEP_SR + s) * SWEEP_SR + s2] =
+    // the same for member s as the dependency of member s2 (s < s2)
+    std::vector<int> xptr[2], xdep[2], xoff[2], xint[2];
+    // recent dependencies of each block for the chain-and-helpers sweeps (index 0 forward,
+    // 1 backward): rec[d][b * SWEEP_T + j] = the j-th dependency within SWEEP_T positions of b
+    // in walk order (-1 past the last), reccol the panel column as in ridx/rcol, sidx/srow
+    std::vector<int> rec[2], reccol[2];
     int bandwidth = 0;
     double setup_flops = 0;
     int max_S = 0, max_M = 0;
     int64_t n_updates = 0;
 };
 
-// far-field incidence lists (cluster order): per leaf l, entries (b << 2 | kind), kind
-// 0 = low-rank row side, 1 = low-rank column side, 2 = dense row side, 3 = dense column side
 // One contraction segment of a leaf's far-field rows (phase 2 of the far product):
 // F(i, k) = Fbase[foff + i * fi + k * fk] (Fbase = U, or V when src & 1), and
 // Y(k, r) = Ybase[(yrow + k) * nrhs + r] (Ybase = t, s, u for src >> 1 = 0, 1, 2), k < len.
@@ -89,6 +101,8 @@ struct FarSegD {
 
 constexpr int FAR_PARTS = 4;
 
+// far-field incidence lists (cluster order): per leaf l, entries (b << 2 | kind), kind
+// 0 = low-rank row side, 1 = low-rank column side, 2 = dense row side, 3 = dense column side
 struct FarPlan {
     int nf = 0;
     int64_t entries = 0;
@@ -113,14 +127,15 @@ struct FarPlan {
     std::vector<int> nptr, nent;
 };
 
-// Online choice of the number of independent column groups of a sweep launch, per
-// precision, direction and width class: candidates are timed on real calls (every
-// candidate computes the same result) and the fastest per column is kept.
+// Online choice of the schedule of a sweep launch -- the number of independent column
+// groups and the blocks per CTA (1, or a super-row of SWEEP_SR) -- per precision, direction
+// and width class: candidates are timed on real calls (every candidate computes the same
+// result) and the fastest per column is kept.
 constexpr int SWEEP_GMAX = 4;
 struct SweepTune {
-    int ncand = 0, trial = 0, best = 0;
-    int cand[3] = {0, 0, 0}, width[3] = {0, 0, 0};
-    cudaEvent_t ev[6] = {};
+    int ncand = 0, trial = 0, best = 0;   // candidate code: groups | blocks per CTA << 4
+    int cand[6] = {}, width[6] = {};
+    cudaEvent_t ev[12] = {};
 };
 
 }  // namespace hm
@@ -164,6 +179,8 @@ struct hm_ctx {
     int *d_size = nullptr, *d_boff = nullptr, *d_sptr = nullptr, *d_sidx = nullptr, *d_srow = nullptr, *d_M = nullptr;
     int64_t *d_coff = nullptr, *d_doff = nullptr;
     int *d_rptr = nullptr, *d_ridx = nullptr, *d_rcol = nullptr;
+    int *d_xptr[2] = {nullptr, nullptr}, *d_xdep[2] = {nullptr, nullptr}, *d_xoff[2] = {nullptr, nullptr},
+        *d_xint[2] = {nullptr, nullptr}, *d_rec[2] = {nullptr, nullptr}, *d_reccol[2] = {nullptr, nullptr};
     // device: setup outputs / workspace
     double2 *d_A = nullptr;      // stacked columns workspace (scratch during setup; FP64 setup)
     float2 *d_A32 = nullptr;     // the same for the mixed-precision setup
@@ -191,6 +208,7 @@ struct hm_ctx {
     int t32_cols = 0;
     bool batch_open = false;   // an hm_batch holds this handle
     hm::SweepTune sweep_tune[2][2][5];   // [FP32][forward][width class]
+    int sweep_fixed = 0;                 // a schedule code set by hm_set_sweep_schedule, 0 = tuned
 };
 
 // Launch wrapper: counts every launch by kernel class and, when profiling is on, brackets

@@ -91,16 +91,20 @@ template <class T, int TR, int TC, int NT, bool FWD>
 __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, const int *boff, const int *lptr,
                                           const int *lidx, const int *lcol, const int64_t *coff, const T *W,
                                           const T *x, T *y, int n, int nrhs, int budget, int *flags, int epoch,
-                                          int *err, T *buf)
+                                          int *err, T *buf, int cut = 0, int *pub = nullptr)
 {
+    // cut > 0: leave the last `cut` dependencies of the walk out (they are added by the
+    // chain CTA of a chain-and-helpers sweep) and publish the partial sum on `pub`
+    if (!pub) pub = flags;
     const int o = boff[o_blk];
     const int nrt = (no + TR - 1) / TR, ntiles = nrt * ((nrhs + TC - 1) / TC);
     const int ldw = stage_ldw(no, TR);
     Tile<T, TR, TC, NT> acc;
     tile_load(acc, x + o, 1, n, no, nrhs, nrt, ntiles);
     // forward: list ascending over [lptr[o], lptr[o+1]); backward: descending
-    const int pa = FWD ? lptr[o_blk] : lptr[o_blk + 1] - 1, pend = FWD ? lptr[o_blk + 1] : lptr[o_blk] - 1;
     const int step = FWD ? 1 : -1;
+    const int pa = FWD ? lptr[o_blk] : lptr[o_blk + 1] - 1,
+              pend = (FWD ? lptr[o_blk + 1] : lptr[o_blk] - 1) - cut * step;
     for (int p = pa; p != pend;) {
         const int q = next_chunk<TR, TC>(p, pend, step, lidx, size, no, nrhs, budget);
         // stage the coefficient blocks (static data) before waiting
@@ -145,7 +149,7 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        *(volatile int *)(flags + o_blk) = epoch;
+        *(volatile int *)(pub + o_blk) = epoch;
     }
 }
 
@@ -188,6 +192,356 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, cons
     const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
     sweep_row<T, TR, TC, NT, false>(k, size[k], size, boff, sptr, sidx, srow, coff, W, x + (int64_t)c0 * n,
                                     y + (int64_t)c0 * n, n, nc, budget, flags + g * nb, epoch, err, (T *)smraw);
+}
+
+// Chain-and-helpers sweep.  The dependencies of block row b are split: the `recent` ones,
+// at most SWEEP_T positions before b in sweep order, come last in b's walk; the others are
+// added by a helper CTA (sweep_row with the recent ones cut off), which leaves the partial
+// sum in y and raises b's partial flag.  One chain CTA per column group then walks the
+// block rows in sweep order: it continues b's sum from the partial, adds the recent
+// dependencies from a shared-memory ring of the last SWEEP_T + 1 results (their coefficient
+// blocks read through L1), stores y_b and raises its final flag, which the helpers wait on.
+// The chain CTAs take the first tickets, so they are resident before any helper; every
+// output adds its terms in the same order as with one block row per CTA.
+// number of recent dependencies at the end of b's walk (|dependency - b| <= SWEEP_T)
+template <bool FWD>
+__device__ __forceinline__ int recent_count(int b, const int *lptr, const int *lidx)
+{
+    int c = 0;
+    if (FWD)
+        for (int p = lptr[b + 1] - 1; p >= lptr[b] && lidx[p] >= b - SWEEP_T; --p) ++c;
+    else
+        for (int p = lptr[b]; p < lptr[b + 1] && lidx[p] <= b + SWEEP_T; ++p) ++c;
+    return c;
+}
+
+constexpr int CHAIN_WCAP = 4096;   // entries of each coefficient staging buffer of a chain CTA
+
+template <class T> __device__ __forceinline__ void cp_async_el(T *dst, const T *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// What the chain CTA needs about one block row: loaded one step ahead (independent loads),
+// so that their latency overlaps the current step.
+struct ChainMeta {
+    int b, nb, o, nrec;
+    int k[SWEEP_T], nk[SWEEP_T];
+    int64_t src[SWEEP_T];   // entry offset of each recent coefficient block in W
+};
+
+template <bool FWD>
+__device__ __forceinline__ ChainMeta chain_meta(int b, const int *size, const int *boff, const int *rec,
+                                                const int *reccol, const int64_t *coff)
+{
+    ChainMeta m;
+    m.b = b;
+    m.nb = size[b];
+    m.o = boff[b];
+    m.nrec = 0;
+    int col[SWEEP_T];
+#pragma unroll
+    for (int j = 0; j < SWEEP_T; ++j) {
+        m.k[j] = rec[b * SWEEP_T + j];
+        col[j] = reccol[b * SWEEP_T + j];
+    }
+    const int64_t cb = coff[b];
+#pragma unroll
+    for (int j = 0; j < SWEEP_T; ++j) {
+        const int k = m.k[j] < 0 ? b : m.k[j];
+        m.nk[j] = size[k];
+        const int64_t ck = coff[k];
+        m.src[j] = FWD ? ck + (int64_t)col[j] * m.nk[j] : cb + (int64_t)col[j] * m.nb;
+        if (m.k[j] >= 0) m.nrec = j + 1;
+    }
+    return m;
+}
+
+template <class T, int TR, int TC, int NT, bool FWD>
+__device__ void chain_run(int nb, const int *size, const int *boff, const int *rec, const int *reccol,
+                          const int64_t *coff, const T *W, T *y, int n, int nc, int *fpart, int *ffin, int epoch,
+                          int *err, T *ring)
+{
+    const int slot_sz = 64 * nc;
+    T *wbuf[2] = {ring + (SWEEP_T + 1) * slot_sz, ring + (SWEEP_T + 1) * slot_sz + CHAIN_WCAP};
+    // copy the recent coefficient blocks of m (concatenated) into buffer `which`; false (nothing
+    // copied) when they do not fit
+    auto stage = [&](const ChainMeta &m, int which) {
+        int tot = 0;
+#pragma unroll
+        for (int j = 0; j < SWEEP_T; ++j)
+            if (j < m.nrec) tot += m.nk[j] * m.nb;
+        bool ok = tot <= CHAIN_WCAP;
+        if (ok) {
+            int off = 0;
+#pragma unroll
+            for (int j = 0; j < SWEEP_T; ++j)
+                if (j < m.nrec) {
+                    const int cnt = m.nk[j] * m.nb;
+                    for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+                        cp_async_el(wbuf[which] + off + e, W + m.src[j] + e);
+                    off += cnt;
+                }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        return ok;
+    };
+    ChainMeta m = chain_meta<FWD>(FWD ? 0 : nb - 1, size, boff, rec, reccol, coff);
+    bool staged = stage(m, 0);
+    for (int q = 0; q < nb; ++q) {
+        const int b = m.b, nb_ = m.nb, o = m.o;
+        const int nrt = (nb_ + TR - 1) / TR, ntiles = nrt * ((nc + TC - 1) / TC);
+        const bool last = q + 1 == nb;
+        ChainMeta mn = chain_meta<FWD>(last ? b : (FWD ? q + 1 : nb - 2 - q), size, boff, rec, reccol, coff);
+        if (threadIdx.x == 0) wait_ready(fpart, b, epoch, err);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        const bool here = staged;
+        if (!last) staged = stage(mn, (q + 1) & 1);   // the next block's coefficients, other buffer
+        Tile<T, TR, TC, NT> acc;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int tile = threadIdx.x + t * blockDim.x;
+            const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+#pragma unroll
+            for (int a = 0; a < TR; ++a)
+#pragma unroll
+                for (int c = 0; c < TC; ++c)
+                    acc.v[t][a][c] = (tile < ntiles && row0 + a < nb_ && r0 + c < nc)
+                                         ? ldcg(y + o + row0 + a + (int64_t)(r0 + c) * n)
+                                         : czero(T());
+        }
+        int woff = 0;
+#pragma unroll
+        for (int j = 0; j < SWEEP_T; ++j) {
+            if (j >= m.nrec) break;
+            const int k = m.k[j], nk = m.nk[j];
+            const int qk = FWD ? k : nb - 1 - k;   // sweep position of k
+            const T *Ys = ring + (qk % (SWEEP_T + 1)) * slot_sz;   // Ys[r * nk + qq]
+            // M(row, qq) = Mb[row * mr + qq * mq]
+            const T *Mb = here ? wbuf[q & 1] + woff : W + m.src[j];
+            const int mr = FWD ? nk : 1, mq = FWD ? 1 : nb_;
+            woff += nk * nb_;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const int tile = threadIdx.x + t * blockDim.x;
+                if (tile < ntiles) {
+                    const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+#pragma unroll 4
+                    for (int qq = 0; qq < nk; ++qq) {
+                        T w[TR], yv[TC];
+#pragma unroll
+                        for (int a = 0; a < TR; ++a)
+                            w[a] = row0 + a < nb_ ? Mb[(row0 + a) * mr + qq * mq] : czero(T());
+#pragma unroll
+                        for (int c = 0; c < TC; ++c) yv[c] = Ys[(r0 + c) * nk + qq];
+#pragma unroll
+                        for (int a = 0; a < TR; ++a)
+#pragma unroll
+                            for (int c = 0; c < TC; ++c) acc.v[t][a][c] = cfms(w[a], yv[c], acc.v[t][a][c]);
+                    }
+                }
+            }
+        }
+        // y_b: to the ring (as a vector block, r * nb_ + row) and to global memory
+        T *slot = ring + (q % (SWEEP_T + 1)) * slot_sz;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int tile = threadIdx.x + t * blockDim.x;
+            const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+#pragma unroll
+            for (int a = 0; a < TR; ++a)
+#pragma unroll
+                for (int c = 0; c < TC; ++c)
+                    if (tile < ntiles && row0 + a < nb_ && r0 + c < nc) {
+                        slot[(r0 + c) * nb_ + row0 + a] = acc.v[t][a][c];
+                        y[o + row0 + a + (int64_t)(r0 + c) * n] = acc.v[t][a][c];
+                    }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            *(volatile int *)(ffin + b) = epoch;
+        }
+        m = mn;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <class T, int TR, int TC, int NT, bool FWD>
+__global__ void __launch_bounds__(256) k_sweep_ch(int nb, const int *size, const int *boff, const int *lptr,
+                                                  const int *lidx, const int *lcol, const int *rec, const int *reccol,
+                                                  const int64_t *coff, const T *W,
+                                                  const T *x, T *y, int n, int nrhs, int G, int gw, int budget,
+                                                  int *flags, int epoch, int *ticket, int *err)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ int s_t;
+    if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= G * (nb + 1)) return;
+    const int g = t < G ? t : (t - G) % G;
+    const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
+    int *ffin = flags + g * nb, *fpart = flags + (SWEEP_GMAX + g) * nb;
+    if (t < G) {
+        chain_run<T, TR, TC, NT, FWD>(nb, size, boff, rec, reccol, coff, W, y + (int64_t)c0 * n, n, nc, fpart, ffin,
+                                      epoch, err, (T *)smraw);
+        return;
+    }
+    const int qpos = (t - G) / G, b = FWD ? qpos : nb - 1 - qpos;
+    const int cut = recent_count<FWD>(b, lptr, lidx);
+    sweep_row<T, TR, TC, NT, FWD>(b, size[b], size, boff, lptr, lidx, lcol, coff, W, x + (int64_t)c0 * n,
+                                  y + (int64_t)c0 * n, n, nc, budget, ffin, epoch, err, (T *)smraw, cut, fpart);
+}
+
+// Super-row sweep (both directions): one CTA computes the SR consecutive blocks (sweep
+// order) of super-row r for one column group.  The members' external dependencies are
+// added chunk by chunk as in sweep_row (members without a coefficient block for a
+// dependency get zero rows, which leave their sums unchanged); then member s is final,
+// stored and published, and its product with the later members' coefficient blocks is
+// taken from shared memory before the next member is published.  Every output therefore
+// adds its terms in the same order as with one block per CTA.
+template <class T, int TR, int TC, int NT, bool FWD>
+__global__ void __launch_bounds__(256) k_sweep_sr(int nb, int nsr, const int *size, const int *boff, const int *xptr,
+                                                  const int *xdep, const int *xoff, const int *xint,
+                                                  const int64_t *coff, const T *W, const T *x, T *y, int n, int nrhs,
+                                                  int G, int gw, int budget, int *flags, int epoch, int *ticket,
+                                                  int *err)
+{
+    constexpr int SR = SWEEP_SR;
+    extern __shared__ unsigned char smraw[];
+    T *buf = (T *)smraw;
+    __shared__ int s_t;
+    if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int r = s_t / G, g = s_t % G;
+    if (r >= nsr) return;
+    const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
+    x += (int64_t)c0 * n;
+    y += (int64_t)c0 * n;
+    flags += g * nb;
+    int mb[SR], R[SR + 1], nm = 0;
+    R[0] = 0;
+#pragma unroll
+    for (int s = 0; s < SR; ++s) {
+        const int q = r * SR + s;
+        mb[s] = q < nb ? (FWD ? q : nb - 1 - q) : -1;
+        if (q < nb) nm = s + 1;
+        R[s + 1] = R[s] + (q < nb ? size[mb[s]] : 0);
+    }
+    const int no = R[nm];
+    const int nrt = (no + TR - 1) / TR, ntiles = nrt * ((nc + TC - 1) / TC);
+    const int ldw = stage_ldw(no, TR);
+    auto member = [&](int row) {
+        int s = 0;
+#pragma unroll
+        for (int t = 1; t < SR; ++t)
+            if (row >= R[t]) s = t;
+        return s;
+    };
+    Tile<T, TR, TC, NT> acc;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int tile = threadIdx.x + t * blockDim.x;
+        const int row0 = (tile % nrt) * TR, q0 = (tile / nrt) * TC;
+#pragma unroll
+        for (int a = 0; a < TR; ++a) {
+            const int row = row0 + a, s = member(row);
+            const int64_t gr = row < no ? boff[mb[s]] + row - R[s] : 0;
+#pragma unroll
+            for (int c = 0; c < TC; ++c)
+                acc.v[t][a][c] = (tile < ntiles && row < no && q0 + c < nc) ? x[gr + (int64_t)(q0 + c) * n] : czero(T());
+        }
+    }
+    // external dependencies, in the stored order
+    const int pa = xptr[r], pend = xptr[r + 1];
+    for (int p = pa; p != pend;) {
+        const int q = next_chunk<TR, TC>(p, pend, 1, xdep, size, no, nc, budget);
+        int off = 0;
+        for (int b = p; b != q; ++b) {
+            const int k = xdep[b], nq = size[k];
+            T *Ws = buf + off;
+            const int *xo = xoff + (int64_t)b * SR;
+            stage_copy(nq * no, [&](int e) {
+                const int qq = e % nq, row = e / nq, s = member(row), o = xo[s], rr = row - R[s];
+                if (o < 0) return czero(T());
+                // forward: W_{k,m_s} (nq x n_s) element (qq, rr); backward: W_{m_s,k} (n_s x nq) element (rr, qq)
+                const int ns = R[s + 1] - R[s];
+                return FWD ? W[coff[k] + (int64_t)o * nq + qq + (int64_t)rr * nq]
+                           : W[coff[mb[s]] + (int64_t)o * ns + rr + (int64_t)qq * ns];
+            }, [&](int e, T v) { Ws[(e % nq) * ldw + e / nq] = v; });
+            off += stage_need(no, nq, nc, TR, TC);
+        }
+        if (threadIdx.x == 0)
+            for (int b = p; b != q; ++b) wait_ready(flags, xdep[b], epoch, err);
+        __syncthreads();
+        off = 0;
+        for (int b = p; b != q; ++b) {
+            const int k = xdep[b], nq = size[k], ok = boff[k];
+            T *Ys = buf + off + nq * ldw;
+            stage_copy(nq * nc, [&](int e) { return ldcg(y + ok + e % nq + (int64_t)(e / nq) * n); },
+                       [&](int e, T v) { Ys[e] = v; });
+            off += stage_need(no, nq, nc, TR, TC);
+        }
+        __syncthreads();
+        off = 0;
+        for (int b = p; b != q; ++b) {
+            const int nq = size[xdep[b]];
+            tile_mac<true>(acc, buf + off, ldw, buf + off + nq * ldw, 1, nq, nq, nrt, ntiles);
+            off += stage_need(no, nq, nc, TR, TC);
+        }
+        __syncthreads();
+        p = q;
+    }
+    // members in sweep order: store and publish member s, then apply it to the later members
+    for (int s = 0; s < nm; ++s) {
+        const int ns = R[s + 1] - R[s];
+        T *Yint = buf + ns * ldw;   // member s's entries as the vector block (nc x ns)
+        const bool more = s + 1 < nm;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int tile = threadIdx.x + t * blockDim.x;
+            const int row0 = (tile % nrt) * TR, q0 = (tile / nrt) * TC;
+#pragma unroll
+            for (int a = 0; a < TR; ++a) {
+                const int row = row0 + a;
+                if (tile < ntiles && row >= R[s] && row < R[s + 1]) {
+                    const int64_t gr = boff[mb[s]] + row - R[s];
+#pragma unroll
+                    for (int c = 0; c < TC; ++c)
+                        if (q0 + c < nc) {
+                            y[gr + (int64_t)(q0 + c) * n] = acc.v[t][a][c];
+                            if (more) Yint[(q0 + c) * ns + row - R[s]] = acc.v[t][a][c];
+                        }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            *(volatile int *)(flags + mb[s]) = epoch;
+        }
+        if (!more) break;
+        // coefficients of member s for the later members: rows of member s2 > s from the
+        // block coupling them (forward W_{m_s, m_s2} in panel m_s, backward W_{m_s2, m_s} in
+        // panel m_s2), zero elsewhere
+        stage_copy(ns * no, [&](int e) {
+            const int qq = e % ns, row = e / ns, s2 = member(row);
+            const int o = s2 > s ? xint[((int64_t)r * SR + s) * SR + s2] : -1;
+            if (o < 0) return czero(T());
+            const int rr = row - R[s2], n2 = R[s2 + 1] - R[s2];
+            return FWD ? W[coff[mb[s]] + (int64_t)o * ns + qq + (int64_t)rr * ns]
+                       : W[coff[mb[s2]] + (int64_t)o * n2 + rr + (int64_t)qq * n2];
+        }, [&](int e, T v) { buf[(e % ns) * ldw + e / ns] = v; });
+        __syncthreads();
+        tile_mac<true>(acc, buf, ldw, Yint, 1, ns, ns, nrt, ntiles);
+        __syncthreads();
+    }
 }
 
 // dst[i*nrhs + r] = src[idx[i] + r*n]   (right-hand sides interleaved)
@@ -351,19 +705,86 @@ static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, cons
     return cudaGetLastError();
 }
 
+// Super-row launch: (TR, TC, NT) = (1, 1, 2) up to 4 columns per group, else (2, 2, 2) up to 16.
+template <class T, int TR, int TC, int NT>
+static cudaError_t sweep_sr_shape(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs, int G,
+                                  int gw, int ep, int maxw)
+{
+    Plan &P = h->plan;
+    const int budget = stage_need(64 * SWEEP_SR, 64, gw, TR, TC);
+    const size_t smem = sizeof(T) * (size_t)budget;
+    static bool attr = false;
+    if (!attr) {
+        const int smax = (int)(sizeof(T) * (size_t)stage_need(64 * SWEEP_SR, 64, maxw, TR, TC));
+        cudaFuncSetAttribute(k_sweep_sr<T, TR, TC, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        cudaFuncSetAttribute(k_sweep_sr<T, TR, TC, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        attr = true;
+    }
+    const int nsr = (P.nb + SWEEP_SR - 1) / SWEEP_SR, dir = forward ? 0 : 1;
+    const unsigned grid = (unsigned)(nsr * G);
+    if (forward)
+        HM_LAUNCH(h, K_SWEEP_FWD,
+                  (k_sweep_sr<T, TR, TC, NT, true><<<grid, 256, smem, h->stream>>>(
+                      P.nb, nsr, h->d_size, h->d_boff, h->d_xptr[dir], h->d_xdep[dir], h->d_xoff[dir], h->d_xint[dir],
+                      h->d_coff, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+    else
+        HM_LAUNCH(h, K_SWEEP_BWD,
+                  (k_sweep_sr<T, TR, TC, NT, false><<<grid, 256, smem, h->stream>>>(
+                      P.nb, nsr, h->d_size, h->d_boff, h->d_xptr[dir], h->d_xdep[dir], h->d_xoff[dir], h->d_xint[dir],
+                      h->d_coff, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+    return cudaGetLastError();
+}
+
+// Chain-and-helpers launch: one chain CTA per column group plus one helper per block row
+// and group; (TR, TC, NT) = (1, 1, 1) up to 4 columns per group, else (2, 2, 1) up to 16.
+template <class T, int TR, int TC, int NT>
+static cudaError_t sweep_ch_shape(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs, int G,
+                                  int gw, int ep, int maxw)
+{
+    Plan &P = h->plan;
+    const int budget = std::max(stage_need(64, 64, gw, TR, TC), (SWEEP_T + 1) * 64 * gw + 2 * CHAIN_WCAP);
+    const size_t smem = sizeof(T) * (size_t)budget;
+    static bool attr = false;
+    if (!attr) {
+        const int smax = (int)(sizeof(T) * (size_t)std::max(stage_need(64, 64, maxw, TR, TC),
+                                                            (SWEEP_T + 1) * 64 * maxw + 2 * CHAIN_WCAP));
+        cudaFuncSetAttribute(k_sweep_ch<T, TR, TC, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        cudaFuncSetAttribute(k_sweep_ch<T, TR, TC, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        attr = true;
+    }
+    const unsigned grid = (unsigned)(G * (P.nb + 1));
+    if (forward)
+        HM_LAUNCH(h, K_SWEEP_FWD,
+                  (k_sweep_ch<T, TR, TC, NT, true><<<grid, 256, smem, h->stream>>>(
+                      P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol, h->d_rec[0], h->d_reccol[0],
+                      h->d_coff, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+    else
+        HM_LAUNCH(h, K_SWEEP_BWD,
+                  (k_sweep_ch<T, TR, TC, NT, false><<<grid, 256, smem, h->stream>>>(
+                      P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow, h->d_rec[1], h->d_reccol[1],
+                      h->d_coff, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+    return cudaGetLastError();
+}
+
 static int width_class(int w) { return w <= 4 ? 0 : w <= 8 ? 1 : w <= 16 ? 2 : w <= 32 ? 3 : 4; }
 
 // Number of column groups for a sweep of nrhs columns: the tuned choice of the width class,
 // or the next untried candidate (then *tu / *slot let the caller time the launch).
 static int sweep_groups(hm_ctx *h, bool fp32, bool forward, int nrhs, SweepTune **tu, int *slot)
 {
-    SweepTune &t = h->sweep_tune[fp32][forward][width_class(nrhs)];
     *tu = nullptr;
+    if (h->sweep_fixed) return h->sweep_fixed;
+    SweepTune &t = h->sweep_tune[fp32][forward][width_class(nrhs)];
     if (t.best) return t.best;
     if (t.ncand == 0)
-        for (int G = 1; G <= SWEEP_GMAX; G *= 2)
-            if (G == 1 || (nrhs + G - 1) / G >= 4) t.cand[t.ncand++] = G;
-    if (t.ncand == 1) return t.best = 1;
+        for (int G = 1; G <= SWEEP_GMAX; G *= 2) {
+            const int gw = (nrhs + G - 1) / G;
+            if (G > 1 && gw < 4) continue;
+            // one block row per CTA; the super-row and chain-and-helpers kinds compute the same
+            // sums but measured slower on every width (they stay selectable)
+            t.cand[t.ncand++] = G | (1 << 4);
+        }
+    if (t.ncand == 1) return t.best = t.cand[0];
     if (t.trial < t.ncand) {
         if (!t.ev[0])
             for (cudaEvent_t &e : t.ev) cudaEventCreate(&e);
@@ -405,10 +826,17 @@ static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x
     const int ep = ++h->epoch;
     SweepTune *tu;
     int slot = 0;
-    const int G = sweep_groups(h, sizeof(T) == 8, forward, nrhs, &tu, &slot);
+    const int code = sweep_groups(h, sizeof(T) == 8, forward, nrhs, &tu, &slot);
+    const int G = std::min(code & 15, nrhs), sr = code >> 4;
     const int gw = (nrhs + G - 1) / G;
     if (tu) cudaEventRecord(tu->ev[2 * slot], h->stream);
-    if (gw <= 4) e = sweep_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
+    if (sr == 3 && gw <= 16) {
+        if (gw <= 4) e = sweep_ch_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
+        else e = sweep_ch_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
+    } else if (sr == 2 && gw <= 16) {
+        if (gw <= 4) e = sweep_sr_shape<T, 1, 1, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
+        else e = sweep_sr_shape<T, 2, 2, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
+    } else if (gw <= 4) e = sweep_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
     else if constexpr (sizeof(T) == 16) e = sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
     else {
         if (gw <= 16) e = sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
@@ -456,8 +884,8 @@ cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs)
     cudaError_t e;
     const int n = h->plan.n;
     if (!h->d_flags) {
-        if ((e = h->arena.alloc((void **)&h->d_flags, sizeof(int) * h->plan.nb * SWEEP_GMAX))) return e;
-        if ((e = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->plan.nb * SWEEP_GMAX, h->stream))) return e;
+        if ((e = h->arena.alloc((void **)&h->d_flags, sizeof(int) * h->plan.nb * SWEEP_GMAX * 2))) return e;
+        if ((e = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->plan.nb * SWEEP_GMAX * 2, h->stream))) return e;
         h->epoch = 0;
     }
     const size_t tl = std::max<int64_t>(1, h->fplan.tlen);

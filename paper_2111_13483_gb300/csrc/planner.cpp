@@ -223,6 +223,71 @@ void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &p
     }
 }
 
+// Super-rows of the sweeps (see Plan::xptr): members are SWEEP_SR consecutive blocks in
+// sweep order; their dependency lists are merged, the pairs inside the super-row kept apart.
+static void plan_superrows(Plan &P)
+{
+    const int nb = P.nb, SR = SWEEP_SR, nsr = (nb + SR - 1) / SR;
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<int> &xp = P.xptr[dir], &xd = P.xdep[dir], &xo = P.xoff[dir], &xi = P.xint[dir];
+        xp.assign(nsr + 1, 0);
+        xd.clear();
+        xo.clear();
+        xi.assign((size_t)nsr * SR * SR, -1);
+        for (int r = 0; r < nsr; ++r) {
+            int mem[SWEEP_SR], nm = 0;
+            for (int s = 0; s < SR && r * SR + s < nb; ++s) mem[nm++] = dir == 0 ? r * SR + s : nb - 1 - (r * SR + s);
+            std::map<int, std::vector<int>> deps;   // dependency block -> offset per member
+            for (int s = 0; s < nm; ++s) {
+                const int b = mem[s];
+                const int lo = dir == 0 ? P.rptr[b] : P.sptr[b], hi = dir == 0 ? P.rptr[b + 1] : P.sptr[b + 1];
+                for (int e = lo; e < hi; ++e) {
+                    const int k = dir == 0 ? P.ridx[e] : P.sidx[e];
+                    const int off = dir == 0 ? P.rcol[e] : P.srow[e];
+                    int sk = -1;
+                    for (int t = 0; t < nm; ++t)
+                        if (mem[t] == k) sk = t;
+                    if (sk >= 0) {
+                        xi[((size_t)r * SR + sk) * SR + s] = off;
+                        continue;
+                    }
+                    std::vector<int> &v = deps[k];
+                    if (v.empty()) v.assign(SR, -1);
+                    v[s] = off;
+                }
+            }
+            std::vector<int> keys;
+            for (auto &kv : deps) keys.push_back(kv.first);
+            if (dir == 1) std::reverse(keys.begin(), keys.end());   // the backward sweep adds downwards
+            for (int k : keys) {
+                xd.push_back(k);
+                for (int s = 0; s < SR; ++s) xo.push_back(deps[k][s]);
+            }
+            xp[r + 1] = (int)xd.size();
+        }
+    }
+    // recent dependencies (chain-and-helpers sweeps), in walk order
+    for (int dir = 0; dir < 2; ++dir) {
+        P.rec[dir].assign((size_t)nb * SWEEP_T, -1);
+        P.reccol[dir].assign((size_t)nb * SWEEP_T, 0);
+        for (int b = 0; b < nb; ++b) {
+            std::vector<std::pair<int, int>> rv;
+            if (dir == 0) {
+                for (int p = P.rptr[b + 1] - 1; p >= P.rptr[b] && P.ridx[p] >= b - SWEEP_T; --p)
+                    rv.push_back({P.ridx[p], P.rcol[p]});
+                std::reverse(rv.begin(), rv.end());   // ascending
+            } else
+                for (int p = P.sptr[b]; p < P.sptr[b + 1] && P.sidx[p] <= b + SWEEP_T; ++p)
+                    rv.push_back({P.sidx[p], P.srow[p]});
+            if (dir == 1) std::reverse(rv.begin(), rv.end());   // descending (the backward walk)
+            for (size_t j = 0; j < rv.size(); ++j) {
+                P.rec[dir][(size_t)b * SWEEP_T + j] = rv[j].first;
+                P.reccol[dir][(size_t)b * SWEEP_T + j] = rv[j].second;
+            }
+        }
+    }
+}
+
 void plan_order(hm_ctx *h)
 {
     Plan &P = h->plan;
@@ -330,6 +395,7 @@ void plan_order(hm_ctx *h)
             P.rcol[fillp[j]] = P.srow[e];
             fillp[j]++;
         }
+    plan_superrows(P);
 }
 
 void plan_far(hm_ctx *h)

@@ -59,7 +59,7 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_last_error", "hmat_destroy", "hm_get_order", "hm_get_fill", "hm_get_block", "hm_apply",
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
-           "hm_batch_step", "hm_batch_result", "hm_batch_close"]
+           "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -110,6 +110,7 @@ def load(build_if_missing=True):
     L.hm_batch_step.argtypes = [vp, _i32p, _i32p, _i32p]
     L.hm_batch_result.argtypes = [vp, ctypes.c_int32, vp, _i32p, _f64p]
     L.hm_batch_close.argtypes = [vp]
+    L.hm_set_sweep_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     _lib = L
     return L
 
@@ -309,6 +310,12 @@ def hm_far_apply_noalloc(h, dx, dy):
     dx, dy: torch complex128 CUDA tensors (nrhs, n) in solve order.  Returns the status code
     (HM_EINVAL when the call needs more scratch than the static array holds)."""
     return load().hm_far_apply_noalloc(h.ptr, dx.data_ptr(), dy.data_ptr(), dx.shape[0])
+
+
+def hm_set_sweep_schedule(h, groups=0, kind=0):
+    """Pins the sweep schedule (column groups 1/2/4; kind 1 row per CTA, 2 two rows, 3 chain +
+    helpers); (0, 0) = tuned."""
+    h.check(load().hm_set_sweep_schedule(h.ptr, groups, kind), "hm_set_sweep_schedule")
 
 
 def hm_get_fill_ranks(h):

@@ -238,3 +238,34 @@ def test_compressed_solve_matches_oracle(cfg1_compressed):
     xo, ito, rro, ok = krylov.solve(S, b, tol=1e-6, restart=30)
     assert code == 0 and ok and abs(int(it[0]) - ito) <= 1
     assert rel(x, xo) <= 1e-8
+
+
+# ---- sweep schedules: every (groups, kind) gives bitwise the same sweeps -------------------------
+# kind 1: one block row per CTA, 2: two-row super-rows, 3: chain CTA + helpers
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sweep_schedules_bitwise_equal(cfg1, cfg1_mixed, prec):
+    P, order, F, S, h64 = cfg1
+    h = h64 if prec == 0 else cfg1_mixed
+    ops = (hm.hmsolve.OP_LINV, hm.hmsolve.OP_LTINV, hm.hmsolve.OP_A)
+    if prec == 1:
+        ops = tuple(hm.hmsolve.OP32 + o for o in ops)
+    rng = np.random.default_rng(11)
+    for nrhs in (1, 5, 16):
+        X = rng.standard_normal((S.n, nrhs)) + 1j * rng.standard_normal((S.n, nrhs))
+        dx = _dev(X)
+        ref = {}
+        for sched in ((1, 1), (1, 2), (1, 3), (2, 1), (2, 2), (2, 3), (4, 1), (4, 2), (4, 3)):
+            hm.hmsolve.hm_set_sweep_schedule(h, *sched)
+            for op in ops:
+                dy = torch.empty_like(dx)
+                hm.hm_apply(h, op, dx, dy)
+                torch.cuda.synchronize()
+                Y = _host(dy)
+                if op not in ref:
+                    ref[op] = Y
+                    if prec == 0 and op == hm.hmsolve.OP_LINV:
+                        for c in range(nrhs):
+                            assert rel(Y[:, c], S.L_inv(X[:, c])) < 1e-10
+                else:
+                    assert np.array_equal(Y, ref[op]), (sched, op, nrhs)
+        hm.hmsolve.hm_set_sweep_schedule(h, 0, 0)
