@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="0: complex FP64; 1: complex-FP32 operator inside FP64 refinement")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the serving leg (Poisson arrivals at 0.8x the measured RHS/s); 0 = skip")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving on two resident geometries (sphere30720 + plate29800), 360 requests each, "
+                         "offered at 0.5/0.8/1.0x the measured throughput")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -161,46 +166,66 @@ def fill_structure(hm, h, P):
             "order": order, "sz": sz, "ptr": ptr, "idx": idx}
 
 
-def roofline(prof, fs, stats, n, nrhs_launch, precision):
-    """Roofline entry for the kernel class with the largest device time."""
+def roofline(prof, fs, stats, n, precision):
+    """Roofline entry for the kernel class with the largest device time.  The algorithmic work
+    uses the right-hand-side columns the class actually processed (the slot engine packs
+    fewer columns as solves finish); the bound is the one the arithmetic intensity selects
+    against the ridge of the measured peaks."""
     cls = max(prof, key=lambda c: prof[c][2])
-    launches, timed, ms = prof[cls]
-    avg_s = ms / max(timed, 1) / 1e3
+    launches, timed, ms, cols = prof[cls]
+    t_s = ms / 1e3
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if "when" in peaks else "fallback 6.8 TB/s"
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "when" in peaks else "fallback 6.8 TB/s (of fallback)"
     E = 8.0 if precision == 1 else 16.0
     alu_peak = FP32_PEAK_TFLOPS if precision == 1 else FP64_PEAK_TFLOPS
     alu_src = ("derived: 152 SMs x %d %s FMA/clk x 2 flop x 2.07 GHz" % ((128, "FP32") if precision == 1 else (2, "FP64")))
 
-    def alu(work, extra):
-        d = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-             "frac": work / avg_s / 1e12 / alu_peak, "traffic": None, "peak_source": alu_src,
-             "work_per_launch": work, "avg_launch_ms": avg_s * 1e3}
-        d.update(extra)
-        return d
-
-    def hbm(bytes_, extra):
-        d = {"bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-             "frac": bytes_ / avg_s / 1e9 / peaks["hbm_gbs"], "traffic": None, "peak_source": hbm_src,
-             "bytes_per_launch": bytes_, "avg_launch_ms": avg_s * 1e3}
+    def entry(flops, bytes_, extra):
+        # flops, bytes_: totals over the class's timed launches
+        ridge = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
+        d = {"avg_launch_ms": ms / max(timed, 1), "launches": launches, "rhs_columns": cols,
+             "flops_per_launch": flops / max(launches, 1), "bytes_per_launch": bytes_ / max(launches, 1),
+             "intensity_flop_per_byte": flops / max(bytes_, 1.0), "traffic": None}
+        if flops / max(bytes_, 1.0) > ridge:
+            d.update({"bound": "alu", "achieved": flops / t_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                      "frac": flops / t_s / 1e12 / alu_peak, "peak_source": alu_src})
+        else:
+            d.update({"bound": "hbm", "achieved": bytes_ / t_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                      "frac": bytes_ / t_s / 1e9 / peaks["hbm_gbs"], "peak_source": hbm_src})
         d.update(extra)
         return d
 
     if cls == "update":
-        return cls, alu(fs["update_flops"] / fs["update_launches"], {})
+        return cls, entry(fs["update_flops"] * launches / fs["update_launches"],
+                          E * fs["nnzL"] * 3.0 * launches / fs["update_launches"], {})
     if cls in ("sweep_fwd", "sweep_bwd"):
-        flops = 8.0 * fs["nnzL"] * nrhs_launch
-        bytes_ = E * (fs["nnzL"] + 2 * n * nrhs_launch)
-        # FP64: 0.5 flop/B x 6.8 TB/s exceeds the FP64 pipe, so the ALU bounds it
-        return cls, (hbm(bytes_, {"flops_per_launch": flops}) if precision == 1
-                     else alu(flops, {"bytes_per_launch": bytes_}))
+        # per launch: the coefficient panels once, the input and output vectors of its columns
+        return cls, entry(8.0 * fs["nnzL"] * cols, E * (fs["nnzL"] * launches + 2.0 * n * cols), {})
     if cls in ("far1", "far2"):
-        bytes_ = E * stats["far_entries"]
-        flops = 8.0 * stats["far_entries"] * nrhs_launch
-        return cls, (hbm(bytes_, {"flops_per_launch": flops}) if precision == 1
-                     else alu(flops, {"bytes_per_launch": bytes_}))
-    return cls, hbm(16.0 * n * nrhs_launch * 2, {})
+        # far2 counts two launches per product (partial products + their sum)
+        per = launches if cls == "far1" else launches / 2
+        return cls, entry(8.0 * stats["far_entries"] * cols, E * (stats["far_entries"] * per + 2.0 * n * cols), {})
+    return cls, entry(0.0, 16.0 * n * max(cols, 1) * 2, {})
+
+
+def serving_run(hm, serve, h, P, requests, rate, tol, restart, seed_rhs=2, seed_arr=1):
+    """Poisson-arrival serving on one resident geometry: requests (monostatic plane waves,
+    host memory) submitted at their arrival times, continuous batching up to 64 slots."""
+    rhs = [V for _, _, V in serve.monostatic_requests(P, requests, seed_rhs, phi_step_deg=360.0 / requests)]
+    arr = serve.poisson_arrivals(requests, rate, seed_arr)
+    srv = serve.Server({"g": h}, max_slots=64, tol=tol, restart=restart)
+    t0 = time.perf_counter()
+    try:
+        reqs = serve.run_stream(srv, [("g", arr, rhs)])
+    finally:
+        srv.close()
+    wall = max(r.t_done for r in reqs) - min(r.t_submit for r in reqs)
+    s = serve.latency_summary(reqs)
+    s.update({"offered_rps": rate, "achieved_rhs_per_s": requests / wall, "wall_s": wall,
+              "not_converged": sum(r.status != 0 for r in reqs), "slots": srv.slots("g")})
+    del t0
+    return s
 
 
 def cpu_reference(P, B, iters_per_rhs, fill_tol, budget_s=15.0):
@@ -259,6 +284,37 @@ def cpu_reference(P, B, iters_per_rhs, fill_tol, budget_s=15.0):
             "%d RHS x (%.1f GPU-measured iterations + 3 operator applications)"
             % (t_plan, ks, nl, t_samp, 100 * step_flops[:ks].sum() / step_flops.sum(), t_far, B, iters_per_rhs))
     return step, desc, time.perf_counter() - t0
+
+
+def serving_full(hm, serve, h_sphere, P_sphere, args, rate1):
+    """Two resident geometries (the sphere and the 10 x 10 lambda plate), 360 monostatic
+    requests each (phi 0..359 deg, VV/HH drawn per request), Poisson arrivals offered at
+    0.5, 0.8 and 1.0 times the measured single-geometry throughput, split between them."""
+    import efie_problem as ep
+    Pp = ep.build("plate29800")
+    hp = hm.hmat_create(Pp, ordering=1, fill_tol=args.fill_tol, precision=args.precision)
+    hm.precond_setup(hp)
+    out = []
+    for f in (0.5, 0.8, 1.0):
+        rate = f * rate1
+        streams = []
+        for name, P, seed in (("sphere", P_sphere, 3), ("plate", Pp, 4)):
+            rhs = [V for _, _, V in serve.monostatic_requests(P, 360, seed)]
+            streams.append((name, serve.poisson_arrivals(360, rate / 2, seed + 10), rhs))
+        srv = serve.Server({"sphere": h_sphere, "plate": hp}, max_slots=64, tol=args.tol,
+                           restarts={"sphere": args.restart, "plate": 50})
+        try:
+            reqs = serve.run_stream(srv, streams)
+        finally:
+            srv.close()
+        wall = max(r.t_done for r in reqs) - min(r.t_submit for r in reqs)
+        s = serve.latency_summary(reqs)
+        s.update({"offered_rps": rate, "achieved_rhs_per_s": len(reqs) / wall,
+                  "per_geometry": {g: serve.latency_summary([r for r in reqs if r.geom == g])
+                                   for g in ("sphere", "plate")}})
+        out.append(s)
+    hm.hmat_destroy(hp)
+    return out
 
 
 def run_reference(args):
@@ -351,7 +407,16 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     value = B * args.steps * world / (ms_total / 1e3)
     iters = np.concatenate(iters_all[-args.steps:])
-    cls, roof = roofline(prof, fs, stats, P.n, min(B, 64 if args.precision == 1 else 16), args.precision)
+    cls, roof = roofline(prof, fs, stats, P.n, args.precision)
+
+    # ---- serving: Poisson arrivals into the continuous-batching engine ------------------
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        from paper_2111_13483_gb300 import serve
+        serving = serving_run(hm, serve, h, P, args.serve_requests, 0.8 * value / world, args.tol, args.restart)
+    if args.serve_full and rank == 0:
+        from paper_2111_13483_gb300 import serve
+        serving = {"single": serving, "full": serving_full(hm, serve, h, P, args, value / world)}
 
     # ---- end to end through the public API from pinned host memory ---------------------
     e2e = None
@@ -425,7 +490,7 @@ def run_ours(args):
             "solve_rhs_per_s": B / max((ms_step - setup_ms) / 1e3, 1e-9),
             "roofline": roof, "roofline_kernel": cls,
             "kernel_ms_per_step": {k: v[2] / args.steps for k, v in prof.items() if v[0]},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck, "serving": serving,
             "stats": {k: stats[k] for k in ("n", "n_blocks", "near_entries", "far_entries", "fill_blocks",
                                             "coef_entries", "diag_entries", "bandwidth", "setup_gflop")}}
     s = json.dumps(line)

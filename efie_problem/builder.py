@@ -284,6 +284,8 @@ SPECS = {
     # small cases for tests
     "sphere480":dict(kind="sphere", d=2, a=0.3, leaf=32, eta=1.0, aca_eps=1e-3),
     "plate_tiny": dict(kind="plate", n=8, w=0.8, jitter=0.1, seed=0, leaf=16, eta=1.0, aca_eps=1e-3),
+    # 2 x 2 lambda jittered plate on the same 0.1 lambda grid as plate29800 (1160 unknowns)
+    "plate1160": dict(kind="plate", n=20, w=2.0, jitter=0.1, seed=0, leaf=64, eta=1.0, aca_eps=1e-3),
 }
 
 

@@ -216,6 +216,9 @@ int hm_get_index_map(hm_handle h, int32_t *new2orig);
  */
 int hm_profile(hm_handle h, int32_t mode);
 int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, double *ms);
+/* Right-hand-side columns processed by class cls since the last reset, summed over its calls
+ * (counted for the sweeps, classes 4-5, and the far-field product, classes 6-7; else 0). */
+int hm_get_profile_cols(hm_handle h, int32_t cls, int64_t *cols);
 
 /*
  * Far-field product y = Z_F x (as hm_apply op 3) that allocates no device memory; the paper

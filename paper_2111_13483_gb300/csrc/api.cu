@@ -91,7 +91,7 @@ void Prof::flush()
 void Prof::reset()
 {
     flush();
-    for (int c = 0; c < K_NCLASS; ++c) count[c] = 0, ms[c] = 0, timed[c] = 0;
+    for (int c = 0; c < K_NCLASS; ++c) count[c] = 0, ms[c] = 0, timed[c] = 0, cols[c] = 0;
 }
 
 void Prof::destroy()
@@ -497,6 +497,13 @@ int hm_get_profile(hm_handle h, int32_t cls, int64_t *launches, int64_t *timed, 
     if (launches) *launches = h->prof.count[cls];
     if (timed) *timed = h->prof.timed[cls];
     if (ms) *ms = h->prof.ms[cls];
+    return HM_OK;
+}
+
+int hm_get_profile_cols(hm_handle h, int32_t cls, int64_t *cols)
+{
+    if (!h || !cols || cls < 0 || cls >= K_NCLASS) return HM_EINVAL;
+    *cols = h->prof.cols[cls];
     return HM_OK;
 }
 

@@ -233,6 +233,8 @@ template <class T> struct FarLaunch {
 template <class T>
 cudaError_t far_product(hm_ctx *h, const T *U, const T *V, T *t, T *s, const T *ucl, T *y, int nrhs)
 {
+    h->prof.cols[K_FAR1] += nrhs;
+    h->prof.cols[K_FAR2] += nrhs;
     FarLaunch<T> f{h, U, V, t, s, ucl, y, nrhs};
     return tile_dispatch<T>(nrhs, f);
 }

@@ -38,6 +38,7 @@ struct Prof {
     int64_t count[K_NCLASS] = {};
     double ms[K_NCLASS] = {};
     int64_t timed[K_NCLASS] = {};
+    int64_t cols[K_NCLASS] = {};   // right-hand-side columns processed (sweeps, far field)
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     cudaEvent_t cur_start = nullptr;

@@ -824,6 +824,7 @@ static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_ticket, 0, sizeof(int), h->stream))) return e;
     const int ep = ++h->epoch;
+    h->prof.cols[forward ? K_SWEEP_FWD : K_SWEEP_BWD] += nrhs;
     SweepTune *tu;
     int slot = 0;
     const int code = sweep_groups(h, sizeof(T) == 8, forward, nrhs, &tu, &slot);

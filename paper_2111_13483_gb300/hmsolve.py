@@ -59,7 +59,8 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_last_error", "hmat_destroy", "hm_get_order", "hm_get_fill", "hm_get_block", "hm_apply",
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
-           "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule"]
+           "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
+           "hm_get_profile_cols"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -111,6 +112,7 @@ def load(build_if_missing=True):
     L.hm_batch_result.argtypes = [vp, ctypes.c_int32, vp, _i32p, _f64p]
     L.hm_batch_close.argtypes = [vp]
     L.hm_set_sweep_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    L.hm_get_profile_cols.argtypes = [vp, ctypes.c_int32, _i64p]
     _lib = L
     return L
 
@@ -295,13 +297,15 @@ def hm_profile(h, mode):
 
 
 def hm_get_profile(h):
-    """{class name: (launches, timed launches, device ms)} for every kernel class."""
+    """{class name: (launches, timed launches, device ms, right-hand-side columns)} per kernel class."""
     out = {}
     L = load()
     for c, name in enumerate(KCLASS):
         a, b, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
         h.check(L.hm_get_profile(h.ptr, c, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)), "hm_get_profile")
-        out[name] = (a.value, b.value, ms.value)
+        cols = ctypes.c_int64()
+        h.check(L.hm_get_profile_cols(h.ptr, c, ctypes.byref(cols)), "hm_get_profile_cols")
+        out[name] = (a.value, b.value, ms.value, cols.value)
     return out
 
 

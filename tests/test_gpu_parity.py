@@ -269,3 +269,38 @@ def test_sweep_schedules_bitwise_equal(cfg1, cfg1_mixed, prec):
                 else:
                     assert np.array_equal(Y, ref[op]), (sched, op, nrhs)
         hm.hmsolve.hm_set_sweep_schedule(h, 0, 0)
+
+
+# ---- plate (the GMRES(50) workload's geometry, 2 x 2 lambda on the same grid) ------------------
+@pytest.fixture(scope="module")
+def plate_cfg():
+    import efie_problem as ep
+    P = ep.build("plate1160")
+    order, F, S = oracle_factor(P)
+    return P, order, F, S
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_plate_solve_matches_oracle(plate_cfg, prec):
+    P, order, F, S = plate_cfg
+    h = hm.hmat_create(P, ordering=1, fill_tol=0.0, precision=prec)
+    hm.precond_setup(h)
+    assert np.array_equal(hm.hm_get_order(h), order)
+    # normal and oblique incidence, both with a field component tangential to the plate
+    B = np.stack([P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0]),
+                  P.plane_wave([0.6, 0.0, -0.8], [0.8, 0.0, 0.6])], axis=1)
+    assert np.all(np.linalg.norm(B, axis=0) > 0)
+    if prec == 0:
+        X, its, rr, code = hm.solve(h, B, tol=1e-6, restart=50)
+        assert code == 0
+        for c in range(B.shape[1]):
+            xo, ito, rro, ok = krylov.solve(S, B[:, c], tol=1e-6, restart=50)
+            assert ok and abs(int(its[c]) - ito) <= 1
+            assert rel(X[:, c], xo) <= 1e-8
+    else:
+        X, its, rr, code = hm.solve(h, B, tol=3e-5, restart=50)
+        assert code == 0
+        for c in range(B.shape[1]):
+            xt = krylov.solve(S, B[:, c], tol=1e-10, restart=50)[0]
+            assert np.linalg.norm(B[:, c] - S.Z_orig(X[:, c])) / np.linalg.norm(B[:, c]) <= 3.1e-5
+            assert rel(X[:, c], xt) <= 1e-4
