@@ -62,6 +62,11 @@ def parse():
                     help="serving on two resident geometries (sphere30720 + plate29800), 360 requests each, "
                          "offered at 0.5/0.8/1.0x the measured throughput")
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--profile-op", type=int, default=0,
+                    help="profiling case: set up the workload, then apply the operator of Eq. 28 this many "
+                         "times to --nrhs columns (complex FP32 when --precision 1) and exit; no bench line")
+    ap.add_argument("--schedule", default="0,0",
+                    help="sweep schedule 'groups,kind' for --profile-op (0,0 = tuned)")
     return ap.parse_args()
 
 
@@ -485,7 +490,8 @@ def run_ours(args):
                                        if args.precision == 1 else "FP64, preconditioned residual", args.fill_tol),
                        "nrhs_per_step": B, "parallelism": "replicas x%d" % world,
                        "l2": "inputs larger than L2 (H-matrix %.2f GB, coefficients %.2f GB resident)" % (
-                           16e-9 * (stats["near_entries"] + stats["far_entries"]), 16e-9 * fs["nnzL"])},
+                           16e-9 * (stats["near_entries"] + stats["far_entries"]),
+                           (8e-9 if args.precision == 1 else 16e-9) * fs["nnzL"])},
             "setup_ms": setup_ms, "iters_mean": float(np.mean(iters)), "iters_max": int(np.max(iters)),
             "solve_rhs_per_s": B / max((ms_step - setup_ms) / 1e3, 1e-9),
             "roofline": roof, "roofline_kernel": cls,
@@ -500,8 +506,30 @@ def run_ours(args):
             f.write(s + "\n")
 
 
+def run_profile_op(args):
+    """A short, deterministic case for ncu captures (no timing of its own)."""
+    import torch
+    import paper_2111_13483_gb300 as hm
+    P = load_problem(args.workload, 0, 1)
+    h = hm.hmat_create(P, ordering=1, fill_tol=args.fill_tol, precision=args.precision)
+    hm.precond_setup(h)
+    g, k = (int(v) for v in args.schedule.split(","))
+    hm.hmsolve.hm_set_sweep_schedule(h, g, k)
+    x = torch.randn(args.nrhs, P.n, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    op = hm.hmsolve.OP32 + hm.hmsolve.OP_A if args.precision == 1 else hm.hmsolve.OP_A
+    for _ in range(args.profile_op):
+        hm.hm_apply(h, op, x, y)
+    torch.cuda.synchronize()
+    print("profile-op done: %s, %d x A on %d columns, coef entries %d" % (
+        args.workload, args.profile_op, args.nrhs, hm.hmat_stats(h)["coef_entries"]), flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_op > 0:
+        run_profile_op(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
