@@ -214,6 +214,25 @@ def roofline(prof, fs, stats, n, precision):
     return cls, entry(0.0, 16.0 * n * max(cols, 1) * 2, {})
 
 
+def traffic_record(cls, workload, precision):
+    """Measured DRAM bytes per launch of `cls` from a profile summary, if it was taken on the
+    current sources of that kernel (else None): (bytes, columns, source file)."""
+    import glob
+    import hashlib
+    src = b"".join(open(os.path.join(ROOT, "paper_2111_13483_gb300", "csrc", f), "rb").read()
+                   for f in ("ops.cu", "tile.cuh"))
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            if not line.startswith("traffic-record:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:])
+            if (kv.get("class") == cls and kv.get("workload") == workload and int(kv.get("precision", -1)) == precision
+                    and kv.get("source") == digest):
+                return int(kv["bytes"]), int(kv["columns"]), os.path.relpath(path, ROOT)
+    return None
+
+
 def serving_run(hm, serve, h, P, requests, rate, tol, restart, seed_rhs=2, seed_arr=1):
     """Poisson-arrival serving on one resident geometry: requests (monostatic plane waves,
     host memory) submitted at their arrival times, continuous batching up to 64 slots."""
@@ -413,6 +432,12 @@ def run_ours(args):
     value = B * args.steps * world / (ms_total / 1e3)
     iters = np.concatenate(iters_all[-args.steps:])
     cls, roof = roofline(prof, fs, stats, P.n, args.precision)
+    tr = traffic_record(cls, args.workload, args.precision)
+    if tr is not None:
+        roof["traffic"] = tr[0]
+        roof["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one %d-column launch (%s); "
+                                "bytes_per_launch above is the algorithmic count at the mean columns per launch"
+                                % (tr[1], tr[2]))
 
     # ---- serving: Poisson arrivals into the continuous-batching engine ------------------
     serving = None
