@@ -146,7 +146,7 @@ int precond_setup(hm_handle h);
  * column's place is taken by the next (the hm_batch engine below).  A column's result
  * does not depend on the others.  HM_ENOCONV if some column did not converge within
  * maxit (its best iterate is still written).  In mixed mode the inner solves run to
- * min(0.5, max(1e-7, 0.3 tol ||V|| / ||V - Z I||)) and at most 40 refinement passes are
+ * min(0.5, max(1e-7, 0.6 tol ||V|| / ||V - Z I||)) and at most 40 refinement passes are
  * made.
  */
 int solve(hm_handle h, const hm_c128 *V, int32_t nrhs, int64_t ldv, double tol, int32_t restart,

@@ -11,7 +11,7 @@
 // FP64 mode: GMRES on A x~ = c with the FP64 operator, stop at |g_{j+1}| <= tol ||c||.
 // Mixed mode: an outer FP64 loop r = V - Z I (near blocks + far factors in FP64), inner
 // GMRES on A d~ = D^{-1} L^{-1} r with the complex-FP32 operator to the tolerance
-// clamp(0.3 tol ||V|| / ||r||, 1e-7, 0.5), I += L^{-T} d~, until ||V - Z I|| <= tol ||V||.
+// clamp(0.6 tol ||V|| / ||r||, 1e-7, 0.5), I += L^{-T} d~, until ||V - Z I|| <= tol ||V||.
 // Krylov vectors, Gram-Schmidt, Givens rotations and the refinement residual are FP64 in
 // both modes.
 #include <algorithm>
@@ -478,7 +478,7 @@ struct Engine {
                     z.status = HM_ENOCONV;
                 } else {
                     // ask the inner solve for a little more than what is still missing
-                    z.itol = std::min(0.5, std::max(1e-7, 0.3 * z.tol / z.rel));
+                    z.itol = std::min(0.5, std::max(1e-7, 0.6 * z.tol / z.rel));
                     z.in_max = std::max(z.maxit - z.it, 1);
                     go.push_back(c);
                 }
