@@ -161,19 +161,26 @@ class Server:
             g.batch.close()
 
 
-def monostatic_requests(prob, count, seed, phi_step_deg=1.0):
-    """Right-hand sides of a monostatic sweep: theta = 90 deg, phi = 0, 1, ... deg, the
-    polarisation theta-hat (VV) or phi-hat (HH) drawn per request from a seeded generator.
+def monostatic_requests(prob, count, seed, phi_step_deg=1.0, plane="xy"):
+    """Right-hand sides of a monostatic sweep: observation directions at phi = 0, 1, ... deg in
+    the xy plane (theta = 90 deg), the polarisation theta-hat (VV) or phi-hat (HH) drawn per
+    request from a seeded generator.  plane="xz" sweeps the same angles in the xz plane
+    (direction (cos phi, 0, sin phi), VV in that plane, HH = y-hat): for a plate in the xy
+    plane this is the horizontal sweep of the same plate standing upright.
     Returns a list of (phi_deg, pol, V)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         phi = np.deg2rad(i * phi_step_deg)
-        rhat = np.array([np.cos(phi), np.sin(phi), 0.0])
+        if plane == "xy":
+            rhat = np.array([np.cos(phi), np.sin(phi), 0.0])
+            pv, ph = np.array([0.0, 0.0, -1.0]), np.array([-np.sin(phi), np.cos(phi), 0.0])
+        else:
+            rhat = np.array([np.cos(phi), 0.0, np.sin(phi)])
+            pv, ph = np.array([-np.sin(phi), 0.0, np.cos(phi)]), np.array([0.0, 1.0, 0.0])
         khat = -rhat                                     # incident from the observation direction
         pol = "VV" if rng.integers(2) == 0 else "HH"
-        p = np.array([0.0, 0.0, -1.0]) if pol == "VV" else np.array([-np.sin(phi), np.cos(phi), 0.0])
-        out.append((i * phi_step_deg, pol, prob.plane_wave(khat, p)))
+        out.append((i * phi_step_deg, pol, prob.plane_wave(khat, pv if pol == "VV" else ph)))
     return out
 
 
