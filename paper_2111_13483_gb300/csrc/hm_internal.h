@@ -206,6 +206,7 @@ struct hm_ctx {
     // kept in FP64 in d_Dinv) and FP32 copies of the far factors for the inner operator
     float2 *d_W32 = nullptr, *d_Ad32 = nullptr, *d_Dinv32 = nullptr, *d_farU32 = nullptr, *d_farV32 = nullptr;
     float2 *d_t32 = nullptr, *d_s32 = nullptr, *d_work32 = nullptr;
+    uint4 *d_ytag = nullptr;   // tagged sweep results (complex FP32 sweeps), n x 64
     int t32_cols = 0;
     bool batch_open = false;   // an hm_batch holds this handle
     hm::SweepTune sweep_tune[2][2][5];   // [FP32][forward][width class]

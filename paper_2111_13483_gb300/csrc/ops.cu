@@ -87,12 +87,57 @@ __device__ __forceinline__ int next_chunk(int p, int pend, int step, const int *
 // M_b y_b, with M_b = W_ko^T (forward, W_ko at Wsrc, nc x no column-major) or W_oj
 // (backward, no x nc column-major).  The CTA stages each chunk's coefficient blocks before
 // waiting on the chunk's ready flags, then the vector blocks, then runs the tile products.
-template <class T, int TR, int TC, int NT, bool FWD>
+// Tagged publication (complex FP32): next to y, every entry is also written as two 8-byte
+// words (value half, launch epoch) -- each naturally aligned 8-byte store is observed whole
+// -- so a consumer validates the data it reads instead of waiting on a flag behind a fence.
+__device__ __forceinline__ uint4 ld_tag(const uint4 *p)
+{
+    uint4 v;
+    asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+template <int SB = 8, class Addr, class St>
+__device__ __forceinline__ void stage_tagged(int count, unsigned epoch, int *err, Addr &&addr, St &&st)
+{
+    for (int e0 = threadIdx.x; e0 < count; e0 += SB * blockDim.x) {
+        uint4 v[SB];
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < count) v[u] = ld_tag(addr(e));
+        }
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= count) continue;
+            if (v[u].y != epoch || v[u].w != epoch) {   // not yet published: poll (bounded)
+                const unsigned long long t0 = gtimer();
+                while (v[u].y != epoch || v[u].w != epoch) {
+                    if (*(volatile int *)err) break;   // a wait already expired: stop waiting
+                    if (gtimer() - t0 > WAIT_NS) {
+                        atomicCAS(err, 0, ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                    v[u] = ld_tag(addr(e));
+                }
+            }
+            st(e, make_float2(__uint_as_float(v[u].x), __uint_as_float(v[u].z)));
+        }
+    }
+}
+
+template <class T, int TR, int TC, int NT, bool FWD, bool LL = false>
 __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, const int *boff, const int *lptr,
                                           const int *lidx, const int *lcol, const int64_t *coff, const T *W,
                                           const T *x, T *y, int n, int nrhs, int budget, int *flags, int epoch,
-                                          int *err, T *buf, int cut = 0, int *pub = nullptr)
+                                          int *err, T *buf, int cut = 0, int *pub = nullptr, uint4 *tag = nullptr)
 {
+    // LL (complex FP32 only): dependencies are read from, and the result published to, the
+    // tagged copy `tag` (same layout as y); no flags, no fence
     // cut > 0: leave the last `cut` dependencies of the walk out (they are added by the
     // chain CTA of a chain-and-helpers sweep) and publish the partial sum on `pub`
     if (!pub) pub = flags;
@@ -123,15 +168,22 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
             }
             off += stage_need(no, nc, nrhs, TR, TC);
         }
-        if (threadIdx.x == 0)
-            for (int b = p; b != q; b += step) wait_ready(flags, lidx[b], epoch, err);
-        __syncthreads();
+        if (!LL) {
+            if (threadIdx.x == 0)
+                for (int b = p; b != q; b += step) wait_ready(flags, lidx[b], epoch, err);
+            __syncthreads();
+        }
         off = 0;
         for (int b = p; b != q; b += step) {
             const int k = lidx[b], nc = size[k], ok = boff[k];
             T *Ys = buf + off + nc * ldw;
-            stage_copy(nc * nrhs, [&](int e) { return ldcg(y + ok + e % nc + (int64_t)(e / nc) * n); },
-                       [&](int e, T v) { Ys[e] = v; });
+            if constexpr (LL)
+                stage_tagged((int)(nc * nrhs), (unsigned)epoch, err,
+                             [&](int e) { return tag + ok + e % nc + (int64_t)(e / nc) * n; },
+                             [&](int e, float2 v) { Ys[e] = v; });
+            else
+                stage_copy(nc * nrhs, [&](int e) { return ldcg(y + ok + e % nc + (int64_t)(e / nc) * n); },
+                           [&](int e, T v) { Ys[e] = v; });
             off += stage_need(no, nc, nrhs, TR, TC);
         }
         __syncthreads();
@@ -145,6 +197,23 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
         p = q;
     }
     tile_store(acc, y + o, 1, n, no, nrhs, nrt, ntiles);
+    if constexpr (LL) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int tile = threadIdx.x + t * blockDim.x;
+            const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+#pragma unroll
+            for (int a = 0; a < TR; ++a)
+#pragma unroll
+                for (int c = 0; c < TC; ++c)
+                    if (tile < ntiles && row0 + a < no && r0 + c < nrhs) {
+                        const float2 v = acc.v[t][a][c];
+                        tag[o + row0 + a + (int64_t)(r0 + c) * n] =
+                            make_uint4(__float_as_uint(v.x), (unsigned)epoch, __float_as_uint(v.y), (unsigned)epoch);
+                    }
+        }
+        return;
+    }
     // publish: the barrier orders every thread's stores before thread 0's fence and flag
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -163,7 +232,8 @@ template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, const int *boff, const int *rptr,
                                                    const int *ridx, const int *rcol, const int64_t *coff,
                                                    const T *W, const T *x, T *y, int n, int nrhs, int G, int gw,
-                                                   int budget, int *flags, int epoch, int *ticket, int *err)
+                                                   int budget, int *flags, int epoch, int *ticket, int *err,
+                                                   uint4 *tag)
 {
     extern __shared__ unsigned char smraw[];
     __shared__ int s_t;
@@ -172,8 +242,10 @@ __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, cons
     const int i = s_t / G, g = s_t % G;
     if (i >= nb) return;
     const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
-    sweep_row<T, TR, TC, NT, true>(i, size[i], size, boff, rptr, ridx, rcol, coff, W, x + (int64_t)c0 * n,
-                                   y + (int64_t)c0 * n, n, nc, budget, flags + g * nb, epoch, err, (T *)smraw);
+    sweep_row<T, TR, TC, NT, true, sizeof(T) == 8>(i, size[i], size, boff, rptr, ridx, rcol, coff, W,
+                                                   x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
+                                                   flags + g * nb, epoch, err, (T *)smraw, 0, nullptr,
+                                                   tag + (int64_t)c0 * n);
 }
 
 // y = L^{-T} x : y_k = x_k - sum_{j in S_k} W_kj y_j   (Eq. 24); j walked downwards
@@ -181,7 +253,8 @@ template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, const int *boff, const int *sptr,
                                                    const int *sidx, const int *srow, const int64_t *coff,
                                                    const T *W, const T *x, T *y, int n, int nrhs, int G, int gw,
-                                                   int budget, int *flags, int epoch, int *ticket, int *err)
+                                                   int budget, int *flags, int epoch, int *ticket, int *err,
+                                                   uint4 *tag)
 {
     extern __shared__ unsigned char smraw[];
     __shared__ int s_t;
@@ -190,8 +263,10 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, cons
     const int k = nb - 1 - s_t / G, g = s_t % G;
     if (k < 0) return;
     const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
-    sweep_row<T, TR, TC, NT, false>(k, size[k], size, boff, sptr, sidx, srow, coff, W, x + (int64_t)c0 * n,
-                                    y + (int64_t)c0 * n, n, nc, budget, flags + g * nb, epoch, err, (T *)smraw);
+    sweep_row<T, TR, TC, NT, false, sizeof(T) == 8>(k, size[k], size, boff, sptr, sidx, srow, coff, W,
+                                                    x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
+                                                    flags + g * nb, epoch, err, (T *)smraw, 0, nullptr,
+                                                    tag + (int64_t)c0 * n);
 }
 
 // Chain-and-helpers sweep.  The dependencies of block row b are split: the `recent` ones,
@@ -696,12 +771,12 @@ static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, cons
         HM_LAUNCH(h, K_SWEEP_FWD,
                   (k_sweep_fwd<T, TR, TC, NT><<<grid, 256, smem, h->stream>>>(
                       P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs, G,
-                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err, h->d_ytag)));
     else
         HM_LAUNCH(h, K_SWEEP_BWD,
                   (k_sweep_bwd<T, TR, TC, NT><<<grid, 256, smem, h->stream>>>(
                       P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs, G,
-                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err, h->d_ytag)));
     return cudaGetLastError();
 }
 
@@ -922,6 +997,10 @@ cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs)
         if ((e = h->arena.alloc((void **)&h->d_s32, sizeof(float2) * tl * nrhs))) return e;
         if ((e = h->arena.alloc((void **)&h->d_work32, sizeof(float2) * (size_t)n * 5 * nrhs))) return e;
         h->t32_cols = nrhs;
+    }
+    if (h->opts.precision == 1 && !h->d_ytag) {   // tagged sweep results, 64 columns, epochs start at 1
+        if ((e = h->arena.alloc((void **)&h->d_ytag, sizeof(uint4) * (size_t)n * 64))) return e;
+        if ((e = cudaMemsetAsync(h->d_ytag, 0, sizeof(uint4) * (size_t)n * 64, h->stream))) return e;
     }
     static bool attr = false;
     if (!attr) {
