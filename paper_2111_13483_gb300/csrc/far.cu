@@ -7,8 +7,8 @@
 //
 // Phase 1 (k_far_t): the rank vectors t_b = V_b^T u[c-range] and s_b = U_b^T u[r-range].
 // Factor columns that contract over the same index range are stacked (up to 64 per task),
-// so one CTA stages each 64-row piece of u once for all of them and runs a register-tiled
-// product (tile.cuh); t and s are stored interleaved like u.
+// so one CTA stages each piece of u once for all of them (cp.async, double buffered) and
+// runs a register-tiled product (tile.cuh); t and s are stored interleaved like u.
 // Phase 2 (k_far_y): one CTA per leaf accumulates, in the order of the leaf's list of
 // covering far blocks, U_b t_b (row side), V_b s_b (column side), B u (dense row side) and
 // B^T u (dense column side) for the leaf's rows; the host plan cuts the list into
@@ -29,15 +29,30 @@ namespace {
 constexpr int SEG = 64;   // longest staged contraction segment
 }
 
+// Phase 1: one CTA per task (a range [lo, hi) and up to 64 stacked factor columns).  The
+// range is walked in pieces of FAR_T1 rows, each piece's factor rows and vector rows copied
+// with cp.async into the two halves of shared memory in turn, so the copy of the next piece
+// overlaps the product of the current; every output sums its rows in ascending order.
+constexpr int FAR_T1 = 32;
+
+template <class T> __device__ __forceinline__ void far_cp(T *dst, const T *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_far_t(const int *task_lo, const int *task_hi, const int *task_ptr,
                                                const int64_t *item_off, const int *item_ld, const int *item_rank,
                                                const int *item_row, const int *item_isv, const T *U, const T *V,
-                                               const T *u, int nrhs, T *t, T *s)
+                                               const T *u, int nrhs, T *t, T *s, int budget)
 {
     extern __shared__ unsigned char smraw[];
-    T *buf = (T *)smraw;
     __shared__ int s_item[64], s_l[64];
+    __shared__ const T *s_src[64];
     __shared__ int s_R;
     const int task = blockIdx.x;
     const int lo = task_lo[task], hi = task_hi[task], i0 = task_ptr[task], i1 = task_ptr[task + 1];
@@ -47,6 +62,7 @@ __global__ void __launch_bounds__(256) k_far_t(const int *task_lo, const int *ta
             for (int l = 0; l < item_rank[it] && R < 64; ++l, ++R) {
                 s_item[R] = it;
                 s_l[R] = l;
+                s_src[R] = (item_isv[it] ? V : U) + item_off[it] + (int64_t)l * item_ld[it];
             }
         s_R = R;
     }
@@ -54,33 +70,44 @@ __global__ void __launch_bounds__(256) k_far_t(const int *task_lo, const int *ta
     const int R = s_R;
     const int nrt = (R + TR - 1) / TR, ntiles = nrt * ((nrhs + TC - 1) / TC);
     const int ldw = stage_ldw(R, TR), ldr = stage_ldr(nrhs, TC);
+    T *const bufs[2] = {(T *)smraw, (T *)smraw + budget / 2};
     Tile<T, TR, TC, NT> acc;
     tile_load(acc, (const T *)nullptr, 0, 0, R, nrhs, nrt, ntiles);
-    for (int c0 = lo; c0 < hi; c0 += SEG) {
-        const int ch = min(SEG, hi - c0);
-        T *Ws = buf, *Ys = buf + ch * ldw;
-        stage_copy(
-            ch * R,
-            [&](int e) {
-                const int rr = e / ch, it = s_item[rr];
-                return ((item_isv[it] ? V : U) + item_off[it] + (int64_t)s_l[rr] * item_ld[it])[c0 - lo + e % ch];
-            },
-            [&](int e, T v) { Ws[(e % ch) * ldw + e / ch] = v; });
+    // copy piece [c0, c0 + ch) into bufs[which]: Ws[qq*ldw + rr] = factor rr at row c0 + qq,
+    // Ys[qq*ldr + r] = u[(c0 + qq) * nrhs + r]
+    auto stage = [&](int c0, int which) {
+        const int ch = min(FAR_T1, hi - c0);
+        T *Ws = bufs[which], *Ys = bufs[which] + ch * ldw;
+        for (int e = threadIdx.x; e < ch * R; e += blockDim.x) {
+            const int qq = e % ch, rr = e / ch;
+            far_cp(Ws + qq * ldw + rr, s_src[rr] + (c0 - lo + qq));
+        }
         const T *uc = u + (int64_t)c0 * nrhs;
-        stage_copy(ch * nrhs, [&](int e) { return uc[e]; }, [&](int e, T v) { Ys[(e / nrhs) * ldr + e % nrhs] = v; });
+        for (int e = threadIdx.x; e < ch * nrhs; e += blockDim.x) far_cp(Ys + (e / nrhs) * ldr + e % nrhs, uc + e);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    if (lo < hi) stage(lo, 0);
+    for (int c0 = lo, it = 0; c0 < hi; c0 += FAR_T1, ++it) {
+        const int ch = min(FAR_T1, hi - c0);
+        if (c0 + FAR_T1 < hi) {
+            stage(c0 + FAR_T1, (it + 1) & 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        tile_mac<false>(acc, Ws, ldw, Ys, ldr, 1, ch, nrt, ntiles);
+        T *Ws = bufs[it & 1];
+        tile_mac<false>(acc, Ws, ldw, Ws + ch * ldw, ldr, 1, ch, nrt, ntiles);
         __syncthreads();
     }
 #pragma unroll
     for (int tt = 0; tt < NT; ++tt) {
-        const int tile = threadIdx.x + tt * blockDim.x;
-        const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+        const TileRC m = tile_rc<TR, TC>(threadIdx.x + tt * blockDim.x, nrt, ntiles);
+        const int row0 = m.row0, r0 = m.c0;
 #pragma unroll
         for (int a = 0; a < TR; ++a)
 #pragma unroll
             for (int c = 0; c < TC; ++c)
-                if (tile < ntiles && row0 + a < R && r0 + c < nrhs) {
+                if (m.ok && row0 + a < R && r0 + c < nrhs) {
                     const int it = s_item[row0 + a];
                     T *dst = item_isv[it] ? t : s;
                     dst[(int64_t)(item_row[it] + s_l[row0 + a]) * nrhs + r0 + c] = acc.v[tt][a][c];
@@ -217,7 +244,7 @@ template <class T> struct FarLaunch {
             HM_LAUNCH(h, K_FAR1,
                       (k_far_t<T, TR, TC, NT><<<ntask, 256, smem, h->stream>>>(
                           h->d_p1_lo, h->d_p1_hi, h->d_p1_ptr, h->d_p1_off, h->d_p1_ld, h->d_p1_rank, h->d_p1_row,
-                          h->d_p1_isv, U, V, ucl, nrhs, t, s)));
+                          h->d_p1_isv, U, V, ucl, nrhs, t, s, budget)));
         T *part = (T *)h->d_farpart;
         HM_LAUNCH(h, K_FAR2,
                   (k_far_y<T, TR, TC, NT><<<h->nl * FAR_PARTS, 256, smem, h->stream>>>(

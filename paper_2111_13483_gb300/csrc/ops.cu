@@ -200,13 +200,13 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
     if constexpr (LL) {
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int tile = threadIdx.x + t * blockDim.x;
-            const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+            const TileRC tm = tile_rc<TR, TC>(threadIdx.x + t * blockDim.x, nrt, ntiles);
+            const int row0 = tm.row0, r0 = tm.c0;
 #pragma unroll
             for (int a = 0; a < TR; ++a)
 #pragma unroll
                 for (int c = 0; c < TC; ++c)
-                    if (tile < ntiles && row0 + a < no && r0 + c < nrhs) {
+                    if (tm.ok && row0 + a < no && r0 + c < nrhs) {
                         const float2 v = acc.v[t][a][c];
                         tag[o + row0 + a + (int64_t)(r0 + c) * n] =
                             make_uint4(__float_as_uint(v.x), (unsigned)epoch, __float_as_uint(v.y), (unsigned)epoch);
@@ -380,13 +380,13 @@ __device__ void chain_run(int nb, const int *size, const int *boff, const int *r
         Tile<T, TR, TC, NT> acc;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int tile = threadIdx.x + t * blockDim.x;
-            const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+            const TileRC tm = tile_rc<TR, TC>(threadIdx.x + t * blockDim.x, nrt, ntiles);
+            const int row0 = tm.row0, r0 = tm.c0;
 #pragma unroll
             for (int a = 0; a < TR; ++a)
 #pragma unroll
                 for (int c = 0; c < TC; ++c)
-                    acc.v[t][a][c] = (tile < ntiles && row0 + a < nb_ && r0 + c < nc)
+                    acc.v[t][a][c] = (tm.ok && row0 + a < nb_ && r0 + c < nc)
                                          ? ldcg(y + o + row0 + a + (int64_t)(r0 + c) * n)
                                          : czero(T());
         }
@@ -403,9 +403,9 @@ __device__ void chain_run(int nb, const int *size, const int *boff, const int *r
             woff += nk * nb_;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
-                const int tile = threadIdx.x + t * blockDim.x;
-                if (tile < ntiles) {
-                    const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+                const TileRC tm = tile_rc<TR, TC>(threadIdx.x + t * blockDim.x, nrt, ntiles);
+                if (tm.ok) {
+                    const int row0 = tm.row0, r0 = tm.c0;
 #pragma unroll 4
                     for (int qq = 0; qq < nk; ++qq) {
                         T w[TR], yv[TC];
@@ -426,13 +426,13 @@ __device__ void chain_run(int nb, const int *size, const int *boff, const int *r
         T *slot = ring + (q % (SWEEP_T + 1)) * slot_sz;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int tile = threadIdx.x + t * blockDim.x;
-            const int row0 = (tile % nrt) * TR, r0 = (tile / nrt) * TC;
+            const TileRC tm = tile_rc<TR, TC>(threadIdx.x + t * blockDim.x, nrt, ntiles);
+            const int row0 = tm.row0, r0 = tm.c0;
 #pragma unroll
             for (int a = 0; a < TR; ++a)
 #pragma unroll
                 for (int c = 0; c < TC; ++c)
-                    if (tile < ntiles && row0 + a < nb_ && r0 + c < nc) {
+                    if (tm.ok && row0 + a < nb_ && r0 + c < nc) {
                         slot[(r0 + c) * nb_ + row0 + a] = acc.v[t][a][c];
                         y[o + row0 + a + (int64_t)(r0 + c) * n] = acc.v[t][a][c];
                     }
@@ -522,15 +522,15 @@ __global__ void __launch_bounds__(256) k_sweep_sr(int nb, int nsr, const int *si
     Tile<T, TR, TC, NT> acc;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-        const int tile = threadIdx.x + t * blockDim.x;
-        const int row0 = (tile % nrt) * TR, q0 = (tile / nrt) * TC;
+        const TileRC tm = tile_rc<TR, TC>(threadIdx.x + t * blockDim.x, nrt, ntiles);
+        const int row0 = tm.row0, q0 = tm.c0;
 #pragma unroll
         for (int a = 0; a < TR; ++a) {
             const int row = row0 + a, s = member(row);
             const int64_t gr = row < no ? boff[mb[s]] + row - R[s] : 0;
 #pragma unroll
             for (int c = 0; c < TC; ++c)
-                acc.v[t][a][c] = (tile < ntiles && row < no && q0 + c < nc) ? x[gr + (int64_t)(q0 + c) * n] : czero(T());
+                acc.v[t][a][c] = (tm.ok && row < no && q0 + c < nc) ? x[gr + (int64_t)(q0 + c) * n] : czero(T());
         }
     }
     // external dependencies, in the stored order
@@ -580,12 +580,12 @@ __global__ void __launch_bounds__(256) k_sweep_sr(int nb, int nsr, const int *si
         const bool more = s + 1 < nm;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int tile = threadIdx.x + t * blockDim.x;
-            const int row0 = (tile % nrt) * TR, q0 = (tile / nrt) * TC;
+            const TileRC tm = tile_rc<TR, TC>(threadIdx.x + t * blockDim.x, nrt, ntiles);
+            const int row0 = tm.row0, q0 = tm.c0;
 #pragma unroll
             for (int a = 0; a < TR; ++a) {
                 const int row = row0 + a;
-                if (tile < ntiles && row >= R[s] && row < R[s + 1]) {
+                if (tm.ok && row >= R[s] && row < R[s + 1]) {
                     const int64_t gr = boff[mb[s]] + row - R[s];
 #pragma unroll
                     for (int c = 0; c < TC; ++c)
