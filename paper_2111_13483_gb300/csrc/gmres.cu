@@ -40,28 +40,29 @@ struct VRef {
 
 // part[((p*ldp + i) * nchunk + chunk)] = sum over the chunk's rows of conj(basis_i) w, i < J[p]
 // (J == nullptr: one vector)
-__global__ void __launch_bounds__(256) k_dots(int n, VRef basis, const int *J, VRef w, double2 *part, int nchunk,
-                                              int ldp)
+__global__ void __launch_bounds__(256, 2) k_dots(int n, VRef basis, const int *J, VRef w, double2 *part, int nchunk,
+                                                 int ldp)
 {
-    __shared__ double2 red[8][33];
+    constexpr int QB = 16;   // vectors per pass (16 accumulators per thread: two CTAs per SM)
+    __shared__ double2 red[8][QB + 1];
     const int chunk = blockIdx.x, p = blockIdx.y;
     const int lo = chunk * DOT_CHUNK, hi = min(n, lo + DOT_CHUNK);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int Jp = J ? J[p] : 1;
     const double2 *wc = w.at(p);
-    for (int i0 = 0; i0 < Jp; i0 += 32) {
-        const int ni = min(32, Jp - i0);
-        double2 acc[32];
+    for (int i0 = 0; i0 < Jp; i0 += QB) {
+        const int ni = min(QB, Jp - i0);
+        double2 acc[QB];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] = make_double2(0, 0);
+        for (int q = 0; q < QB; ++q) acc[q] = make_double2(0, 0);
         for (int row = lo + threadIdx.x; row < hi; row += blockDim.x) {
             double2 wv = wc[row];
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
+            for (int q = 0; q < QB; ++q)
                 if (q < ni) acc[q] = cjfma(basis.at(p, i0 + q)[row], wv, acc[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < QB; ++q) {
             if (q >= ni) break;
             double2 v = acc[q];
             for (int o = 16; o > 0; o >>= 1) {

@@ -10,8 +10,9 @@
 //                       their transposes (Sec. 3.2);
 //   Dinv + doff[k]      D_k^{-1} for the Eq. 28 preconditioner.
 // Step k: pivot inverse (one CTA), panel (M_k/64 CTAs), Schur updates
-// A_ij -= A_ik W_kj for i >= j in S_k (Eq. 19; one CTA per block pair, diagonal blocks
-// in full).  Stream order gives the step dependencies.
+// A_ij -= A_ik W_kj for i >= j in S_k (Eq. 19; diagonal blocks in full; one CTA per block
+// pair in FP64, one CTA per row block and group of up to 8 column blocks in FP32).  Stream
+// order gives the step dependencies.
 //
 // S is the storage and arithmetic type of A, the diagonal blocks and W: complex FP64, or
 // complex FP32 in the mixed-precision setup, where the pivot blocks are still inverted in
@@ -303,6 +304,155 @@ __global__ void __launch_bounds__(256) k_update(int k, int ns, const int *size, 
         update_tile<S, QC, 4>(As, Ws, Aik, Mk, Wkj, nk, ni, nj, C, ldc);
 }
 
+// Grouped Schur updates of step k for the complex-FP32 setup.  CTA -> (a, g): row block a
+// of S_k and the column blocks b = g*gb .. min(a, g*gb + gb - 1).  For each, C_ij -= A_ik W_kj
+// with the thread layout and q order of update_tile, so the result is bitwise that of
+// k_update, on a tile fitted to the block in steps of 16 rows and columns (update_tile pads
+// to 32 x 32 or 64 x 64: up to 5x the useful FMAs for uneven pairs).  A_ik is staged once
+// per CTA, the W_kj blocks stream through two cp.async buffers (the copy of the next overlaps
+// the product of the current) and each C block's old values are loaded before its product,
+// so their latency hides behind the FMAs.
+constexpr int UPD_LD = 65;
+constexpr size_t UPD_SMEM = sizeof(float2) * 3 * 64 * UPD_LD;   // A_ik + two W_kj buffers
+
+// CTAs of the rows a' < a: sum over m = 1..a of ceil(m / gb)
+__host__ __device__ __forceinline__ long upd_first(int a, int gb)
+{
+    const long q = a / gb, r = a % gb;
+    return (long)gb * q * (q + 1) / 2 + r * (q + 1);
+}
+
+__device__ __forceinline__ void upd_cp(float2 *dst, const float2 *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// C (ni x nj) -= A W on a (16 UR) x (16 UC) tile, UR = ceil(ni / 16), UC = ceil(nj / 16):
+// thread (tx, ty) owns rows tx + 16u and columns ty + 16v, as in update_tile.
+template <int UR, int UC>
+__device__ __forceinline__ void upd_product(const float2 (*As)[UPD_LD], const float2 (*Ws)[UPD_LD], int nk, int ni,
+                                            int nj, float2 *C, int ldc)
+{
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float2 old[UR][UC], acc[UR][UC];
+#pragma unroll
+    for (int u = 0; u < UR; ++u)
+#pragma unroll
+        for (int v = 0; v < UC; ++v) {
+            const int r = tx + 16 * u, c = ty + 16 * v;
+            old[u][v] = (r < ni && c < nj) ? C[r + (int64_t)c * ldc] : czero(float2());
+            acc[u][v] = czero(float2());
+        }
+    for (int q = 0; q < nk; ++q) {
+        float2 av[UR], wv[UC];
+#pragma unroll
+        for (int u = 0; u < UR; ++u) av[u] = As[q][tx + 16 * u];
+#pragma unroll
+        for (int v = 0; v < UC; ++v) wv[v] = Ws[q][ty + 16 * v];
+#pragma unroll
+        for (int u = 0; u < UR; ++u)
+#pragma unroll
+            for (int v = 0; v < UC; ++v) acc[u][v] = cfma(av[u], wv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < UR; ++u)
+#pragma unroll
+        for (int v = 0; v < UC; ++v) {
+            const int r = tx + 16 * u, c = ty + 16 * v;
+            if (r < ni && c < nj) {
+                float2 o = old[u][v];
+                o.x -= acc[u][v].x;
+                o.y -= acc[u][v].y;
+                C[r + (int64_t)c * ldc] = o;
+            }
+        }
+}
+
+__global__ void __launch_bounds__(256, 2) k_update_grp(int k, int ns, int gb, const int *size, const int *sptr,
+                                                       const int *sidx, const int *srow, const int *M,
+                                                       const int64_t *coff, const int64_t *doff, const float2 *W,
+                                                       float2 *A, float2 *Ad)
+{
+    extern __shared__ float2 upd_sm[];
+    float2(*As)[UPD_LD] = (float2(*)[UPD_LD])upd_sm;   // As[q][r] = A_ik[r, q], rows >= n_i zero
+    // W buffer w: Ws[q][c] = W_kj[q, c], columns >= n_j zero up to the tile size
+    auto wbuf = [&](int w) { return (float2(*)[UPD_LD])(upd_sm + (1 + w) * 64 * UPD_LD); };
+    const long t = blockIdx.x;
+    int lo = 0, hi = ns;   // largest a with upd_first(a) <= t
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (upd_first(mid, gb) <= t) lo = mid;
+        else hi = mid;
+    }
+    const int a = lo, b0 = (int)(t - upd_first(a, gb)) * gb, b1 = min(a + 1, b0 + gb);
+    if (b0 > a) return;   // cannot happen: row a has ceil((a + 1) / gb) groups
+    const int e0 = sptr[k], i = sidx[e0 + a], nk = size[k], ni = size[i], Mk = M[k];
+    const float2 *Aik = A + coff[k] + srow[e0 + a];   // ld Mk; panel k is not written in this step
+    for (int e = threadIdx.x; e < 64 * nk; e += blockDim.x) {
+        const int r = e & 63, q = e >> 6;
+        if (r < ni) upd_cp(&As[q][r], Aik + r + (int64_t)q * Mk);
+        else As[q][r] = czero(float2());
+    }
+    auto stage_w = [&](int b, int buf) {
+        const int nj = size[sidx[e0 + b]];
+        const float2 *Wkj = W + coff[k] + (int64_t)srow[e0 + b] * nk;   // ld nk
+        const int ts = (nj + 15) / 16 * 16;
+        float2(*Ws)[UPD_LD] = wbuf(buf);
+        for (int e = threadIdx.x; e < nk * ts; e += blockDim.x) {
+            const int q = e % nk, c = e / nk;
+            if (c < nj) upd_cp(&Ws[q][c], Wkj + q + (int64_t)c * nk);
+            else Ws[q][c] = czero(float2());
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    stage_w(b0, 0);   // one group with the A_ik copies
+    for (int b = b0, it = 0; b < b1; ++b, ++it) {
+        if (b + 1 < b1) {
+            stage_w(b + 1, (it + 1) & 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        const int j = sidx[e0 + b], nj = size[j];
+        float2 *C = nullptr;
+        int ldc = 0;
+        if (i == j) {
+            C = Ad + doff[i];
+            ldc = ni;
+        } else {
+            const int r = find_row(sptr, sidx, srow, j, i);   // >= 0 when S is the symbolic fill
+            if (r >= 0) {
+                C = A + coff[j] + r;
+                ldc = M[j];
+            }
+        }
+        if (C) {
+            const float2(*Ws)[UPD_LD] = wbuf(it & 1);
+            switch (((ni - 1) >> 4) * 4 + ((nj - 1) >> 4)) {   // (UR - 1) * 4 + (UC - 1)
+#define HM_UPD(R, C_) \
+    case (R - 1) * 4 + (C_ - 1): upd_product<R, C_>(As, Ws, nk, ni, nj, C, ldc); break;
+                HM_UPD(1, 1) HM_UPD(1, 2) HM_UPD(1, 3) HM_UPD(1, 4)
+                HM_UPD(2, 1) HM_UPD(2, 2) HM_UPD(2, 3) HM_UPD(2, 4)
+                HM_UPD(3, 1) HM_UPD(3, 2) HM_UPD(3, 3) HM_UPD(3, 4)
+                HM_UPD(4, 1) HM_UPD(4, 2) HM_UPD(4, 3) HM_UPD(4, 4)
+#undef HM_UPD
+            default: break;   // block sizes are 1..64
+            }
+        }
+        __syncthreads();   // the buffer is restaged two products later
+    }
+}
+
+// Column blocks per CTA of the grouped update: the most (up to 8) that still leaves at least
+// four CTAs per SM.
+static int upd_group(int ns, int nsm)
+{
+    int gb = 8;
+    while (gb > 1 && upd_first(ns, gb) < 4L * nsm) gb >>= 1;
+    return gb;
+}
+
 template <class S>
 static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *Dinv32, int *bad_block)
 {
@@ -324,6 +474,9 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
         return e;
     if ((e = cudaFuncSetAttribute(k_panel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem)))
         return e;
+    if ((e = cudaFuncSetAttribute(k_update_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UPD_SMEM))) return e;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
     for (int k = 0; k < P.nb; ++k) {
         int nk = P.size[k];
         HM_LAUNCH(h, K_PIVOT,
@@ -335,10 +488,19 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
             HM_LAUNCH(h, K_PANEL,
                       k_panel<S><<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff,
                                                                           DinvS, A, W));
-            long nt = (long)ns * (ns + 1) / 2;
-            HM_LAUNCH(h, K_UPDATE,
-                      k_update<S><<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx, h->d_srow,
-                                                                h->d_M, h->d_coff, h->d_doff, W, A, Ad));
+            if constexpr (sizeof(S) == 8) {
+                const int gb = upd_group(ns, nsm);
+                HM_LAUNCH(h, K_UPDATE,
+                          k_update_grp<<<(unsigned)upd_first(ns, gb), 256, UPD_SMEM, st>>>(
+                              k, ns, gb, h->d_size, h->d_sptr, h->d_sidx, h->d_srow, h->d_M, h->d_coff, h->d_doff,
+                              W, A, Ad));
+            } else {
+                long nt = (long)ns * (ns + 1) / 2;
+                HM_LAUNCH(h, K_UPDATE,
+                          k_update<S><<<(unsigned)nt, 256, 0, st>>>(k, ns, h->d_size, h->d_sptr, h->d_sidx,
+                                                                    h->d_srow, h->d_M, h->d_coff, h->d_doff, W, A,
+                                                                    Ad));
+            }
         }
         if ((e = cudaGetLastError())) return e;
     }
