@@ -99,6 +99,9 @@ __device__ __forceinline__ uint4 ld_tag(const uint4 *p)
     return v;
 }
 
+// Staging copy from the tagged array: SB words per thread are loaded together; while any of
+// them still carries another epoch, those are loaded again together (one round trip per
+// retry, bounded by WAIT_NS, given up once *err is set).
 template <int SB = 8, class Addr, class St>
 __device__ __forceinline__ void stage_tagged(int count, unsigned epoch, int *err, Addr &&addr, St &&st)
 {
@@ -109,23 +112,32 @@ __device__ __forceinline__ void stage_tagged(int count, unsigned epoch, int *err
             const int e = e0 + u * blockDim.x;
             if (e < count) v[u] = ld_tag(addr(e));
         }
+        bool timing = false;
+        unsigned long long t0 = 0;
+        for (;;) {
+            unsigned stale = 0;
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                const int e = e0 + u * blockDim.x;
+                if (e < count && (v[u].y != epoch || v[u].w != epoch)) stale |= 1u << u;
+            }
+            if (!stale || *(volatile int *)err) break;   // all current, or a wait already expired
+            if (!timing) {
+                timing = true;
+                t0 = gtimer();
+            } else if (gtimer() - t0 > WAIT_NS) {
+                atomicCAS(err, 0, ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+#pragma unroll
+            for (int u = 0; u < SB; ++u)
+                if (stale & (1u << u)) v[u] = ld_tag(addr(e0 + u * blockDim.x));
+        }
 #pragma unroll
         for (int u = 0; u < SB; ++u) {
             const int e = e0 + u * blockDim.x;
-            if (e >= count) continue;
-            if (v[u].y != epoch || v[u].w != epoch) {   // not yet published: poll (bounded)
-                const unsigned long long t0 = gtimer();
-                while (v[u].y != epoch || v[u].w != epoch) {
-                    if (*(volatile int *)err) break;   // a wait already expired: stop waiting
-                    if (gtimer() - t0 > WAIT_NS) {
-                        atomicCAS(err, 0, ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(32);
-                    v[u] = ld_tag(addr(e));
-                }
-            }
-            st(e, make_float2(__uint_as_float(v[u].x), __uint_as_float(v[u].z)));
+            if (e < count) st(e, make_float2(__uint_as_float(v[u].x), __uint_as_float(v[u].z)));
         }
     }
 }
@@ -196,24 +208,21 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
         __syncthreads();
         p = q;
     }
-    tile_store(acc, y + o, 1, n, no, nrhs, nrt, ntiles);
     if constexpr (LL) {
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const TileRC tm = tile_rc<TR, TC>(threadIdx.x + t * blockDim.x, nrt, ntiles);
-            const int row0 = tm.row0, r0 = tm.c0;
-#pragma unroll
-            for (int a = 0; a < TR; ++a)
-#pragma unroll
-                for (int c = 0; c < TC; ++c)
-                    if (tm.ok && row0 + a < no && r0 + c < nrhs) {
-                        const float2 v = acc.v[t][a][c];
-                        tag[o + row0 + a + (int64_t)(r0 + c) * n] =
-                            make_uint4(__float_as_uint(v.x), (unsigned)epoch, __float_as_uint(v.y), (unsigned)epoch);
-                    }
+        // the block goes through shared memory (free after the last product) so that the
+        // tagged words, which the consumers wait on, leave first and coalesced (a warp writes
+        // 32 consecutive rows of a column); y follows
+        tile_store(acc, buf, 1, no, no, nrhs, nrt, ntiles);   // buf[r * no + row]
+        __syncthreads();
+        for (int e = threadIdx.x; e < no * nrhs; e += blockDim.x) {
+            const float2 v = buf[e];
+            tag[o + e % no + (int64_t)(e / no) * n] =
+                make_uint4(__float_as_uint(v.x), (unsigned)epoch, __float_as_uint(v.y), (unsigned)epoch);
         }
+        for (int e = threadIdx.x; e < no * nrhs; e += blockDim.x) y[o + e % no + (int64_t)(e / no) * n] = buf[e];
         return;
     }
+    tile_store(acc, y + o, 1, n, no, nrhs, nrt, ntiles);
     // publish: the barrier orders every thread's stores before thread 0's fence and flag
     __syncthreads();
     if (threadIdx.x == 0) {
