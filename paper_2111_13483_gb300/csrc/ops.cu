@@ -83,6 +83,34 @@ __device__ __forceinline__ int next_chunk(int p, int pend, int step, const int *
     return q;
 }
 
+template <class T> __device__ __forceinline__ void cp_async_el(T *dst, const T *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// Complex-FP32 sweeps: a chunk's contraction length is at most 64, so its coefficient blocks
+// fit one of two buffers of SW_WCAP entries (64 x stage_ldw(64)) and its vector blocks a
+// 64 x stage_ldr(nrhs) area; the shared memory of a row is 2 SW_WCAP + 64 stage_ldr entries.
+constexpr int SW_WCAP = 64 * 65;
+
+__device__ __forceinline__ int next_chunk_ll(int p, int pend, int step, const int *dep, const int *size)
+{
+    const int tail0 = pend - TAIL * step;
+    if ((step > 0 && p >= tail0) || (step < 0 && p <= tail0)) return p + step;
+    int q = p, used = 0;
+    while (q != tail0) {
+        const int nc = size[dep[q]];
+        if (used > 0 && used + nc > 64) break;
+        used += nc;
+        q += step;
+    }
+    return q;
+}
+
 // One block row of a sweep (Eqs. 23, 24): out = x_o - sum over the dependency list of
 // M_b y_b, with M_b = W_ko^T (forward, W_ko at Wsrc, nc x no column-major) or W_oj
 // (backward, no x nc column-major).  The CTA stages each chunk's coefficient blocks before
@@ -162,7 +190,67 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
     const int step = FWD ? 1 : -1;
     const int pa = FWD ? lptr[o_blk] : lptr[o_blk + 1] - 1,
               pend = (FWD ? lptr[o_blk + 1] : lptr[o_blk] - 1) - cut * step;
-    for (int p = pa; p != pend;) {
+    if constexpr (LL) {
+        // the coefficient blocks of the next chunk are copied (cp.async, no registers held)
+        // into the other buffer while the current chunk waits for its vector blocks and
+        // multiplies, so the copies of static data stay off the wait-to-publish path
+        T *const ys = buf + 2 * SW_WCAP;
+        auto wbuf = [&](int w) { return buf + w * SW_WCAP; };
+        auto stage_w = [&](int p, int q, T *dst) {
+            int off = 0;
+            for (int b = p; b != q; b += step) {
+                const int k = lidx[b], nc = size[k];
+                T *Ws = dst + off;
+                if (FWD) {   // W_ko: nc x no at coff[k] + lcol*nc; M(row, qq) = W_ko(qq, row)
+                    const T *src = W + coff[k] + (int64_t)lcol[b] * nc;
+                    for (int e = threadIdx.x; e < nc * no; e += blockDim.x)
+                        cp_async_el(Ws + (e % nc) * ldw + e / nc, src + e);
+                } else {     // W_oj: no x nc at coff[o] + lcol*no; M(row, qq) = W_oj(row, qq)
+                    const T *src = W + coff[o_blk] + (int64_t)lcol[b] * no;
+                    for (int e = threadIdx.x; e < nc * no; e += blockDim.x)
+                        cp_async_el(Ws + (e / no) * ldw + e % no, src + e);
+                }
+                off += nc * ldw;
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        };
+        if (pa != pend) {
+            int p = pa, q = next_chunk_ll(pa, pend, step, lidx, size);
+            stage_w(p, q, wbuf(0));
+            for (int cur = 0; p != pend; cur ^= 1) {
+                int q2 = q;
+                if (q != pend) {
+                    q2 = next_chunk_ll(q, pend, step, lidx, size);
+                    stage_w(q, q2, wbuf(cur ^ 1));
+                }
+                int yoff = 0;
+                for (int b = p; b != q; b += step) {
+                    const int k = lidx[b], nc = size[k], ok = boff[k];
+                    T *Ys = ys + yoff;
+                    stage_tagged((int)(nc * nrhs), (unsigned)epoch, err,
+                                 [&](int e) { return tag + ok + e % nc + (int64_t)(e / nc) * n; },
+                                 [&](int e, float2 v) { Ys[e] = v; });
+                    yoff += nc * nrhs;
+                }
+                if (q != pend) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                __syncthreads();
+                const T *wc = wbuf(cur);
+                int woff = 0;
+                yoff = 0;
+                for (int b = p; b != q; b += step) {
+                    const int nc = size[lidx[b]];
+                    tile_mac<true>(acc, wc + woff, ldw, ys + yoff, 1, nc, nc, nrt, ntiles);
+                    woff += nc * ldw;
+                    yoff += nc * nrhs;
+                }
+                __syncthreads();
+                p = q;
+                q = q2;
+            }
+        }
+    }
+    for (int p = pa; !LL && p != pend;) {
         const int q = next_chunk<TR, TC>(p, pend, step, lidx, size, no, nrhs, budget);
         // stage the coefficient blocks (static data) before waiting
         int off = 0;
@@ -180,22 +268,15 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
             }
             off += stage_need(no, nc, nrhs, TR, TC);
         }
-        if (!LL) {
-            if (threadIdx.x == 0)
-                for (int b = p; b != q; b += step) wait_ready(flags, lidx[b], epoch, err);
-            __syncthreads();
-        }
+        if (threadIdx.x == 0)
+            for (int b = p; b != q; b += step) wait_ready(flags, lidx[b], epoch, err);
+        __syncthreads();
         off = 0;
         for (int b = p; b != q; b += step) {
             const int k = lidx[b], nc = size[k], ok = boff[k];
             T *Ys = buf + off + nc * ldw;
-            if constexpr (LL)
-                stage_tagged((int)(nc * nrhs), (unsigned)epoch, err,
-                             [&](int e) { return tag + ok + e % nc + (int64_t)(e / nc) * n; },
-                             [&](int e, float2 v) { Ys[e] = v; });
-            else
-                stage_copy(nc * nrhs, [&](int e) { return ldcg(y + ok + e % nc + (int64_t)(e / nc) * n); },
-                           [&](int e, T v) { Ys[e] = v; });
+            stage_copy(nc * nrhs, [&](int e) { return ldcg(y + ok + e % nc + (int64_t)(e / nc) * n); },
+                       [&](int e, T v) { Ys[e] = v; });
             off += stage_need(no, nc, nrhs, TR, TC);
         }
         __syncthreads();
@@ -301,14 +382,6 @@ __device__ __forceinline__ int recent_count(int b, const int *lptr, const int *l
 
 constexpr int CHAIN_WCAP = 4096;   // entries of each coefficient staging buffer of a chain CTA
 
-template <class T> __device__ __forceinline__ void cp_async_el(T *dst, const T *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if constexpr (sizeof(T) == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
 
 // What the chain CTA needs about one block row: loaded one step ahead (independent loads),
 // so that their latency overlaps the current step.
@@ -759,18 +832,23 @@ template <class T> static int max_cols() { return sizeof(T) == 16 ? 16 : 64; }
 
 // Register tile per group width: (TR, TC, NT) = (1, 1, 1) up to 4 columns, (2, 2, 1) up
 // to 16, (2, 4, 2) up to 64 (complex FP32 only); 256 threads cover every output tile of a
-// 64-row block.  The shared memory of a CTA holds one chunk: at least one 64 x 64
-// coefficient block with its vector block.
+// 64-row block (a 2 x 2 tile at 17-32 columns measured 2% slower).  Shared memory: FP64,
+// one chunk (at least one 64 x 64 coefficient block with its vector block); complex FP32,
+// see SW_WCAP.
 template <class T, int TR, int TC, int NT>
 static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs, int G,
                                int gw, int ep, int maxw)
 {
     Plan &P = h->plan;
-    const int budget = stage_need(64, 64, gw, TR, TC);
+    // complex FP32: two coefficient buffers and a vector area (sweep_row); FP64: one chunk
+    auto need = [](int w) {
+        return sizeof(T) == 8 ? 2 * SW_WCAP + 64 * stage_ldr(w, TC) : stage_need(64, 64, w, TR, TC);
+    };
+    const int budget = need(gw);
     const size_t smem = sizeof(T) * (size_t)budget;
     static bool attr = false;
     if (!attr) {
-        const int smax = (int)(sizeof(T) * (size_t)stage_need(64, 64, maxw, TR, TC));
+        const int smax = (int)(sizeof(T) * (size_t)need(maxw));
         cudaFuncSetAttribute(k_sweep_fwd<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         cudaFuncSetAttribute(k_sweep_bwd<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         attr = true;
