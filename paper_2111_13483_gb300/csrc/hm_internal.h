@@ -100,7 +100,7 @@ struct FarSegD {
     int fi, fk, len, src;
 };
 
-constexpr int FAR_PARTS = 4;
+constexpr int FAR_PARTS = 8;
 
 // far-field incidence lists (cluster order): per leaf l, entries (b << 2 | kind), kind
 // 0 = low-rank row side, 1 = low-rank column side, 2 = dense row side, 3 = dense column side
