@@ -231,14 +231,26 @@ def roofline(prof, fs, stats, n, precision):
     return cls, entry(0.0, 16.0 * n * max(cols, 1) * 2, {})
 
 
+def sweep_code_digest(texts=None):
+    """Key of the sweep kernels' code: sha256 (first 16 hex digits) of ops.cu + tile.cuh with
+    comments and whitespace removed, so that an edit of comments keeps a measurement valid
+    and any code change invalidates it."""
+    import hashlib
+    import re
+    if texts is None:
+        texts = [open(os.path.join(ROOT, "paper_2111_13483_gb300", "csrc", f)).read() for f in ("ops.cu", "tile.cuh")]
+    code = "".join(texts)
+    code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+    code = re.sub(r"//[^\n]*", " ", code)
+    code = re.sub(r"\s+", " ", code).strip()
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def traffic_record(cls, workload, precision):
     """Measured DRAM bytes per launch of `cls` from a profile summary, if it was taken on the
-    current sources of that kernel (else None): (bytes, columns, source file)."""
+    current code of that kernel (sweep_code_digest; else None): (bytes, columns, source file)."""
     import glob
-    import hashlib
-    src = b"".join(open(os.path.join(ROOT, "paper_2111_13483_gb300", "csrc", f), "rb").read()
-                   for f in ("ops.cu", "tile.cuh"))
-    digest = hashlib.sha256(src).hexdigest()[:16]
+    digest = sweep_code_digest()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             if not line.startswith("traffic-record:"):

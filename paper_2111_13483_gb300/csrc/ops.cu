@@ -113,11 +113,14 @@ __device__ __forceinline__ int next_chunk_ll(int p, int pend, int step, const in
 
 // One block row of a sweep (Eqs. 23, 24): out = x_o - sum over the dependency list of
 // M_b y_b, with M_b = W_ko^T (forward, W_ko at Wsrc, nc x no column-major) or W_oj
-// (backward, no x nc column-major).  The CTA stages each chunk's coefficient blocks before
-// waiting on the chunk's ready flags, then the vector blocks, then runs the tile products.
-// Tagged publication (complex FP32): next to y, every entry is also written as two 8-byte
-// words (value half, launch epoch) -- each naturally aligned 8-byte store is observed whole
-// -- so a consumer validates the data it reads instead of waiting on a flag behind a fence.
+// (backward, no x nc column-major).  FP64: the CTA stages each chunk's coefficient blocks
+// before waiting on the chunk's ready flags, then the vector blocks, then runs the tile
+// products.  Complex FP32: the coefficient blocks of the next chunk are copied with cp.async
+// while the current chunk waits and multiplies, and the vector blocks come from the tagged
+// copy.  Tagged publication (complex FP32): next to y, every entry is also written as two
+// 8-byte words (value half, launch epoch) -- each naturally aligned 8-byte store is observed
+// whole -- so a consumer validates the data it reads instead of waiting on a flag behind a
+// fence.
 __device__ __forceinline__ uint4 ld_tag(const uint4 *p)
 {
     uint4 v;

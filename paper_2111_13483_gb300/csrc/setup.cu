@@ -213,8 +213,8 @@ __global__ void __launch_bounds__(256) k_panel(int k, const int *size, const int
     }
 }
 
-// Schur updates of step k (Eq. 19): one CTA per pair (a >= b) of S_k, A_ij -= A_ik W_kj,
-// in S arithmetic.  C (ni x nj) -= A (ni x nk) W (nk x nj) on a 16U x 16U tile: thread
+// Schur updates of step k (Eq. 19), FP64 setup: one CTA per pair (a >= b) of S_k,
+// A_ij -= A_ik W_kj, in S arithmetic (the FP32 setup uses k_update_grp below).  C (ni x nj) -= A (ni x nk) W (nk x nj) on a 16U x 16U tile: thread
 // (tx, ty) owns rows tx + 16u and columns ty + 16v (u, v < U).  The shared tiles are
 // zero-padded to the tile size, so every thread runs the same unpredicated FMA sequence;
 // padded outputs are dropped.

@@ -1,0 +1,60 @@
+"""Host-side logic of bench.py (no GPU): the key that ties a measured DRAM-traffic record to
+the sweep kernels' code, the record lookup, and the roofline entry's choice of bound."""
+import os
+
+import pytest
+
+import bench
+
+
+def test_sweep_code_digest_ignores_comments_and_whitespace():
+    a = bench.sweep_code_digest(["int a = 1;  // one\n", "/* block\n comment */ float b;\n"])
+    b = bench.sweep_code_digest(["int a = 1;\n\n", "  float   b;"])
+    assert a == b
+    assert bench.sweep_code_digest(["int a = 2;", "float b;"]) != a   # a code change is seen
+
+
+def _tree(tmp_path, code, records):
+    csrc = tmp_path / "paper_2111_13483_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "ops.cu").write_text(code)
+    (csrc / "tile.cuh").write_text("// tile\nint t;\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k.md").write_text("# summary\n\n" + "\n".join(records) + "\n")
+
+
+def test_traffic_record_lookup(tmp_path, monkeypatch):
+    code = "__global__ void k() {}\n"
+    digest = bench.sweep_code_digest([code, "// tile\nint t;\n"])
+    _tree(tmp_path, code, [
+        "traffic-record: class=sweep_fwd workload=sphere30720 precision=1 columns=64 bytes=123 source=%s" % digest,
+        "traffic-record: class=sweep_bwd workload=sphere30720 precision=1 columns=64 bytes=456 source=0000",
+    ])
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    got = bench.traffic_record("sweep_fwd", "sphere30720", 1)
+    assert got is not None and got[0] == 123 and got[1] == 64 and got[2] == os.path.join("profiles", "k.md")
+    assert bench.traffic_record("sweep_bwd", "sphere30720", 1) is None      # taken on other code
+    assert bench.traffic_record("sweep_fwd", "sphere30720", 0) is None      # other precision
+    assert bench.traffic_record("sweep_fwd", "plate29800", 1) is None       # other workload
+    # a comment edit of the kernel source keeps the record valid
+    (tmp_path / "paper_2111_13483_gb300" / "csrc" / "ops.cu").write_text("// edited\n" + code)
+    assert bench.traffic_record("sweep_fwd", "sphere30720", 1)[0] == 123
+
+
+@pytest.mark.parametrize("cols, bound", [(64 * 10, "alu"), (1 * 10, "hbm")])
+def test_roofline_bound_follows_intensity(cols, bound):
+    # ten complex-FP32 sweep launches over a 1e6-entry panel; n = 1000
+    nnzL, n, launches = 1_000_000, 1000, 10
+    prof = {"sweep_fwd": (launches, launches, 20.0, cols), "dots": (5, 5, 1.0, 5)}
+    fs = {"nnzL": nnzL, "update_flops": 1.0, "update_launches": 1}
+    cls, r = bench.roofline(prof, fs, {"far_entries": 0}, n, 1)
+    assert cls == "sweep_fwd" and r["bound"] == bound
+    flops = 8.0 * nnzL * cols
+    bytes_ = 8.0 * (nnzL * launches + 2.0 * n * cols)
+    assert r["intensity_flop_per_byte"] == pytest.approx(flops / bytes_)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    if bound == "alu":
+        assert r["achieved"] == pytest.approx(flops / 0.020 / 1e12)
+    else:
+        assert r["achieved"] == pytest.approx(bytes_ / 0.020 / 1e9)
