@@ -87,6 +87,26 @@ def dist():
     return world, rank, local
 
 
+def max_over_ranks(ms, world):
+    """The largest of the ranks' values of a per-rank time (every rank gets it); the value
+    itself at world size 1.  Uses the initialised process group (NCCL on the GPU machine, gloo in
+    the CPU tests)."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as td
+    dev = "cuda" if td.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(B, steps, world, ms_total):
+    """Whole-job RHS/s of `world` independent replicas: the columns all ranks processed
+    (B per step each) over the slowest rank's time for the `steps` steps."""
+    return B * steps * world / (ms_total / 1e3)
+
+
 def rhs_batch(P, B, plate=False):
     """Monostatic plane waves, phi_j = 360 j / B: theta = 90 deg with VV (theta-hat)
     polarisation; for a plate (in the xy plane) the same sweep in the xz plane, i.e. the
@@ -455,12 +475,9 @@ def run_ours(args):
     hm.hm_profile(h, 0)
     launches = int(sum(v[0] for v in prof.values()))
     setup_ms = hm.hmat_stats(h)["setup_ms"]
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    value = B * args.steps * world / (ms_total / 1e3)
+    value = replica_value(B, args.steps, world, ms_total)
     iters = np.concatenate(iters_all[-args.steps:])
     cls, roof = roofline(prof, fs, stats, P.n, args.precision)
     tr = traffic_record(cls, args.workload, args.precision)
@@ -538,11 +555,8 @@ def run_ours(args):
         a1.record(stream)
         torch.cuda.synchronize()
         ems = a0.elapsed_time(a1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": B * args.e2e_steps * world / (ems / 1e3), "unit": "RHS/s", "h2d_bytes_per_step": int(h2d),
+        ems = max_over_ranks(ems, world)
+        e2e = {"value": replica_value(B, args.e2e_steps, world, ems), "unit": "RHS/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": ems / args.e2e_steps}
 
     if rank != 0:
