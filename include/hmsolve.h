@@ -313,6 +313,30 @@ int hm_plan_order(int32_t n_leaves, int32_t n_pairs, const int32_t *t, const int
 int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int32_t *j, int32_t *ptr,
                  int32_t *idx, int64_t idx_cap);
 
+/*
+ * The library's plan of the far-field product Z_F u (the U (V^T u) products of Sec. 2, Eq. 11,
+ * over the admissible blocks of Eq. 8) for the far blocks of an H-matrix description, in
+ * cluster order: the same checks as hmat_create on n, leaf_ptr and the far arrays (fields of
+ * hm_desc; far_U / far_V are not needed), no device work.  `what` selects one table, written
+ * as int64 rows into out:
+ *   0  seg_ptr, n_leaves + 1 entries: the phase-2 segments of leaf l are seg_ptr[l] ..
+ *      seg_ptr[l+1] - 1;
+ *   1  segments, 6 per segment (foff, yrow, fi, fk, len, src): for the leaf's rows a + i,
+ *      y[a + i] += sum_{k < len} F[foff + i*fi + k*fk] * Y[yrow + k], with F = far_V when
+ *      src & 1 else far_U, and Y = the rank vectors t (src >> 1 == 0), s (1) or u itself (2);
+ *   2  part_ptr, n_leaves * parts + 1 entries: part p of leaf l (one CTA) covers segments
+ *      part_ptr[l*parts + p] .. part_ptr[l*parts + p + 1] - 1;
+ *   3  phase-1 tasks, 4 per task (lo, hi, first item, end item): items contract over the
+ *      cluster-order range [lo, hi);
+ *   4  phase-1 items, 5 per item (off, ld, rank, row, isv): for l < rank,
+ *      (isv ? t : s)[row + l] = sum_{lo <= i < hi} (isv ? far_V : far_U)[off + l*ld + i - lo] * u[i].
+ * *count: in, the capacity of out in int64 entries; out, the entries of the table (always
+ * written).  out == NULL only queries the count.  HM_EINVAL on bad input or a too small out.
+ */
+int hm_plan_far(int32_t n, int32_t n_leaves, const int32_t *leaf_ptr, int32_t n_far, const int32_t *far_r0,
+                const int32_t *far_r1, const int32_t *far_c0, const int32_t *far_c1, const int32_t *far_rank,
+                const int64_t *far_uoff, const int64_t *far_voff, int32_t what, int64_t *out, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

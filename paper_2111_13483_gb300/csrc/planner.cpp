@@ -567,3 +567,57 @@ extern "C" int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i,
     }
     return HM_OK;
 }
+
+extern "C" int hm_plan_far(int32_t n, int32_t n_leaves, const int32_t *leaf_ptr, int32_t n_far, const int32_t *far_r0,
+                           const int32_t *far_r1, const int32_t *far_c0, const int32_t *far_c1,
+                           const int32_t *far_rank, const int64_t *far_uoff, const int64_t *far_voff, int32_t what,
+                           int64_t *out, int64_t *count)
+{
+    if (n <= 0 || n_leaves <= 0 || !leaf_ptr || n_far < 0 || !count || what < 0 || what > 4) return HM_EINVAL;
+    if (n_far > 0 && (!far_r0 || !far_r1 || !far_c0 || !far_c1 || !far_rank || !far_uoff || !far_voff))
+        return HM_EINVAL;
+    if (leaf_ptr[0] != 0 || leaf_ptr[n_leaves] != n) return HM_EINVAL;
+    std::vector<char> is_bound(n + 1, 0);
+    for (int l = 0; l < n_leaves; ++l) {
+        const int sz = leaf_ptr[l + 1] - leaf_ptr[l];
+        if (sz < 1 || sz > 64) return HM_EINVAL;
+        is_bound[leaf_ptr[l]] = 1;
+    }
+    is_bound[n] = 1;
+    for (int b = 0; b < n_far; ++b) {
+        const int r0 = far_r0[b], r1 = far_r1[b], c0 = far_c0[b], c1 = far_c1[b], r = far_rank[b];
+        if (r0 < 0 || r0 >= r1 || r1 > c0 || c0 >= c1 || c1 > n) return HM_EINVAL;
+        if (!is_bound[r0] || !is_bound[r1] || !is_bound[c0] || !is_bound[c1]) return HM_EINVAL;
+        if (r < -1 || r > std::min(r1 - r0, c1 - c0) || far_uoff[b] < 0 || far_voff[b] < 0) return HM_EINVAL;
+    }
+    hm_ctx h;   // host fields only: the planner does no device work
+    h.n = n;
+    h.nl = n_leaves;
+    h.leaf_ptr.assign(leaf_ptr, leaf_ptr + n_leaves + 1);
+    h.far_r0.assign(far_r0, far_r0 + n_far);
+    h.far_r1.assign(far_r1, far_r1 + n_far);
+    h.far_c0.assign(far_c0, far_c0 + n_far);
+    h.far_c1.assign(far_c1, far_c1 + n_far);
+    h.far_rank.assign(far_rank, far_rank + n_far);
+    h.far_uoff.assign(far_uoff, far_uoff + n_far);
+    h.far_voff.assign(far_voff, far_voff + n_far);
+    hm::plan_far(&h);
+    const hm::FarPlan &F = h.fplan;
+    std::vector<int64_t> v;
+    if (what == 0) v.assign(F.seg_ptr.begin(), F.seg_ptr.end());
+    if (what == 1)
+        for (const hm::FarSegD &g : F.segs) v.insert(v.end(), {g.foff, g.yrow, g.fi, g.fk, g.len, g.src});
+    if (what == 2) v.assign(F.part_ptr.begin(), F.part_ptr.end());
+    if (what == 3)
+        for (size_t t = 0; t < F.p1_lo.size(); ++t) v.insert(v.end(), {F.p1_lo[t], F.p1_hi[t], F.p1_ptr[t], F.p1_ptr[t + 1]});
+    if (what == 4)
+        for (size_t e = 0; e < F.p1_off.size(); ++e)
+            v.insert(v.end(), {F.p1_off[e], F.p1_ld[e], F.p1_rank[e], F.p1_row[e], F.p1_isv[e]});
+    const int64_t cap = *count;
+    *count = (int64_t)v.size();
+    if (out) {
+        if ((int64_t)v.size() > cap) return HM_EINVAL;
+        std::memcpy(out, v.data(), sizeof(int64_t) * v.size());
+    }
+    return HM_OK;
+}

@@ -60,7 +60,7 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
            "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
-           "hm_get_profile_cols"]
+           "hm_get_profile_cols", "hm_plan_far"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -101,6 +101,8 @@ def load(build_if_missing=True):
     L.hm_apply.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32]
     L.hm_plan_order.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]
     L.hm_plan_fill.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int64]
+    L.hm_plan_far.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p,
+                              _i64p, _i64p, ctypes.c_int32, _i64p, _i64p]
     L.hm_profile.argtypes = [vp, ctypes.c_int32]
     L.hm_get_profile.argtypes = [vp, ctypes.c_int32, _i64p, _i64p, _f64p]
     L.hm_far_apply_noalloc.argtypes = [vp, vp, vp, ctypes.c_int32]
@@ -290,6 +292,35 @@ def hm_plan_fill(n_blocks, i, j):
         raise HMError(code, "hm_plan_fill")
     return [idx[ptr[k]:ptr[k + 1]].tolist() for k in range(n_blocks)]
 
+
+
+def hm_plan_far(P):
+    """Host-only far-field plan of a problem description (no GPU), as numpy int64 tables:
+    seg_ptr, segs (foff, yrow, fi, fk, len, src), part_ptr, tasks (lo, hi, item0, item1),
+    items (off, ld, rank, row, isv); see hm_plan_far in the header."""
+    L = load()
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)
+    args = [i32(P.leaf_ptr), i32(P.far_r0), i32(P.far_r1), i32(P.far_c0), i32(P.far_c1), i32(P.far_rank),
+            i64(P.far_uoff), i64(P.far_voff)]
+    lp, r0, r1, c0, c1, rk, uo, vo = args
+    widths = {0: 1, 1: 6, 2: 1, 3: 4, 4: 5}
+    names = {0: "seg_ptr", 1: "segs", 2: "part_ptr", 3: "tasks", 4: "items"}
+    out = {}
+    for what, w in widths.items():
+        cnt = np.zeros(1, dtype=np.int64)
+        call = lambda buf: L.hm_plan_far(int(P.n), len(lp) - 1, _p(lp, _i32p), len(r0), _p(r0, _i32p), _p(r1, _i32p),
+                                         _p(c0, _i32p), _p(c1, _i32p), _p(rk, _i32p), _p(uo, _i64p), _p(vo, _i64p),
+                                         what, buf, _p(cnt, _i64p))
+        code = call(None)
+        if code != HM_OK:
+            raise HMError(code, "hm_plan_far")
+        tab = np.zeros(max(1, int(cnt[0])), dtype=np.int64)
+        code = call(_p(tab, _i64p))
+        if code != HM_OK:
+            raise HMError(code, "hm_plan_far")
+        out[names[what]] = tab[:int(cnt[0])].reshape(-1, w) if w > 1 else tab[:int(cnt[0])]
+    return out
 
 def hm_profile(h, mode):
     """mode 1: time every launch with CUDA events; 0: stop timing; 2: zero the counters."""
