@@ -146,8 +146,9 @@ int precond_setup(hm_handle h);
  * column's place is taken by the next (the hm_batch engine below).  A column's result
  * does not depend on the others.  HM_ENOCONV if some column did not converge within
  * maxit (its best iterate is still written).  In mixed mode the inner solves run to
- * min(0.5, max(1e-7, 0.6 tol ||V|| / ||V - Z I||)) and at most 40 refinement passes are
- * made.
+ * min(0.5, max(1e-7, 0.6 tol ||V|| / ||V - Z I||, 0.1 rho)), rho = the factor by which the
+ * last refinement pass reduced ||V - Z I|| (fill_tol before the first pass), and at most 40
+ * refinement passes are made.
  */
 int solve(hm_handle h, const hm_c128 *V, int32_t nrhs, int64_t ldv, double tol, int32_t restart,
           int32_t maxit, hm_c128 *I, int64_t ldi, int32_t *iters, double *relres);
@@ -230,7 +231,9 @@ int hm_get_profile_cols(hm_handle h, int32_t cls, int64_t *cols);
  * (1,048,576 complex doubles) held by every GPU that loads the library until exit; a call
  * needing more than n*nrhs + 2*sum(rank)*nrhs entries of it returns HM_EINVAL.  The first
  * call on a device looks up the array's device address: make it before any stream capture.
- * All calls share the array, so calls that overlap on the GPU race and must be serialised.
+ * The address is cached per device for the life of the process and belongs to the device's
+ * primary context as the first call found it: after cudaDeviceReset the library must be
+ * unloaded and loaded again before this call is used.  All calls share the array, so calls that overlap on the GPU race and must be serialised.
  * Synchronises the handle's stream before returning.
  */
 int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
@@ -246,6 +249,32 @@ int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
  * 3 apply to groups of at most 16 columns (kind 1 otherwise).  HM_EINVAL for other values.
  */
 int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind);
+
+/*
+ * Test hook for the bounded device-side waits of the sweeps (Eqs. 23, 24; the paper has no
+ * counterpart).  After this call every triangular sweep on the handle leaves block row
+ * `block` (solve order) out -- it is never computed or published -- and any single wait of a
+ * sweep on another block gives up after `wait_ns` nanoseconds (0 = the default bound of 2 s),
+ * so the operator or solve that contains the sweep returns HM_ETIMEOUT instead of hanging and
+ * the handle stays usable.  hm_test_hold(h, -1, 0) restores normal operation.  Synchronises
+ * the handle's stream first.  HM_EINVAL for block outside -1 .. n_blocks-1 or wait_ns < 0.
+ */
+int hm_test_hold(hm_handle h, int32_t block, int64_t wait_ns);
+
+/*
+ * One complex-FP32 block product C = A B, computed by the tensor-core micro-kernel that the
+ * complex-FP32 sweeps use for their block products (Eqs. 23, 24: y_i -= W_ki^T y_k and
+ * x_k -= W_kj y_j): tcgen05 MMAs on TF32 operands, each FP32 value split into a rounded TF32
+ * part and a TF32 remainder (three products per step, the remainder-times-remainder term
+ * dropped), accumulated in FP32 in tensor memory.  A is m x k, B is k x ncols, C is m x ncols,
+ * column-major, complex FP32 (interleaved re, im floats), device memory; 1 <= m <= 64,
+ * 1 <= ncols <= 64, k >= 0 (k = 0 writes zeros).  One CTA on `stream` (NULL = the legacy
+ * default stream); synchronises the stream before returning.  A column of C depends only on
+ * A and that column of B: it is bitwise the same for any ncols.  HM_EINVAL on bad sizes or
+ * leading dimensions (lda >= m, ldb >= k, ldc >= m), HM_ECUDA on a CUDA error.
+ */
+int hm_tc_cgemm(int32_t m, int32_t k, int32_t ncols, const void *dA, int64_t lda, const void *dB, int64_t ldb,
+                void *dC, int64_t ldc, void *stream);
 
 /* ---- continuous batching (serving) ---------------------------------------------------- */
 

@@ -225,9 +225,11 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
         delete h;
         return s;
     }
-    if ((e = h->arena.alloc((void **)&h->d_err, sizeof(int))) ||
+    int err_init[ERR_WORDS] = {0, -1, 0, 0};
+    std::memcpy(err_init + ERR_BOUND, &WAIT_NS_DEFAULT, sizeof(WAIT_NS_DEFAULT));
+    if ((e = h->arena.alloc((void **)&h->d_err, sizeof(int) * ERR_WORDS)) ||
         (e = h->arena.alloc((void **)&h->d_ticket, sizeof(int))) ||
-        (e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream)) ||
+        (e = cudaMemcpy(h->d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice)) ||
         (h->opts.precision == 1 && (e = make_fp32_copies(h))) || (e = cudaStreamSynchronize(h->stream))) {
         int s = cuda_fail(h, e, "hmat_create");
         h->arena.release_all();
@@ -474,6 +476,22 @@ int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind)
     if ((groups != 1 && groups != 2 && groups != 4) || (kind != 1 && kind != SWEEP_SR && kind != 3))
         return HM_EINVAL;
     h->sweep_fixed = groups | (kind << 4);
+    return HM_OK;
+}
+
+int hm_test_hold(hm_handle h, int32_t block, int64_t wait_ns)
+{
+    if (!h || block < -1 || block >= h->plan.nb || wait_ns < 0) return HM_EINVAL;
+    cudaSetDevice(h->dev);
+    int w[ERR_WORDS] = {0, block, 0, 0};
+    const unsigned long long ns = wait_ns ? (unsigned long long)wait_ns : WAIT_NS_DEFAULT;
+    std::memcpy(w + ERR_BOUND, &ns, sizeof(ns));
+    cudaError_t e;
+    // the stream first: no kernel of this handle may be reading the words while they change
+    if ((e = cudaStreamSynchronize(h->stream)) ||
+        (e = cudaMemcpy(h->d_err + ERR_HOLD, w + ERR_HOLD, sizeof(int) * (ERR_WORDS - ERR_HOLD),
+                        cudaMemcpyHostToDevice)))
+        return cuda_fail(h, e, "hm_test_hold");
     return HM_OK;
 }
 

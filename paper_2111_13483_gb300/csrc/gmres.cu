@@ -10,8 +10,12 @@
 //
 // FP64 mode: GMRES on A x~ = c with the FP64 operator, stop at |g_{j+1}| <= tol ||c||.
 // Mixed mode: an outer FP64 loop r = V - Z I (near blocks + far factors in FP64), inner
-// GMRES on A d~ = D^{-1} L^{-1} r with the complex-FP32 operator to the tolerance
-// clamp(0.6 tol ||V|| / ||r||, 1e-7, 0.5), I += L^{-T} d~, until ||V - Z I|| <= tol ||V||.
+// GMRES on A d~ = D^{-1} L^{-1} r with the complex-FP32 operator, I += L^{-T} d~, until
+// ||V - Z I|| <= tol ||V||.  The inner tolerance is clamp(max(0.6 tol ||V|| / ||r||, f),
+// 1e-7, 0.5): f = 0.1 rho, rho = ||r|| / ||r_prev|| the contraction the last pass achieved
+// (0.1 fill_tol before the first pass).  A pass cannot reduce the true residual by much more
+// than the mismatch between the inner operator (FP32, fill-in blocks compressed to fill_tol)
+// and Z allows, so solving the inner system further than that only costs iterations.
 // Krylov vectors, Gram-Schmidt, Givens rotations and the refinement residual are FP64 in
 // both modes.
 #include <algorithm>
@@ -278,7 +282,7 @@ struct Slot {
     int state = FREE;
     int j = 0, it = 0, it_in = 0, in_max = 0, outer = 0, maxit = 0, status = HM_OK;
     bool first = false, conv = false, reported = false;
-    double tol = 0, itol = 0, bn = 0, cn = 0, rel = 0;
+    double tol = 0, itol = 0, bn = 0, cn = 0, rel = 0, prev_rel = 0;
 };
 
 struct Engine {
@@ -478,8 +482,12 @@ struct Engine {
                     z.state = DONE;
                     z.status = HM_ENOCONV;
                 } else {
-                    // ask the inner solve for a little more than what is still missing
-                    z.itol = std::min(0.5, std::max(1e-7, 0.6 * z.tol / z.rel));
+                    // ask the inner solve for a little more than what is still missing, but not
+                    // for much more than one pass can gain (the contraction of the last pass, or
+                    // the fill compression tolerance before the first)
+                    const double rho = z.outer == 0 ? h->opts.fill_tol : std::min(1.0, z.rel / z.prev_rel);
+                    z.itol = std::min(0.5, std::max({1e-7, 0.6 * z.tol / z.rel, 0.1 * rho}));
+                    z.prev_rel = z.rel;
                     z.in_max = std::max(z.maxit - z.it, 1);
                     go.push_back(c);
                 }

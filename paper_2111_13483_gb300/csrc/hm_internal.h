@@ -224,6 +224,10 @@ struct hm_ctx {
 
 namespace hm {
 constexpr int ERR_TIMEOUT = 0x40000000;   // d_err bit: a bounded device-side wait expired
+// words of the handle's error block d_err (ERR_WORDS ints): the error code, the block row the
+// sweeps leave out (test hook, -1 = none) and the bound on one device-side wait (uint64 ns)
+constexpr int ERR_CODE = 0, ERR_HOLD = 1, ERR_BOUND = 2, ERR_WORDS = 4;
+constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ull;
 
 // planner.cpp
 int validate_and_copy(hm_ctx *h, const hm_desc *d);

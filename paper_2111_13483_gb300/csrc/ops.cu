@@ -27,7 +27,14 @@ namespace hm {
 
 namespace {
 
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
+// The handle's error word block: err[ERR_CODE] is set by a failing wait, err[ERR_HOLD] names a
+// block row the sweeps leave out (a test hook: -1 = none; every wait on that row then runs
+// out), err[ERR_BOUND..+1] holds the bound on any single wait in ns (2 s unless a test sets it).
+__device__ __forceinline__ unsigned long long wait_bound(const int *err)
+{
+    return __ldcg((const unsigned long long *)(err + ERR_BOUND));
+}
+__device__ __forceinline__ bool held_back(const int *err, int blk) { return __ldcg(err + ERR_HOLD) == blk; }
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -45,10 +52,10 @@ __device__ bool wait_ready(const int *flags, int k, int epoch, int *err)
         __threadfence();
         return true;
     }
-    unsigned long long t0 = gtimer();
+    const unsigned long long t0 = gtimer(), bound = wait_bound(err);
     while (*f != epoch) {
         if (*(volatile int *)err) return false;
-        if (gtimer() - t0 > WAIT_NS) {
+        if (gtimer() - t0 > bound) {
             atomicCAS(err, 0, ERR_TIMEOUT);
             return false;
         }
@@ -132,7 +139,7 @@ __device__ __forceinline__ uint4 ld_tag(const uint4 *p)
 
 // Staging copy from the tagged array: SB words per thread are loaded together; while any of
 // them still carries another epoch, those are loaded again together (one round trip per
-// retry, bounded by WAIT_NS, given up once *err is set).
+// retry, bounded by the handle's wait bound, given up once *err is set).
 template <int SB = 8, class Addr, class St>
 __device__ __forceinline__ void stage_tagged(int count, unsigned epoch, int *err, Addr &&addr, St &&st)
 {
@@ -156,7 +163,7 @@ __device__ __forceinline__ void stage_tagged(int count, unsigned epoch, int *err
             if (!timing) {
                 timing = true;
                 t0 = gtimer();
-            } else if (gtimer() - t0 > WAIT_NS) {
+            } else if (gtimer() - t0 > wait_bound(err)) {
                 atomicCAS(err, 0, ERR_TIMEOUT);
                 break;
             }
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, cons
     if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
     const int i = s_t / G, g = s_t % G;
-    if (i >= nb) return;
+    if (i >= nb || held_back(err, i)) return;
     const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
     sweep_row<T, TR, TC, NT, true, sizeof(T) == 8>(i, size[i], size, boff, rptr, ridx, rcol, coff, W,
                                                    x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
@@ -354,7 +361,7 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, cons
     if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
     const int k = nb - 1 - s_t / G, g = s_t % G;
-    if (k < 0) return;
+    if (k < 0 || held_back(err, k)) return;
     const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
     sweep_row<T, TR, TC, NT, false, sizeof(T) == 8>(k, size[k], size, boff, sptr, sidx, srow, coff, W,
                                                     x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
@@ -554,6 +561,7 @@ __global__ void __launch_bounds__(256) k_sweep_ch(int nb, const int *size, const
         return;
     }
     const int qpos = (t - G) / G, b = FWD ? qpos : nb - 1 - qpos;
+    if (held_back(err, b)) return;
     const int cut = recent_count<FWD>(b, lptr, lidx);
     sweep_row<T, TR, TC, NT, FWD>(b, size[b], size, boff, lptr, lidx, lcol, coff, W, x + (int64_t)c0 * n,
                                   y + (int64_t)c0 * n, n, nc, budget, ffin, epoch, err, (T *)smraw, cut, fpart);
@@ -594,6 +602,9 @@ __global__ void __launch_bounds__(256) k_sweep_sr(int nb, int nsr, const int *si
         if (q < nb) nm = s + 1;
         R[s + 1] = R[s] + (q < nb ? size[mb[s]] : 0);
     }
+#pragma unroll
+    for (int s = 0; s < SR; ++s)
+        if (mb[s] >= 0 && held_back(err, mb[s])) return;
     const int no = R[nm];
     const int nrt = (no + TR - 1) / TR, ntiles = nrt * ((nc + TC - 1) / TC);
     const int ldw = stage_ldw(no, TR);

@@ -60,7 +60,7 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
            "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
-           "hm_get_profile_cols", "hm_plan_far"]
+           "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -115,6 +115,9 @@ def load(build_if_missing=True):
     L.hm_batch_close.argtypes = [vp]
     L.hm_set_sweep_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     L.hm_get_profile_cols.argtypes = [vp, ctypes.c_int32, _i64p]
+    L.hm_test_hold.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
+    L.hm_tc_cgemm.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                              vp, ctypes.c_int64, vp]
     _lib = L
     return L
 
@@ -351,6 +354,21 @@ def hm_set_sweep_schedule(h, groups=0, kind=0):
     """Pins the sweep schedule (column groups 1/2/4; kind 1 row per CTA, 2 two rows, 3 chain +
     helpers); (0, 0) = tuned."""
     h.check(load().hm_set_sweep_schedule(h.ptr, groups, kind), "hm_set_sweep_schedule")
+
+
+def hm_test_hold(h, block=-1, wait_ns=0):
+    """Test hook: the sweeps leave block row ``block`` (solve order) out and every device-side
+    wait gives up after ``wait_ns`` (0 = the default 2 s); (-1, 0) restores normal operation."""
+    h.check(load().hm_test_hold(h.ptr, block, wait_ns), "hm_test_hold")
+
+
+def hm_tc_cgemm(dA, dB, dC, stream=None):
+    """C = A B on the tensor-core micro-kernel of the complex-FP32 sweeps.  Torch complex64
+    CUDA tensors, contiguous: dA (k, m), dB (ncols, k), dC (ncols, m) -- row j of each is column
+    j of the column-major matrix the library sees.  Returns the status code."""
+    k, m = dA.shape
+    nc = dB.shape[0]
+    return load().hm_tc_cgemm(m, k, nc, dA.data_ptr(), m, dB.data_ptr(), k, dC.data_ptr(), m, stream)
 
 
 def hm_get_fill_ranks(h):

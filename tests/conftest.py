@@ -25,3 +25,15 @@ def sphere480():
 def sphere1920():
     import efie_problem as ep
     return ep.build("sphere1920")
+
+
+@pytest.fixture(scope="session")
+def sphere7680():
+    import efie_problem as ep
+    return ep.build("sphere7680")
+
+
+@pytest.fixture(scope="session")
+def sphere30720():
+    import efie_problem as ep
+    return ep.build("sphere30720")
