@@ -53,6 +53,7 @@ WORKLOADS = {
     "sphere122880": "PEC sphere r=5 lambda, icosphere d=6, 122880 RWG unknowns, leaf 64, eta 1, ACA 1e-4",
     "sphere7680": "PEC sphere r=1.2 lambda, icosphere d=4, 7680 RWG unknowns, leaf 64, eta 1, ACA 1e-3",
 }
+ORDERINGS = {0: "cluster (no)", 1: "reverse Cuthill-McKee", 2: "Sloan"}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 FMA/clk/SM x 2 flop x max SM clock
 
@@ -76,6 +77,11 @@ def parse():
                          "(Eq. 28 GMRES to a preconditioned residual of --fp64-tol); 0 = skip")
     ap.add_argument("--fp64-tol", type=float, default=1e-4)
     ap.add_argument("--cpu-anchor-run", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--ordering", type=int, default=1, choices=[0, 1, 2],
+                    help="Algorithm 1 reordering: 0 none, 1 reverse Cuthill-McKee, 2 Sloan")
+    ap.add_argument("--compare-orderings", action="store_true",
+                    help="Sec. 3.3 Tables 3-4 style comparison on the workload: setup ms, coefficient entries, "
+                         "operator ms and iterations for no ordering, RCM and Sloan; prints one JSON line")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="0: complex FP64; 1: complex-FP32 operator inside FP64 refinement")
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -484,10 +490,11 @@ def bench_config(args, P, world=1):
     plate = args.workload.startswith("plate")
     hmat_gb = 16e-9 * (len(P.near_data) + len(P.far_U) + len(P.far_V))
     return {"workload": WORKLOADS.get(args.workload, args.workload) + "; %d plane-wave RHS per step (%s), "
-                        "GMRES(%d), fill_tol %g; solutions within 1e-4 of the FP64 solution: the mixed-precision "
-                        "path stops at ||V - Z I||/||V|| <= %g, the FP64 forms at a preconditioned residual of %g"
+                        "GMRES(%d), fill_tol %g, %s ordering; solutions within 1e-4 of the FP64 solution: the "
+                        "mixed-precision path stops at ||V - Z I||/||V|| <= %g, the FP64 forms at a preconditioned "
+                        "residual of %g"
                         % (args.nrhs, "xz-plane phi sweep, HH" if plate else "theta 90 deg, phi sweep, VV",
-                           args.restart, args.fill_tol, args.tol, args.fp64_tol),
+                           args.restart, args.fill_tol, ORDERINGS[args.ordering], args.tol, args.fp64_tol),
             "nrhs_per_step": args.nrhs, "parallelism": "replicas x%d" % world,
             "l2": "inputs larger than L2 (H-matrix %.2f GB resident)" % hmat_gb}
 
@@ -532,7 +539,7 @@ def run_ours(args):
     plate = args.workload.startswith("plate")
     Vh = rhs_batch(P, B, plate)
     stream = torch.cuda.current_stream()
-    h = hm.hmat_create(P, ordering=1, fill_tol=args.fill_tol, precision=args.precision, device=local,
+    h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision, device=local,
                        stream=stream.cuda_stream)
     stats = hm.hmat_stats(h)
     dV = torch.from_numpy(np.ascontiguousarray(Vh.T)).to("cuda")
@@ -607,7 +614,7 @@ def run_ours(args):
         if args.fp64_rhs > 0:
             # the paper's arithmetic: FP64 setup (fill_tol as the headline) and GMRES(restart)
             # to a preconditioned residual of fp64_tol, one right-hand side per solve
-            g = hm.hmat_create(P, ordering=1, fill_tol=args.fill_tol, precision=0, device=local,
+            g = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=0, device=local,
                                stream=stream.cuda_stream)
             hm.precond_setup(g)           # first call allocates the factors
             hm.precond_setup(g)
@@ -683,7 +690,7 @@ def run_ours(args):
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for _ in range(args.e2e_steps):
-            g = hm.hmat_create(Q, ordering=1, fill_tol=args.fill_tol, precision=args.precision, device=local,
+            g = hm.hmat_create(Q, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision, device=local,
                                stream=stream.cuda_stream)
             hm.precond_setup(g)
             I, it2, rr2, code = hm.solve(g, Vp.numpy().T, tol=args.tol, restart=args.restart, maxit=5000)
@@ -725,12 +732,51 @@ def run_ours(args):
             f.write(s + "\n")
 
 
+def run_compare_orderings(args):
+    """Sec. 3.3 (Tables 3-4) on the workload, per ordering: setup ms (second call), block
+    bandwidth, coefficient blocks and entries, ms of one Eq. 28 operator application at 1 and
+    at --nrhs columns, and the iterations of one solve (the first right-hand side of the
+    bench batch)."""
+    import torch
+    import paper_2111_13483_gb300 as hm
+    P = load_problem(args.workload, 0, 1)
+    plate = args.workload.startswith("plate")
+    V = rhs_batch(P, args.nrhs, plate)
+    op = hm.hmsolve.OP32 + hm.hmsolve.OP_A if args.precision == 1 else hm.hmsolve.OP_A
+    out = {"workload": args.workload, "precision": args.precision, "fill_tol": args.fill_tol, "orderings": {}}
+    for o in (0, 1, 2):
+        h = hm.hmat_create(P, ordering=o, fill_tol=args.fill_tol, precision=args.precision)
+        hm.precond_setup(h)
+        hm.precond_setup(h)
+        st = hm.hmat_stats(h)
+        times = {}
+        for w in (1, args.nrhs):
+            x = torch.randn(w, P.n, dtype=torch.complex128, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(3):
+                hm.hm_apply(h, op, x, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                hm.hm_apply(h, op, x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            times["op_ms_%d_cols" % w] = e0.elapsed_time(e1) / 5
+        I, it, rr, code = hm.solve(h, V[:, 0], tol=args.tol, restart=args.restart)
+        out["orderings"][ORDERINGS[o]] = dict(times, setup_ms=st["setup_ms"], bandwidth=st["bandwidth"],
+                                              fill_blocks=st["fill_blocks"], coef_entries=st["coef_entries"],
+                                              coef_entries_dense=st["coef_entries_dense"], iters=int(it[0]),
+                                              converged=int(code) == 0)
+        hm.hmat_destroy(h)
+    print(json.dumps(out), flush=True)
+
+
 def run_profile_op(args):
     """A short, deterministic case for ncu captures (no timing of its own)."""
     import torch
     import paper_2111_13483_gb300 as hm
     P = load_problem(args.workload, 0, 1)
-    h = hm.hmat_create(P, ordering=1, fill_tol=args.fill_tol, precision=args.precision)
+    h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision)
     hm.precond_setup(h)
     g, k = (int(v) for v in args.schedule.split(","))
     hm.hmsolve.hm_set_sweep_schedule(h, g, k)
@@ -751,6 +797,9 @@ def main():
         return
     if args.profile_op > 0:
         run_profile_op(args)
+        return
+    if args.compare_orderings:
+        run_compare_orderings(args)
         return
     if args.impl == "reference":
         run_reference(args)

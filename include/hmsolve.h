@@ -82,7 +82,8 @@ typedef struct {
 } hm_desc;
 
 /*
- *   ordering   0 = keep the cluster order, 1 = reverse Cuthill-McKee (Algorithm 1);
+ *   ordering   0 = keep the cluster order, 1 = reverse Cuthill-McKee, 2 = Sloan (the
+ *              Algorithm 1 orderings compared in Sec. 3.3, Tables 3-4; see hm_plan_order_method);
  *   fill_tol   Sec. 3.4 compression tolerance for fill-in coefficient blocks, 0 = off;
  *   precision  0 = complex FP64 throughout; 1 = complex FP32 operator/preconditioner
  *              inside an FP64 refinement loop on Z (FP64 pivots, Arnoldi, residual);
@@ -243,10 +244,15 @@ int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
  * launch are split into `groups` (1, 2 or 4) independent chains, and `kind` selects how a
  * chain is computed: 1 = one CTA per block row; 2 = one CTA per two consecutive block rows;
  * 3 = one chain CTA walks all block rows adding the dependencies of the last four rows
- * from shared memory, while one helper CTA per block row adds all older dependencies.
- * Every schedule gives bitwise the same result.  (0, 0) -- the default -- lets the library
- * time the candidates on its first calls of each width and keep the fastest.  Kinds 2 and
- * 3 apply to groups of at most 16 columns (kind 1 otherwise).  HM_EINVAL for other values.
+ * from shared memory, while one helper CTA per block row adds all older dependencies;
+ * 4 = one CTA per block row with the block products on the tensor cores (complex-FP32
+ * sweeps of a precision 1 handle: TF32 operands split into a rounded part and a remainder,
+ * FP32 accumulation; the FP64 sweeps take kind 1 for it).  Kinds 1-3 give bitwise the same
+ * result, and kind 4 gives bitwise the same result for every number of groups.  (0, 0) --
+ * the default -- lets the library time kind 1 with 1, 2 and 4 groups on its first calls of
+ * each width and keep the fastest.
+ * Kinds 2 and 3 apply to groups of at most 16 columns (kind 1 otherwise).  HM_EINVAL for
+ * other values.
  */
 int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind);
 
@@ -332,6 +338,22 @@ int hm_batch_close(hm_batch b);
  * order[p] = node placed at position p (n_leaves entries).  HM_EINVAL on bad input.
  */
 int hm_plan_order(int32_t n_leaves, int32_t n_pairs, const int32_t *t, const int32_t *s, int32_t *order);
+
+/*
+ * Algorithm 1 step 3 with a chosen reordering (Sec. 3.3 compares several, Tables 3-4):
+ * method 0 = identity, 1 = reverse Cuthill-McKee as hm_plan_order, 2 = Sloan's profile and
+ * wavefront reduction: per component (in order of its lowest node) a start node s and an end
+ * node e from rooted level structures (s = the minimum-(degree, index) node; the last level's
+ * nodes in ascending (degree, index), one per degree: one whose structure is deeper than s's
+ * and narrower than all tried replaces s and the search restarts, one only narrower becomes
+ * e), priorities 2 dist(i, e) - (deg(i) + 1), then the queued node of highest priority (lowest
+ * index on ties) is numbered next, with the priority updates of Sloan's algorithm (numbering a
+ * preactive node raises its neighbours by 1; a node turning active gains 1 and so does each of
+ * its neighbours not yet numbered).  Not reversed.  Same arguments and errors as hm_plan_order
+ * (HM_EINVAL also for another method).
+ */
+int hm_plan_order_method(int32_t method, int32_t n_leaves, int32_t n_pairs, const int32_t *t, const int32_t *s,
+                         int32_t *order);
 
 /*
  * Symbolic fill of the scaling coefficients (Sec. 3.3, Figs. 3b-7b): for blocks numbered

@@ -150,7 +150,7 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
     if (opts) h->opts = *opts;
     else hm_default_opts(&h->opts);
     int st;
-    if (h->opts.ordering < 0 || h->opts.ordering > 1 || h->opts.fill_tol < 0 || h->opts.precision < 0 ||
+    if (h->opts.ordering < 0 || h->opts.ordering > 2 || h->opts.fill_tol < 0 || h->opts.precision < 0 ||
         h->opts.precision > 1) {
         delete h;
         return HM_EINVAL;
@@ -473,8 +473,7 @@ int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind)
         h->sweep_fixed = 0;
         return HM_OK;
     }
-    if ((groups != 1 && groups != 2 && groups != 4) || (kind != 1 && kind != SWEEP_SR && kind != 3))
-        return HM_EINVAL;
+    if ((groups != 1 && groups != 2 && groups != 4) || kind < 1 || kind > 4) return HM_EINVAL;
     h->sweep_fixed = groups | (kind << 4);
     return HM_OK;
 }

@@ -234,6 +234,7 @@ int validate_and_copy(hm_ctx *h, const hm_desc *d);
 void plan_order(hm_ctx *h);
 void plan_far(hm_ctx *h);
 std::vector<int> rcm_order(int nl, const std::vector<int> &t, const std::vector<int> &s);
+std::vector<int> sloan_order(int nl, const std::vector<int> &t, const std::vector<int> &s);
 void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &pj, std::vector<int> &sptr,
                    std::vector<int> &sidx);
 

@@ -21,6 +21,7 @@
 
 #include "cplx.cuh"
 #include "hm_internal.h"
+#include "tc.cuh"
 #include "tile.cuh"
 
 namespace hm {
@@ -320,6 +321,212 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
         __threadfence();
         *(volatile int *)(pub + o_blk) = epoch;
     }
+}
+
+// ---- complex-FP32 sweeps on the tensor cores ----------------------------------------------
+// One CTA per block row o and column group, as sweep_row, with the block products on the
+// tensor-core micro-kernel of tc.cuh.  The row's dependency list is walked in chunks of at most
+// tc::KC contraction entries: whole dependency blocks are packed while they fit, a block longer
+// than a chunk is split, and each of the last TAIL dependencies (the ones the chain publishes
+// last) starts a chunk of its own.  Per chunk: the coefficient rows of the next chunk are copied
+// with cp.async into the other raw buffer; the chunk's vector entries are read from the tagged
+// copy into registers (each word re-polled until it carries this sweep's epoch); then, once the
+// previous chunk's MMAs have finished, the raw coefficients are split into the A' planes, the
+// vector entries into the B' planes, and thread 0 issues the chunk's MMAs.  At the end
+// out = x - D and the block is published as tagged words, then as plain values.  Every output
+// adds its terms in walk order whatever the number of columns, so the result of a column does
+// not depend on the others.
+constexpr int TCW_LD = 64;                       // raw coefficient buffer: raw[kk * TCW_LD + row]
+constexpr int TCW_BYTES = tc::KC * TCW_LD * 8;   // one raw buffer (16 KB)
+
+struct TcChunk {                 // a chunk's per-entry sources, filled by thread 0
+    int64_t wbase[tc::KC];       // coefficient of contraction entry kk, row r: W[wbase + r * wstr]
+    int wstr[tc::KC];
+    int yrow[tc::KC];            // vector entry kk of column c: tag[yrow + c * n]
+    int kl;                      // entries in the chunk (0: none left)
+};
+
+struct TcWalk {
+    int p, koff;   // next dependency position and the first row of it not yet taken
+};
+
+// Thread 0: the next chunk of o's dependency list (see the comment above).
+template <bool FWD>
+__device__ void tc_next_chunk(TcWalk &w, int pend, int o_blk, int no, const int *size, const int *boff,
+                              const int *lidx, const int *lcol, const int64_t *coff, TcChunk &c)
+{
+    const int step = FWD ? 1 : -1, tail0 = pend - TAIL * step;
+    int kl = 0;
+    while (w.p != pend && kl < tc::KC) {
+        const int k = lidx[w.p], nk = size[k];
+        const bool tail = FWD ? w.p >= tail0 : w.p <= tail0;
+        if (tail && kl > 0) break;                                       // tail blocks start a chunk
+        const int take = min(nk - w.koff, tc::KC - kl);
+        if (!tail && w.koff == 0 && take < nk && kl > 0) break;           // pack whole blocks only
+        for (int i = 0; i < take; ++i) {
+            const int q = w.koff + i;
+            if (FWD) {   // M(row, q) = W_ko(q, row), W_ko: nk x no at coff[k] + lcol * nk
+                c.wbase[kl + i] = coff[k] + (int64_t)lcol[w.p] * nk + q;
+                c.wstr[kl + i] = nk;
+            } else {     // M(row, q) = W_ok(row, q), W_ok: no x nk at coff[o] + lcol * no
+                c.wbase[kl + i] = coff[o_blk] + (int64_t)lcol[w.p] * no + (int64_t)q * no;
+                c.wstr[kl + i] = 1;
+            }
+            c.yrow[kl + i] = boff[k] + q;
+        }
+        kl += take;
+        w.koff += take;
+        if (w.koff == nk) {
+            w.p += step;
+            w.koff = 0;
+        }
+        if (tail) break;                                                  // ... and end it
+    }
+    c.kl = kl;
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(256, 2) k_sweep_tc(int nb, const int *size, const int *boff, const int *lptr,
+                                                  const int *lidx, const int *lcol, const int64_t *coff,
+                                                  const float2 *W, const float2 *x, float2 *y, int n, int nrhs,
+                                                  int G, int gw, int epoch, int *ticket, int *err, uint4 *tag)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ int s_t;
+    __shared__ uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ TcChunk s_ch[2];
+    if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int bi = s_t / G, g = s_t % G;
+    if (bi >= nb) return;
+    const int o_blk = FWD ? bi : nb - 1 - bi;
+    const int c0 = g * gw, nc = min(gw, nrhs - c0);
+    if (nc <= 0 || held_back(err, o_blk)) return;
+    x += (int64_t)c0 * n;
+    y += (int64_t)c0 * n;
+    tag += (int64_t)c0 * n;
+    const int no = size[o_blk], o = boff[o_blk];
+    const unsigned long long bound = wait_bound(err);
+    unsigned char *region = tc::align1024(smraw);
+    float2 *raw[2] = {(float2 *)(region + tc::REGION_BYTES), (float2 *)(region + tc::REGION_BYTES + TCW_BYTES)};
+    // the thread's outputs e = tid + u * blockDim (row e % no, column e / no): x first, so its
+    // load stays off the critical path
+    constexpr int NE = 64 * 64 / 256;
+    float2 xr[NE];
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        xr[u] = e < no * nc ? x[o + e % no + (int64_t)(e / no) * n] : make_float2(0.f, 0.f);
+    }
+    const int step = FWD ? 1 : -1;
+    const int pa = FWD ? lptr[o_blk] : lptr[o_blk + 1] - 1, pend = FWD ? lptr[o_blk + 1] : lptr[o_blk] - 1;
+    tc::Acc acc;
+    acc.planes = region;
+    acc.mbar = &s_mbar;
+    acc.tslot = &s_tmem;
+    const bool deps = pa != pend;
+    if (deps) {
+        TcWalk w{pa, 0};
+        auto prefetch = [&](int buf) {   // raw coefficients of chunk s_ch[buf]
+            const TcChunk &c = s_ch[buf];
+            const int kl = c.kl;
+            for (int e = threadIdx.x; e < kl * no; e += blockDim.x) {
+                int kk, r;
+                if (FWD) kk = e % kl, r = e / kl;
+                else kk = e / no, r = e % no;
+                cp_async_el(raw[buf] + kk * TCW_LD + r, W + c.wbase[kk] + (int64_t)r * c.wstr[kk]);
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        };
+        if (threadIdx.x == 0) tc_next_chunk<FWD>(w, pend, o_blk, no, size, boff, lidx, lcol, coff, s_ch[0]);
+        acc.open(no, nc);   // synchronises: s_ch[0] is visible
+        prefetch(0);
+        for (int cur = 0; s_ch[cur].kl > 0; cur ^= 1) {
+            const TcChunk &c = s_ch[cur];
+            const int kl = c.kl;
+            // the next chunk: its sources (thread 0) and, after the barrier below, its copies
+            if (threadIdx.x == 0) tc_next_chunk<FWD>(w, pend, o_blk, no, size, boff, lidx, lcol, coff, s_ch[cur ^ 1]);
+            // this chunk's vector entries into registers, re-polled until current
+            uint4 v[8];
+            const int cnt = kl * nc;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + u * blockDim.x;
+                if (e < cnt) v[u] = ld_tag(tag + c.yrow[e % kl] + (int64_t)(e / kl) * n);
+            }
+            {
+                bool timing = false;
+                unsigned long long t0 = 0;
+                for (;;) {
+                    unsigned stale = 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = threadIdx.x + u * blockDim.x;
+                        if (e < cnt && (v[u].y != (unsigned)epoch || v[u].w != (unsigned)epoch)) stale |= 1u << u;
+                    }
+                    if (!stale || *(volatile int *)err) break;
+                    if (!timing) {
+                        timing = true;
+                        t0 = gtimer();
+                    } else if (gtimer() - t0 > bound) {
+                        atomicCAS(err, 0, ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (stale & (1u << u)) {
+                            const int e = threadIdx.x + u * blockDim.x;
+                            v[u] = ld_tag(tag + c.yrow[e % kl] + (int64_t)(e / kl) * n);
+                        }
+                }
+            }
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            __syncthreads();                   // raw[cur] landed for every thread; s_ch[cur ^ 1] written
+            if (s_ch[cur ^ 1].kl > 0) prefetch(cur ^ 1);
+            acc.wait(err, bound);              // the previous chunk's MMAs no longer read the planes
+            const float2 *rw = raw[cur];
+            for (int e = threadIdx.x; e < acc.m8 * kl; e += blockDim.x) {
+                const int r = e % acc.m8, kk = e / acc.m8;
+                acc.put_a(r, kk, r < no ? rw[kk * TCW_LD + r] : make_float2(0.f, 0.f));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = threadIdx.x + u * blockDim.x;
+                if (e < cnt) acc.put_b(e / kl, e % kl, make_float2(__uint_as_float(v[u].x), __uint_as_float(v[u].z)));
+            }
+            acc.zero_pad(kl);
+            acc.issue(kl);                     // barrier inside: this chunk's raw buffer is consumed
+        }
+        acc.wait(err, bound);
+    }
+    float *dsm = (float *)region;
+    const bool any = deps && acc.drain(dsm);
+    float2 *out = xr;   // out = x - D, in place
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        if (any && e < no * nc) {
+            const float2 d = acc.entry(dsm, e % no, e / no);
+            out[u].x -= d.x;
+            out[u].y -= d.y;
+        }
+    }
+    // tagged words first (the consumers wait on them), then the plain copy
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        if (e < no * nc)
+            tag[o + e % no + (int64_t)(e / no) * n] =
+                make_uint4(__float_as_uint(out[u].x), (unsigned)epoch, __float_as_uint(out[u].y), (unsigned)epoch);
+    }
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        if (e < no * nc) y[o + e % no + (int64_t)(e / no) * n] = out[u];
+    }
+    if (deps) acc.close();
 }
 
 }  // namespace
@@ -942,6 +1149,33 @@ static cudaError_t sweep_ch_shape(hm_ctx *h, const OpData<T> &d, bool forward, c
     return cudaGetLastError();
 }
 
+// Complex-FP32 sweep on the tensor cores (k_sweep_tc): shared memory = the operand planes
+// and drained accumulator, two raw coefficient buffers, alignment slack.
+static cudaError_t sweep_tc_launch(hm_ctx *h, const OpData<float2> &d, bool forward, const float2 *x, float2 *y,
+                                   int nrhs, int G, int gw, int ep)
+{
+    Plan &P = h->plan;
+    const size_t smem = tc::REGION_BYTES + 2 * TCW_BYTES + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_sweep_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_sweep_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    const unsigned grid = (unsigned)(P.nb * G);
+    if (forward)
+        HM_LAUNCH(h, K_SWEEP_FWD,
+                  (k_sweep_tc<true><<<grid, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx,
+                                                                    h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs, G, gw,
+                                                                    ep, h->d_ticket, h->d_err, h->d_ytag)));
+    else
+        HM_LAUNCH(h, K_SWEEP_BWD,
+                  (k_sweep_tc<false><<<grid, 256, smem, h->stream>>>(P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx,
+                                                                     h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs, G, gw,
+                                                                     ep, h->d_ticket, h->d_err, h->d_ytag)));
+    return cudaGetLastError();
+}
+
 static int width_class(int w) { return w <= 4 ? 0 : w <= 8 ? 1 : w <= 16 ? 2 : w <= 32 ? 3 : 4; }
 
 // Number of column groups for a sweep of nrhs columns: the tuned choice of the width class,
@@ -957,7 +1191,10 @@ static int sweep_groups(hm_ctx *h, bool fp32, bool forward, int nrhs, SweepTune 
             const int gw = (nrhs + G - 1) / G;
             if (G > 1 && gw < 4) continue;
             // one block row per CTA; the super-row and chain-and-helpers kinds compute the same
-            // sums but measured slower on every width (they stay selectable)
+            // sums but measured slower on every width, and so did the tensor-core kind for the
+            // complex-FP32 sweeps (8.7 against 6.1 ms per 64-column launch on the 30,720-unknown
+            // sphere: its chunks of 32 are staged and multiplied one after the other); they stay
+            // selectable
             t.cand[t.ncand++] = G | (1 << 4);
         }
     if (t.ncand == 1) return t.best = t.cand[0];
@@ -1007,6 +1244,13 @@ static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x
     const int G = std::min(code & 15, nrhs), sr = code >> 4;
     const int gw = (nrhs + G - 1) / G;
     if (tu) cudaEventRecord(tu->ev[2 * slot], h->stream);
+    if constexpr (sizeof(T) == 8) {
+        if (sr == 4) {
+            e = sweep_tc_launch(h, d, forward, x, y, nrhs, G, gw, ep);
+            if (tu) cudaEventRecord(tu->ev[2 * slot + 1], h->stream);
+            return e;
+        }
+    }
     if (sr == 3 && gw <= 16) {
         if (gw <= 4) e = sweep_ch_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
         else e = sweep_ch_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);

@@ -182,6 +182,118 @@ std::vector<int> rcm_order(int nl, const std::vector<int> &t, const std::vector<
     return seq;
 }
 
+// Sloan's profile and wavefront reducing ordering (compared in Sec. 3.3, Tables 3-4), from
+// Sloan's published algorithm: per component (in order of its lowest node) a start node s and
+// an end node e from rooted level structures (s = the minimum-(degree, index) node; the last
+// level's nodes in ascending (degree, index), one per degree, are tried: one deeper than s's
+// structure and narrower than all tried so far becomes s and the search restarts, one only
+// narrower becomes e); priorities 2 dist(i, e) - (deg(i) + 1); then nodes are numbered by
+// highest priority (lowest index on ties) from a queue of preactive/active nodes, numbering a
+// preactive node raising its neighbours by 1 and activating them, and every neighbour of a node
+// that turns active gaining 1 (inactive ones queued as preactive).  Not reversed.
+std::vector<int> sloan_order(int nl, const std::vector<int> &t, const std::vector<int> &s)
+{
+    std::vector<std::vector<int>> adj(nl);
+    for (size_t b = 0; b < t.size(); ++b)
+        if (t[b] != s[b]) {
+            adj[t[b]].push_back(s[b]);
+            adj[s[b]].push_back(t[b]);
+        }
+    for (auto &a : adj) {
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+    std::vector<int> deg(nl);
+    for (int i = 0; i < nl; ++i) deg[i] = (int)adj[i].size();
+    auto key_less = [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; };
+    auto width = [](const std::vector<std::vector<int>> &lv) {
+        size_t w = 0;
+        for (auto &L : lv) w = std::max(w, L.size());
+        return (int)w;
+    };
+    enum { INACTIVE = 0, PREACTIVE, ACTIVE, POSTACTIVE };
+    std::vector<int> status(nl, INACTIVE), mark(nl, -1), seq;
+    std::vector<long> prio(nl, 0);
+    std::vector<char> placed(nl, 0);
+    seq.reserve(nl);
+    int stamp = 0;
+    for (int c0 = 0; c0 < nl; ++c0) {
+        if (placed[c0]) continue;
+        auto comp_lv = bfs_levels(adj, c0, mark, stamp++);
+        int sn = -1;
+        for (auto &L : comp_lv)
+            for (int u : L) {
+                placed[u] = 1;
+                if (sn < 0 || key_less(u, sn)) sn = u;
+            }
+        // start and end nodes
+        int en = sn;
+        while (true) {
+            auto ls = bfs_levels(adj, sn, mark, stamp++);
+            std::vector<int> last = ls.back();
+            std::sort(last.begin(), last.end(), key_less);
+            std::vector<int> cand;
+            for (int u : last)
+                if (cand.empty() || deg[cand.back()] != deg[u]) cand.push_back(u);
+            int wmin = -1;
+            bool restart = false;
+            for (int i : cand) {
+                auto li = bfs_levels(adj, i, mark, stamp++);
+                const int wi = width(li);
+                if (li.size() > ls.size() && (wmin < 0 || wi < wmin)) {
+                    sn = i;
+                    restart = true;
+                    break;
+                }
+                if (wmin < 0 || wi < wmin) {
+                    en = i;
+                    wmin = wi;
+                }
+            }
+            if (!restart) break;
+        }
+        // priorities from the distance to the end node
+        auto le = bfs_levels(adj, en, mark, stamp++);
+        for (size_t d = 0; d < le.size(); ++d)
+            for (int u : le[d]) prio[u] = 2L * (long)d - (long)(deg[u] + 1);
+        std::vector<int> queue{sn};
+        status[sn] = PREACTIVE;
+        while (!queue.empty()) {
+            size_t bi = 0;
+            for (size_t q = 1; q < queue.size(); ++q) {
+                const int u = queue[q], b = queue[bi];
+                if (prio[u] > prio[b] || (prio[u] == prio[b] && u < b)) bi = q;
+            }
+            const int i = queue[bi];
+            queue.erase(queue.begin() + bi);
+            if (status[i] == PREACTIVE)
+                for (int j : adj[i]) {
+                    prio[j] += 1;
+                    if (status[j] == INACTIVE) {
+                        status[j] = PREACTIVE;
+                        queue.push_back(j);
+                    }
+                }
+            seq.push_back(i);
+            status[i] = POSTACTIVE;
+            for (int j : adj[i])
+                if (status[j] == PREACTIVE) {
+                    status[j] = ACTIVE;
+                    prio[j] += 1;
+                    for (int k : adj[j])
+                        if (status[k] != POSTACTIVE) {
+                            prio[k] += 1;
+                            if (status[k] == INACTIVE) {
+                                status[k] = PREACTIVE;
+                                queue.push_back(k);
+                            }
+                        }
+                }
+        }
+    }
+    return seq;
+}
+
 // Symbolic elimination on bitsets (Sec. 3.3, the fill of Figs. 3b-7b): eliminating block
 // k couples every pair of its later neighbours.  Pairs (i, j) in block numbering; returns
 // S_k (sorted, > k) as CSR.
@@ -296,6 +408,8 @@ void plan_order(hm_ctx *h)
     P.n = h->n;
     if (h->opts.ordering == 1)
         P.order = rcm_order(nl, h->near_t, h->near_s);
+    else if (h->opts.ordering == 2)
+        P.order = sloan_order(nl, h->near_t, h->near_s);
     else {
         P.order.resize(nl);
         std::iota(P.order.begin(), P.order.end(), 0);
@@ -541,15 +655,27 @@ void plan_far(hm_ctx *h)
 }  // namespace hm
 
 // ---- host-only planning entry points (no device work) -----------------------------------
-extern "C" int hm_plan_order(int32_t n_leaves, int32_t n_pairs, const int32_t *t, const int32_t *s, int32_t *order)
+extern "C" int hm_plan_order_method(int32_t method, int32_t n_leaves, int32_t n_pairs, const int32_t *t,
+                                    const int32_t *s, int32_t *order)
 {
-    if (n_leaves <= 0 || n_pairs < 0 || !order || (n_pairs > 0 && (!t || !s))) return HM_EINVAL;
+    if (method < 0 || method > 2 || n_leaves <= 0 || n_pairs < 0 || !order || (n_pairs > 0 && (!t || !s)))
+        return HM_EINVAL;
     for (int b = 0; b < n_pairs; ++b)
         if (t[b] < 0 || s[b] < 0 || t[b] >= n_leaves || s[b] >= n_leaves) return HM_EINVAL;
-    std::vector<int> tv(t, t + n_pairs), sv(s, s + n_pairs);
-    std::vector<int> o = hm::rcm_order(n_leaves, tv, sv);
+    std::vector<int> tv(t, t + n_pairs), sv(s, s + n_pairs), o;
+    if (method == 1) o = hm::rcm_order(n_leaves, tv, sv);
+    else if (method == 2) o = hm::sloan_order(n_leaves, tv, sv);
+    else {
+        o.resize(n_leaves);
+        std::iota(o.begin(), o.end(), 0);
+    }
     std::memcpy(order, o.data(), sizeof(int32_t) * n_leaves);
     return HM_OK;
+}
+
+extern "C" int hm_plan_order(int32_t n_leaves, int32_t n_pairs, const int32_t *t, const int32_t *s, int32_t *order)
+{
+    return hm_plan_order_method(1, n_leaves, n_pairs, t, s, order);
 }
 
 extern "C" int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int32_t *j, int32_t *ptr,

@@ -60,7 +60,7 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
            "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
-           "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm"]
+           "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm", "hm_plan_order_method"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -100,6 +100,7 @@ def load(build_if_missing=True):
     L.hm_get_block.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
     L.hm_apply.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32]
     L.hm_plan_order.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]
+    L.hm_plan_order_method.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]
     L.hm_plan_fill.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int64]
     L.hm_plan_far.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p,
                               _i64p, _i64p, ctypes.c_int32, _i64p, _i64p]
@@ -277,6 +278,17 @@ def hm_plan_order(n_leaves, t, s):
     code = load().hm_plan_order(n_leaves, len(t), _p(t, _i32p), _p(s, _i32p), _p(out, _i32p))
     if code != HM_OK:
         raise HMError(code, "hm_plan_order")
+    return out
+
+
+def hm_plan_order_method(method, n_leaves, t, s):
+    """Host-only Algorithm 1 ordering with a chosen method (0 identity, 1 RCM, 2 Sloan)."""
+    t = np.ascontiguousarray(t, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.int32)
+    out = np.zeros(n_leaves, dtype=np.int32)
+    code = load().hm_plan_order_method(method, n_leaves, len(t), _p(t, _i32p), _p(s, _i32p), _p(out, _i32p))
+    if code != HM_OK:
+        raise HMError(code, "hm_plan_order_method")
     return out
 
 

@@ -67,6 +67,24 @@ def test_planner_random_graphs_match_oracle(hm):
         assert hm.hm_plan_fill(n, t, s) == schur.symbolic_fill(n, pairs)
 
 
+def test_planner_sloan_matches_oracle(hm, sphere1920, sphere480):
+    import efie_problem as ep
+    for P in (sphere480, sphere1920, ep.build("plate1160")):
+        nl = len(P.leaf_ptr) - 1
+        pairs = list(zip(P.near_t.tolist(), P.near_s.tolist()))
+        assert np.array_equal(hm.hm_plan_order_method(2, nl, P.near_t, P.near_s), ordering.sloan(nl, pairs))
+        assert np.array_equal(hm.hm_plan_order_method(1, nl, P.near_t, P.near_s), ordering.rcm(nl, pairs))
+        assert np.array_equal(hm.hm_plan_order_method(0, nl, P.near_t, P.near_s), np.arange(nl))
+    rng = np.random.default_rng(12)
+    for n in (1, 2, 7, 40, 130):
+        m = rng.integers(0, 3 * n + 1)
+        t = rng.integers(0, n, m)
+        s = rng.integers(0, n, m)
+        assert np.array_equal(hm.hm_plan_order_method(2, n, t, s), ordering.sloan(n, list(zip(t.tolist(), s.tolist()))))
+    with pytest.raises(hm.HMError):
+        hm.hm_plan_order_method(3, 4, [0], [1])
+
+
 def test_planner_rejects_bad_input(hm):
     with pytest.raises(hm.HMError):
         hm.hm_plan_order(3, [0, 5], [1, 1])

@@ -175,16 +175,17 @@ def test_mixed_factors_close_to_fp64(cfg1, cfg1_mixed):
 
 
 def test_mixed_solution_error_against_tight_oracle(cfg1, cfg1_mixed, cfg1_tight):
-    """The FP64 refinement loop stops on the true residual ||V - Z I||/||V||; at 3e-5 the
-    solution is within 1e-4 of the oracle's tight solve, and the residual is verified with
-    the oracle's own H-matrix product."""
+    """The FP64 refinement loop stops on the true residual ||V - Z I||/||V||; at 1e-5 (the
+    setting the benchmark uses for its 1e-4 error bar) the solution is within 1e-4 of the
+    oracle's tight solve, and the residual is verified with the oracle's own H-matrix
+    product."""
     P, order, F, S, h = cfg1
     B, X = cfg1_tight
-    I, its, rr, code = hm.solve(cfg1_mixed, B, tol=3e-5, restart=30)
+    I, its, rr, code = hm.solve(cfg1_mixed, B, tol=1e-5, restart=30)
     assert code == 0
     for c in range(B.shape[1]):
-        assert rr[c] <= 3e-5
-        assert np.linalg.norm(B[:, c] - S.Z_orig(I[:, c])) / np.linalg.norm(B[:, c]) <= 3.1e-5
+        assert rr[c] <= 1e-5
+        assert np.linalg.norm(B[:, c] - S.Z_orig(I[:, c])) / np.linalg.norm(B[:, c]) <= 1.01e-5
         assert rel(I[:, c], X[:, c]) <= 1e-4
 
 
@@ -240,8 +241,10 @@ def test_compressed_solve_matches_oracle(cfg1_compressed):
     assert rel(x, xo) <= 1e-8
 
 
-# ---- sweep schedules: every (groups, kind) gives bitwise the same sweeps -------------------------
-# kind 1: one block row per CTA, 2: two-row super-rows, 3: chain CTA + helpers
+# ---- sweep schedules: (groups, kind) choices that give bitwise the same sweeps ------------------
+# kind 1: one block row per CTA, 2: two-row super-rows, 3: chain CTA + helpers (CUDA cores,
+# the same summation order); kind 4: complex FP32 on the tensor cores (its own fixed order,
+# bitwise the same for every column grouping; FP64 sweeps take kind 1 for it)
 @pytest.mark.parametrize("prec", [0, 1])
 def test_sweep_schedules_bitwise_equal(cfg1, cfg1_mixed, prec):
     P, order, F, S, h64 = cfg1
@@ -249,25 +252,38 @@ def test_sweep_schedules_bitwise_equal(cfg1, cfg1_mixed, prec):
     ops = (hm.hmsolve.OP_LINV, hm.hmsolve.OP_LTINV, hm.hmsolve.OP_A)
     if prec == 1:
         ops = tuple(hm.hmsolve.OP32 + o for o in ops)
+    families = [[(g, k) for g in (1, 2, 4) for k in (1, 2, 3)]]
+    tc = [(g, 4) for g in (1, 2, 4)]
+    if prec == 0:
+        families[0] += tc
+    else:
+        families.append(tc)
     rng = np.random.default_rng(11)
-    for nrhs in (1, 5, 16):
+    for nrhs in (1, 5, 16, 64):
         X = rng.standard_normal((S.n, nrhs)) + 1j * rng.standard_normal((S.n, nrhs))
         dx = _dev(X)
-        ref = {}
-        for sched in ((1, 1), (1, 2), (1, 3), (2, 1), (2, 2), (2, 3), (4, 1), (4, 2), (4, 3)):
-            hm.hmsolve.hm_set_sweep_schedule(h, *sched)
+        refs = []
+        for fam in families:
+            ref = {}
+            for sched in fam:
+                hm.hmsolve.hm_set_sweep_schedule(h, *sched)
+                for op in ops:
+                    dy = torch.empty_like(dx)
+                    hm.hm_apply(h, op, dx, dy)
+                    torch.cuda.synchronize()
+                    Y = _host(dy)
+                    if op not in ref:
+                        ref[op] = Y
+                        if prec == 0 and op == hm.hmsolve.OP_LINV:
+                            for c in range(nrhs):
+                                assert rel(Y[:, c], S.L_inv(X[:, c])) < 1e-10
+                    else:
+                        assert np.array_equal(Y, ref[op]), (sched, op, nrhs)
+            refs.append(ref)
+        if len(refs) == 2:   # tensor cores (3xTF32) against CUDA cores (FP32): FP32-level agreement
             for op in ops:
-                dy = torch.empty_like(dx)
-                hm.hm_apply(h, op, dx, dy)
-                torch.cuda.synchronize()
-                Y = _host(dy)
-                if op not in ref:
-                    ref[op] = Y
-                    if prec == 0 and op == hm.hmsolve.OP_LINV:
-                        for c in range(nrhs):
-                            assert rel(Y[:, c], S.L_inv(X[:, c])) < 1e-10
-                else:
-                    assert np.array_equal(Y, ref[op]), (sched, op, nrhs)
+                for c in range(nrhs):
+                    assert rel(refs[1][op][:, c], refs[0][op][:, c]) < 1e-5, (op, c)
         hm.hmsolve.hm_set_sweep_schedule(h, 0, 0)
 
 
@@ -298,9 +314,41 @@ def test_plate_solve_matches_oracle(plate_cfg, prec):
             assert ok and abs(int(its[c]) - ito) <= 1
             assert rel(X[:, c], xo) <= 1e-8
     else:
-        X, its, rr, code = hm.solve(h, B, tol=3e-5, restart=50)
+        X, its, rr, code = hm.solve(h, B, tol=1e-5, restart=50)
         assert code == 0
         for c in range(B.shape[1]):
             xt = krylov.solve(S, B[:, c], tol=1e-10, restart=50)[0]
-            assert np.linalg.norm(B[:, c] - S.Z_orig(X[:, c])) / np.linalg.norm(B[:, c]) <= 3.1e-5
+            assert np.linalg.norm(B[:, c] - S.Z_orig(X[:, c])) / np.linalg.norm(B[:, c]) <= 1.01e-5
             assert rel(X[:, c], xt) <= 1e-4
+
+
+# ---- Sloan's ordering (Sec. 3.3, Tables 3-4) through the whole path --------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sloan_ordering_solve_matches_oracle(prec):
+    import efie_problem as ep
+    P = ep.build("plate1160")
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.sloan(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    F = schur.setup(P, order, fill_tol=0.0)
+    S = krylov.System(P, F)
+    h = hm.hmat_create(P, ordering=2, fill_tol=0.0, precision=prec)
+    hm.precond_setup(h)
+    assert np.array_equal(hm.hm_get_order(h), order)
+    ptr, idx = hm.hm_get_fill(h)
+    for k in range(F.nb):
+        assert list(idx[ptr[k]:ptr[k + 1]]) == F.S[k]
+    b = P.plane_wave([0.6, 0.0, -0.8], [0.8, 0.0, 0.6])
+    if prec == 0:
+        for k in range(0, F.nb, 3):
+            nk = int(F.size[k])
+            assert rel(hm.hm_get_block(h, 0, k, (nk, nk)), F.D[k]) < 1e-10, k
+        x, it, rr, code = hm.solve(h, b, tol=1e-6, restart=50)
+        xo, ito, rro, ok = krylov.solve(S, b, tol=1e-6, restart=50)
+        assert code == 0 and ok and abs(int(it[0]) - ito) <= 1
+        assert rel(x, xo) <= 1e-8
+    else:
+        x, it, rr, code = hm.solve(h, b, tol=1e-5, restart=50)
+        xt = krylov.solve(S, b, tol=1e-10, restart=50)[0]
+        assert code == 0
+        assert np.linalg.norm(b - S.Z_orig(x)) / np.linalg.norm(b) <= 1.01e-5
+        assert rel(x, xt) <= 1e-4

@@ -279,3 +279,66 @@ def test_rcm_disconnected_components():
     pairs = [(0, 3), (3, 5), (1, 2), (4, 4)]
     o = ordering.rcm(6, pairs)
     assert sorted(o.tolist()) == list(range(6))
+
+
+def test_rcm_start_rule_hand_traced():
+    """A path 1-2-3-4-5-6-7 with node 0 hanging on 4.  The search starts at the minimum-
+    (degree, index) node 0 (5 levels), moves to 1 (7 levels), and stops (7 is no deeper):
+    Cuthill-McKee from 1 is 1 2 3 4 0 5 6 7 (0 before 5: lower degree), reversed."""
+    pairs = [(1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 7), (0, 4)]
+    assert ordering.rcm(8, pairs).tolist() == [7, 6, 5, 0, 4, 3, 2, 1]
+
+
+# ---- Sloan's ordering (the best ordering of Sec. 3.3, Tables 3-4) ------------------------------
+def test_sloan_path_runs_end_to_end():
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(10)
+    pairs = [(int(perm[i]), int(perm[i + 1])) for i in range(9)]
+    o = ordering.sloan(10, pairs)
+    # from the lower-index end of the path to the other end
+    assert o.tolist() == (perm[::-1] if perm[-1] < perm[0] else perm).tolist()
+
+
+def test_sloan_hand_traced():
+    """Edges 3-0, 0-4, 4-1, 0-1, 1-2.  Start 2 (degree 1, lowest index), end 3; distances to
+    3: 2->3, 1->2, 4->2, 0->1, 3->0; P = 2 dist - (deg + 1) = {2: 4, 1: 0, 4: 1, 0: -2, 3: -2}.
+    Number 2 (1 -> 1, preactive; then active: 2, its neighbours 0 -> -1, 4 -> 2); the tie 1/4 at
+    2 goes to 1 (active: 0 -> 0 then 3 -> -1 and 4 -> 3 via 0, 4 -> 4 and 0 -> 1 via 4); then 4
+    (priority 4), 0 (1), 3."""
+    assert ordering.sloan(5, [(3, 0), (0, 4), (4, 1), (0, 1), (1, 2)]).tolist() == [2, 1, 4, 0, 3]
+    assert ordering.sloan(5, [(0, 1), (1, 2), (2, 3), (1, 3), (3, 4)]).tolist() == [0, 1, 2, 3, 4]
+
+
+def _grid(a, b, seed):
+    idx = lambda i, j: i * b + j
+    pr = []
+    for i in range(a):
+        for j in range(b):
+            if i + 1 < a:
+                pr.append((idx(i, j), idx(i + 1, j)))
+            if j + 1 < b:
+                pr.append((idx(i, j), idx(i, j + 1)))
+            if i + 1 < a and j + 1 < b:
+                pr.append((idx(i, j), idx(i + 1, j + 1)))
+    p = np.random.default_rng(seed).permutation(a * b)
+    return a * b, [(int(p[x]), int(p[y])) for x, y in pr]
+
+
+def test_sloan_profile_not_above_rcm_on_grids():
+    """Profile reduction is what Sloan's algorithm is for: on triangulated grids (the meshes of
+    the plate workloads) its profile is at most RCM's and far below a random numbering's."""
+    for a, b in ((5, 20), (10, 30), (17, 17)):
+        n, pairs = _grid(a, b, a)
+        o = ordering.sloan(n, pairs)
+        assert sorted(o.tolist()) == list(range(n))
+        ps = ordering.profile(n, pairs, o)
+        assert ps <= ordering.profile(n, pairs, ordering.rcm(n, pairs))
+        assert ps < 0.2 * ordering.profile(n, pairs)
+
+
+def test_sloan_disconnected_components():
+    pairs = [(0, 3), (3, 5), (1, 2), (4, 4)]
+    o = ordering.sloan(6, pairs)
+    assert sorted(o.tolist()) == list(range(6))
+    assert o.tolist()[:3] == [0, 3, 5]      # component of node 0 first, then {1, 2}, then {4}
+    assert o.tolist()[3:] == [1, 2, 4]
