@@ -264,8 +264,12 @@ def roofline(prof, fs, stats, n, precision):
         return cls, entry(fs["update_flops"] * launches / fs["update_launches"],
                           E * fs["nnzL"] * 3.0 * launches / fs["update_launches"], {})
     if cls in ("sweep_fwd", "sweep_bwd"):
-        # per launch: the coefficient panels once, the input and output vectors of its columns
-        return cls, entry(8.0 * fs["nnzL"] * cols, E * (fs["nnzL"] * launches + 2.0 * n * cols), {})
+        # per launch: the stored coefficients once (dense blocks, and the factors of the
+        # compressed fill-in blocks: each stored entry is one complex MAC per column), the input
+        # and output vectors of its columns
+        ce = stats["coef_entries"]
+        return cls, entry(8.0 * ce * cols, E * (ce * launches + 2.0 * n * cols),
+                          {"coef_entries": ce, "coef_entries_dense": fs["nnzL"]})
     if cls in ("far1", "far2"):
         # far2 counts two launches per product (partial products + their sum)
         per = launches if cls == "far1" else launches / 2
@@ -555,6 +559,7 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         step()
+    stats = hm.hmat_stats(h)          # after a setup: the coefficient entries as stored
     fs = fill_structure(hm.hmsolve, h, P)
     hm.hm_profile(h, 2)
     hm.hm_profile(h, 1)

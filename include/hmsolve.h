@@ -282,6 +282,15 @@ int hm_test_hold(hm_handle h, int32_t block, int64_t wait_ns);
 int hm_tc_cgemm(int32_t m, int32_t k, int32_t ncols, const void *dA, int64_t lda, const void *dB, int64_t ldb,
                 void *dC, int64_t ldc, void *stream);
 
+/*
+ * How the complex-FP32 far-field product (Z_F u of Sec. 2, Eq. 11, inside the operator of a
+ * precision 1 handle) computes its block products: kind 1 = register-tiled FMAs on the CUDA
+ * cores, kind 2 = the tensor-core micro-kernel of hm_tc_cgemm; 0 = the default (2).  Both
+ * sum every output's terms in a fixed order, each its own; the FP64 far field always runs on
+ * the CUDA cores.  HM_EINVAL for other values.
+ */
+int hm_set_far_schedule(hm_handle h, int32_t kind);
+
 /* ---- continuous batching (serving) ---------------------------------------------------- */
 
 /*

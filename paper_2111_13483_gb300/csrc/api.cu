@@ -1,8 +1,10 @@
 // C-ABI entry points of hmsolve (declared in include/hmsolve.h).  Argument checks, device
 // uploads, error mapping; the arithmetic is in setup.cu and solve.cu.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "hm_internal.h"
 
@@ -217,7 +219,10 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
         (e = upload(h, &h->d_xoff[1], P.xoff[1])) || (e = upload(h, &h->d_xint[1], P.xint[1])) ||
         (e = upload(h, &h->d_rec[0], P.rec[0])) || (e = upload(h, &h->d_reccol[0], P.reccol[0])) ||
         (e = upload(h, &h->d_rec[1], P.rec[1])) || (e = upload(h, &h->d_reccol[1], P.reccol[1])) ||
-        (e = upload(h, &h->d_fill_k, P.fill_k))) {
+        (e = upload(h, &h->d_fill_k, P.fill_k)) || (e = upload(h, &h->d_rent, P.rent)) ||
+        (e = upload(h, &h->d_pboff, P.pboff)) || (e = upload(h, &h->d_cboff, P.pboff)) ||
+        (e = h->arena.alloc((void **)&h->d_crank, sizeof(int) * std::max<size_t>(P.sidx.size(), 1))) ||
+        (e = cudaMemsetAsync(h->d_crank, 0xff, sizeof(int) * std::max<size_t>(P.sidx.size(), 1), h->stream))) {
         int s = cuda_fail(h, e, "hmat_create upload");
         std::fprintf(stderr, "hmat_create: %s\n", h->err.c_str());
         h->arena.release_all();
@@ -268,6 +273,7 @@ int precond_setup(hm_handle h)
     int bad = -1;
     e = setup_run(h, &bad);
     if (!e && bad < 0) e = compress_run(h);
+    if (!e && bad < 0) e = pack_run(h);
     cudaEventRecord(e1, h->stream);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -357,14 +363,7 @@ int hmat_stats(hm_handle h, hm_stats *s)
     s->near_entries = ne;
     s->far_entries = h->fplan.entries;
     s->fill_blocks = P.sptr.empty() ? 0 : P.sptr[P.nb];
-    int64_t ce = P.coef_entries;
-    for (size_t f = 0; f < h->fill_ranks.size() && f < P.fill_e.size(); ++f) {
-        const int r = h->fill_ranks[f];
-        if (r < 0) continue;
-        const int64_t nk = P.size[P.fill_k[f]], nj = P.size[P.sidx[P.fill_e[f]]];
-        ce += (int64_t)r * (nk + nj) - nk * nj;
-    }
-    s->coef_entries = ce;
+    s->coef_entries = h->lowrank ? h->wc_len : P.coef_entries;   // what the sweeps read
     s->coef_entries_dense = P.coef_entries;
     s->diag_entries = P.diag_entries;
     s->bandwidth = P.bandwidth;
@@ -446,6 +445,41 @@ int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out)
     } else if (what == 1) {
         src = h->d_Dinv + P.doff[k];
         cnt = nk * nk;
+    } else if (h->lowrank) {   // the row's blocks from the compact store, factors expanded
+        const int64_t a = h->cboff[P.sptr[k]], b = h->cboff[P.sptr[k + 1]];
+        std::vector<hm_c128> st(b - a);
+        cudaError_t e;
+        if (mixed) {
+            std::vector<float2> tmp(b - a);
+            if ((e = cudaMemcpyAsync(tmp.data(), h->d_Wc32 + a, sizeof(float2) * (b - a), cudaMemcpyDeviceToHost,
+                                     h->stream)) ||
+                (e = cudaStreamSynchronize(h->stream)))
+                return cuda_fail(h, e, "hm_get_block");
+            for (size_t i = 0; i < tmp.size(); ++i) st[i] = hm_c128{(double)tmp[i].x, (double)tmp[i].y};
+        } else if ((e = cudaMemcpyAsync(st.data(), h->d_Wc + a, sizeof(double2) * (b - a), cudaMemcpyDeviceToHost,
+                                        h->stream)) ||
+                   (e = cudaStreamSynchronize(h->stream)))
+            return cuda_fail(h, e, "hm_get_block");
+        for (int x = P.sptr[k]; x < P.sptr[k + 1]; ++x) {
+            const int64_t nj = P.size[P.sidx[x]], r = h->crank[x];
+            const hm_c128 *blk = st.data() + (h->cboff[x] - a);
+            hm_c128 *dst = out + (int64_t)P.srow[x] * nk;   // the panel's columns of block x
+            for (int64_t c = 0; c < nj; ++c)
+                for (int64_t q = 0; q < nk; ++q) {
+                    if (r < 0) {
+                        dst[q + c * nk] = blk[q + c * nk];
+                        continue;
+                    }
+                    double re = 0, im = 0;   // sum_l P(q, l) Q(c, l)
+                    for (int64_t l = 0; l < r; ++l) {
+                        const hm_c128 p = blk[q + l * nk], w = blk[nk * r + c + l * nj];
+                        re += p.re * w.re - p.im * w.im;
+                        im += p.re * w.im + p.im * w.re;
+                    }
+                    dst[q + c * nk] = hm_c128{re, im};
+                }
+        }
+        return HM_OK;
     } else {
         src = mixed ? (const void *)(h->d_W32 + P.coff[k]) : (const void *)(h->d_W + P.coff[k]);
         f32 = mixed;
@@ -491,6 +525,13 @@ int hm_test_hold(hm_handle h, int32_t block, int64_t wait_ns)
         (e = cudaMemcpy(h->d_err + ERR_HOLD, w + ERR_HOLD, sizeof(int) * (ERR_WORDS - ERR_HOLD),
                         cudaMemcpyHostToDevice)))
         return cuda_fail(h, e, "hm_test_hold");
+    return HM_OK;
+}
+
+int hm_set_far_schedule(hm_handle h, int32_t kind)
+{
+    if (!h || kind < 0 || kind > 2) return HM_EINVAL;
+    h->far_kind = kind == 0 ? 2 : kind;
     return HM_OK;
 }
 

@@ -4,8 +4,10 @@
 // not a near-field pair (a fill-in block) is replaced by its truncated SVD of the smallest
 // rank r whose singular-value tail has Frobenius norm <= fill_tol ||W_kj||_F; blocks for
 // which r (n_k + n_j) >= n_k n_j stay dense.  Near-pattern blocks are never compressed.
-// The truncated block is written back in place (the sweeps then apply the compressed
-// coefficients), and its rank is recorded.
+// The truncation is written into the block's own panel slot as its factors P (n_k x r, the
+// left singular vectors scaled by the singular values) then Q (n_j x r), W_kj ~ P Q^T
+// (r (n_k + n_j) < n_k n_j entries, so they fit), and its rank is recorded; pack_run then
+// gathers every block -- dense, or its factors -- into the compact store the sweeps read.
 //
 // One CTA per fill-in block: one-sided (Hestenes) Jacobi SVD in shared memory of A = W when
 // n_k >= n_j and of A = W^H otherwise, so that A never has more columns than rows (surplus
@@ -177,18 +179,94 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
     __syncthreads();
     const int r = s_rank;
     if (r >= 0) {
-        for (int x = threadIdx.x; x < m * n; x += blockDim.x) {
-            const int row = x % m, c = x / m;
-            TC acc = czero(TC());
-            for (int l = 0; l < r; ++l) {   // W = A V^H, or (A V^H)^H = V A^H for the transposed case
-                const int o = ord[l];
-                acc = tr ? cfma(V[o * 64 + row], conjd(A[o * 64 + c]), acc)
-                         : cfma(A[o * 64 + row], conjd(V[o * 64 + c]), acc);
-            }
-            Wb[x] = acc;
+        // W ~ sum over the r largest of a_o conj(v_o)^T (W = A V^H), or of v_o conj(a_o)^T in the
+        // transposed case (W = (A V^H)^H = V A^H): P(:, l) and Q(:, l) from the l-th largest
+        TC *Pb = Wb, *Qb = Wb + (int64_t)m * r;
+        for (int x = threadIdx.x; x < m * r; x += blockDim.x) {
+            const int row = x % m, o = ord[x / m];
+            Pb[x] = tr ? V[o * 64 + row] : A[o * 64 + row];
+        }
+        for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
+            const int c = x % n, o = ord[x / n];
+            Qb[x] = conjd(tr ? A[o * 64 + c] : V[o * 64 + c]);
         }
     }
     if (threadIdx.x == 0) rank_out[f] = r;
+}
+
+// dst[e] <- the block's stored entries (dense n_k n_j, or r (n_k + n_j) factor entries), one
+// CTA per S-list entry
+template <class TC>
+__global__ void k_pack(int ne, const int64_t *pboff, const int64_t *cboff, const TC *W, TC *Wc)
+{
+    const int e = blockIdx.x;
+    if (e >= ne) return;
+    const int64_t len = cboff[e + 1] - cboff[e];
+    const TC *src = W + pboff[e];
+    TC *dst = Wc + cboff[e];
+    for (int64_t x = threadIdx.x; x < len; x += blockDim.x) dst[x] = src[x];
+}
+
+// The store the sweeps read (see hm_ctx::d_Wc): with no compressed block the panels themselves;
+// otherwise a compact copy with the factors of the compressed blocks, offsets and ranks uploaded.
+cudaError_t pack_run(hm_ctx *h)
+{
+    const Plan &P = h->plan;
+    const bool mixed = h->opts.precision == 1;
+    const int ne = (int)P.sidx.size();
+    cudaError_t e;
+    bool lr = false;
+    for (int r : h->fill_ranks) lr = lr || r >= 0;
+    if (!lr) {
+        if (h->wc_len) {
+            h->arena.release(mixed ? (void *)h->d_Wc32 : (void *)h->d_Wc, 0);
+            h->wc_len = 0;
+        }
+        if (h->lowrank) {   // back to the panel layout
+            if ((e = cudaMemcpyAsync(h->d_cboff, P.pboff.data(), sizeof(int64_t) * ne, cudaMemcpyHostToDevice,
+                                     h->stream)))
+                return e;
+            if ((e = cudaMemsetAsync(h->d_crank, 0xff, sizeof(int) * ne, h->stream))) return e;
+        }
+        h->lowrank = false;
+        h->d_Wc = h->d_W;
+        h->d_Wc32 = h->d_W32;
+        h->cboff = P.pboff;
+        h->crank.assign(ne, -1);
+        return cudaStreamSynchronize(h->stream);
+    }
+    h->crank.assign(ne, -1);
+    for (size_t f = 0; f < P.fill_e.size(); ++f) h->crank[P.fill_e[f]] = h->fill_ranks[f];
+    h->cboff.assign(ne + 1, 0);
+    for (int k = 0; k < P.nb; ++k)
+        for (int x = P.sptr[k]; x < P.sptr[k + 1]; ++x) {
+            const int64_t nk = P.size[k], nj = P.size[P.sidx[x]], r = h->crank[x];
+            h->cboff[x + 1] = h->cboff[x] + (r < 0 ? nk * nj : r * (nk + nj));
+        }
+    const int64_t total = h->cboff[ne];
+    if (h->wc_len != total) {
+        if (h->wc_len) h->arena.release(mixed ? (void *)h->d_Wc32 : (void *)h->d_Wc, 0);
+        h->wc_len = 0;
+        if ((e = mixed ? h->arena.alloc((void **)&h->d_Wc32, sizeof(float2) * total)
+                       : h->arena.alloc((void **)&h->d_Wc, sizeof(double2) * total)))
+            return e;
+        h->wc_len = total;
+    }
+    if ((e = cudaMemcpyAsync(h->d_cboff, h->cboff.data(), sizeof(int64_t) * (ne + 1), cudaMemcpyHostToDevice,
+                             h->stream)) ||
+        (e = cudaMemcpyAsync(h->d_crank, h->crank.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, h->stream)))
+        return e;
+    if (ne > 0) {
+        if (mixed)
+            HM_LAUNCH(h, K_COMPRESS, k_pack<float2><<<ne, 128, 0, h->stream>>>(ne, h->d_pboff, h->d_cboff, h->d_W32,
+                                                                               h->d_Wc32));
+        else
+            HM_LAUNCH(h, K_COMPRESS, k_pack<double2><<<ne, 128, 0, h->stream>>>(ne, h->d_pboff, h->d_cboff, h->d_W,
+                                                                                h->d_Wc));
+    }
+    h->lowrank = true;
+    if ((e = cudaGetLastError())) return e;
+    return cudaStreamSynchronize(h->stream);
 }
 
 cudaError_t compress_run(hm_ctx *h)

@@ -19,6 +19,7 @@
 // sides share the launch.
 #include "cplx.cuh"
 #include "hm_internal.h"
+#include "tc.cuh"
 #include "tile.cuh"
 
 namespace hm {
@@ -201,6 +202,209 @@ __global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, cons
     tile_store(acc, part + (size_t)pp * n * nrhs + cl2new[a], 1, n, ni, nrhs, nrt, ntiles);
 }
 
+// ---- complex FP32 on the tensor cores ------------------------------------------------------
+// The same two phases with the block products on the tensor-core micro-kernel of tc.cuh
+// (TF32 operands split into a rounded part and a remainder, FP32 accumulation in tensor
+// memory), contraction chunks of tc::KC: the coefficient rows of the next chunk are copied
+// with cp.async into the other raw buffer while the current chunk's vector rows are loaded into
+// registers; once the previous chunk's MMAs have finished both are split into the operand
+// planes and thread 0 issues the chunk's MMAs.  Fixed chunk order, so every output sums its
+// terms in one order whatever the number of right-hand sides.
+constexpr int FTC_LD = 64;                          // raw coefficients: raw[kk * FTC_LD + row]
+constexpr int FTC_RAW = tc::KC * FTC_LD * 8;         // bytes of one raw buffer
+constexpr unsigned long long FTC_WAIT_NS = 2000000000ull;
+constexpr size_t FTC_SMEM = tc::REGION_BYTES + 2 * FTC_RAW + 1024;
+
+// Phase 1: task -> up to 64 factor columns (rows of the product) contracted over [lo, hi)
+__global__ void __launch_bounds__(256, 2) k_far_t_tc(const int *task_lo, const int *task_hi, const int *task_ptr,
+                                                     const int64_t *item_off, const int *item_ld,
+                                                     const int *item_rank, const int *item_row, const int *item_isv,
+                                                     const float2 *U, const float2 *V, const float2 *u, int nrhs,
+                                                     float2 *t, float2 *s, int *err)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ int s_item[64], s_l[64];
+    __shared__ const float2 *s_src[64];
+    __shared__ int s_R;
+    __shared__ uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    const int task = blockIdx.x;
+    const int lo = task_lo[task], hi = task_hi[task], i0 = task_ptr[task], i1 = task_ptr[task + 1];
+    if (threadIdx.x == 0) {
+        int R = 0;
+        for (int it = i0; it < i1; ++it)
+            for (int l = 0; l < item_rank[it] && R < 64; ++l, ++R) {
+                s_item[R] = it;
+                s_l[R] = l;
+                s_src[R] = (item_isv[it] ? V : U) + item_off[it] + (int64_t)l * item_ld[it];
+            }
+        s_R = R;
+    }
+    __syncthreads();
+    const int R = s_R;
+    if (R == 0) return;
+    unsigned char *region = tc::align1024(smraw);
+    float2 *raw[2] = {(float2 *)(region + tc::REGION_BYTES), (float2 *)(region + tc::REGION_BYTES + FTC_RAW)};
+    tc::Acc acc;
+    acc.planes = region;
+    acc.mbar = &s_mbar;
+    acc.tslot = &s_tmem;
+    acc.open(R, nrhs);
+    auto prefetch = [&](int c0, int buf) {
+        const int kl = min(tc::KC, hi - c0);
+        for (int e = threadIdx.x; e < kl * R; e += blockDim.x) {
+            const int kk = e % kl, rr = e / kl;
+            cp_async_el(raw[buf] + kk * FTC_LD + rr, s_src[rr] + (c0 - lo + kk));
+        }
+        cp_async_commit();
+    };
+    if (lo < hi) prefetch(lo, 0);
+    for (int c0 = lo, it = 0; c0 < hi; c0 += tc::KC, ++it) {
+        const int kl = min(tc::KC, hi - c0), cnt = kl * nrhs;
+        float2 v[8];
+        const float2 *uc = u + (int64_t)c0 * nrhs;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = threadIdx.x + q * blockDim.x;
+            if (e < cnt) v[q] = uc[e];
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        if (c0 + tc::KC < hi) prefetch(c0 + tc::KC, (it + 1) & 1);
+        acc.wait(err, FTC_WAIT_NS);
+        const float2 *rw = raw[it & 1];
+        for (int e = threadIdx.x; e < acc.m8 * kl; e += blockDim.x) {
+            const int r = e % acc.m8, kk = e / acc.m8;
+            acc.put_a(r, kk, r < R ? rw[kk * FTC_LD + r] : make_float2(0.f, 0.f));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = threadIdx.x + q * blockDim.x;
+            if (e < cnt) acc.put_b(e % nrhs, e / nrhs, v[q]);
+        }
+        acc.zero_pad(kl);
+        acc.issue(kl);
+    }
+    acc.wait(err, FTC_WAIT_NS);
+    float *dsm = (float *)region;
+    const bool any = acc.drain(dsm);
+    for (int e = threadIdx.x; e < R * nrhs; e += blockDim.x) {
+        const int rr = e / nrhs, r = e % nrhs, it = s_item[rr];
+        float2 *dst = item_isv[it] ? t : s;
+        dst[(int64_t)(item_row[it] + s_l[rr]) * nrhs + r] = any ? acc.entry(dsm, rr, r) : make_float2(0.f, 0.f);
+    }
+    acc.close();
+}
+
+// Phase 2: CTA = (leaf, part); chunks of whole segments up to tc::KC entries
+struct FarTcChunk {
+    const float2 *f[tc::KC];   // coefficient entry kk of row i: f[kk][i * fi[kk]]
+    int fi[tc::KC];
+    const float2 *y[tc::KC];   // vector entry kk of column r: y[kk][r]
+    int kl, next;
+};
+
+// warp 0: the chunk of segments starting at p (those whose stacked length fits tc::KC)
+__device__ __forceinline__ void far_tc_chunk(int p, int w1, const int *kcum, const FarSegD *segs, const float2 *U,
+                                             const float2 *V, const float2 *t, const float2 *s, const float2 *u,
+                                             int nrhs, FarTcChunk &c)
+{
+    const int lane = threadIdx.x & 31, q = p + lane;
+    const int k0 = p < w1 ? kcum[p] : 0;
+    const bool fit = p < w1 && q < w1 && kcum[q + 1] - k0 <= tc::KC;
+    const unsigned m = __ballot_sync(0xffffffffu, fit);
+    const int cnt = __popc(m);
+    if (fit) {
+        const FarSegD g = segs[q];
+        const int kb = kcum[q] - k0;
+        const float2 *F = ((g.src & 1) ? V : U) + g.foff;
+        const int ys = g.src >> 1;
+        const float2 *Yb = (ys == 0 ? t : (ys == 1 ? s : u)) + g.yrow * nrhs;
+        for (int k = 0; k < g.len; ++k) {
+            c.f[kb + k] = F + (int64_t)k * g.fk;
+            c.fi[kb + k] = g.fi;
+            c.y[kb + k] = Yb + (int64_t)k * nrhs;
+        }
+    }
+    if (lane == 0) {
+        c.kl = cnt > 0 ? kcum[p + cnt] - k0 : 0;
+        c.next = p + cnt;
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_far_y_tc(int nl, const int *leaf_ptr, const int *part_ptr,
+                                                     const int *kcum, const FarSegD *segs, const float2 *U,
+                                                     const float2 *V, const float2 *t, const float2 *s,
+                                                     const float2 *u, const int *cl2new, int n, int nrhs,
+                                                     float2 *part, int *err)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ FarTcChunk s_ch[2];
+    __shared__ uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    const int l = blockIdx.x / FAR_PARTS, pp = blockIdx.x % FAR_PARTS;
+    if (l >= nl) return;
+    const int a = leaf_ptr[l], ni = leaf_ptr[l + 1] - a;
+    const int p0 = part_ptr[blockIdx.x], w1 = part_ptr[blockIdx.x + 1];
+    float2 *out = part + (size_t)pp * n * nrhs + cl2new[a];
+    if (p0 >= w1) {   // an empty part still contributes zeros to the sum
+        for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) out[e % ni + (int64_t)(e / ni) * n] = make_float2(0.f, 0.f);
+        return;
+    }
+    unsigned char *region = tc::align1024(smraw);
+    float2 *raw[2] = {(float2 *)(region + tc::REGION_BYTES), (float2 *)(region + tc::REGION_BYTES + FTC_RAW)};
+    tc::Acc acc;
+    acc.planes = region;
+    acc.mbar = &s_mbar;
+    acc.tslot = &s_tmem;
+    if (threadIdx.x < 32) far_tc_chunk(p0, w1, kcum, segs, U, V, t, s, u, nrhs, s_ch[0]);
+    acc.open(ni, nrhs);   // synchronises: s_ch[0] is visible
+    auto prefetch = [&](int buf) {
+        const FarTcChunk &c = s_ch[buf];
+        for (int e = threadIdx.x; e < c.kl * ni; e += blockDim.x) {
+            const int i = e % ni, kk = e / ni;
+            cp_async_el(raw[buf] + kk * FTC_LD + i, c.f[kk] + (int64_t)i * c.fi[kk]);
+        }
+        cp_async_commit();
+    };
+    prefetch(0);
+    for (int cur = 0; s_ch[cur].kl > 0; cur ^= 1) {
+        const FarTcChunk &c = s_ch[cur];
+        const int kl = c.kl, cnt = kl * nrhs;
+        if (threadIdx.x < 32) far_tc_chunk(c.next, w1, kcum, segs, U, V, t, s, u, nrhs, s_ch[cur ^ 1]);
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = threadIdx.x + q * blockDim.x;
+            if (e < cnt) v[q] = c.y[e / nrhs][e % nrhs];
+        }
+        cp_async_wait<0>();
+        __syncthreads();   // raw[cur] landed everywhere; s_ch[cur ^ 1] written
+        if (s_ch[cur ^ 1].kl > 0) prefetch(cur ^ 1);
+        acc.wait(err, FTC_WAIT_NS);
+        const float2 *rw = raw[cur];
+        for (int e = threadIdx.x; e < acc.m8 * kl; e += blockDim.x) {
+            const int r = e % acc.m8, kk = e / acc.m8;
+            acc.put_a(r, kk, r < ni ? rw[kk * FTC_LD + r] : make_float2(0.f, 0.f));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = threadIdx.x + q * blockDim.x;
+            if (e < cnt) acc.put_b(e % nrhs, e / nrhs, v[q]);
+        }
+        acc.zero_pad(kl);
+        acc.issue(kl);
+    }
+    acc.wait(err, FTC_WAIT_NS);
+    float *dsm = (float *)region;
+    const bool any = acc.drain(dsm);
+    for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {
+        const int i = e % ni, r = e / ni;
+        out[i + (int64_t)r * n] = any ? acc.entry(dsm, i, r) : make_float2(0.f, 0.f);
+    }
+    acc.close();
+}
+
 // y = sum of the FAR_PARTS partial products, added in part order
 template <class T> __global__ void k_far_sum(int64_t len, const T *part, T *y)
 {
@@ -257,11 +461,43 @@ template <class T> struct FarLaunch {
 };
 }  // namespace
 
+// complex FP32 on the tensor cores: phase 1, the phase-2 partial products, their sum
+static cudaError_t far_tc_launch(hm_ctx *h, const float2 *U, const float2 *V, float2 *t, float2 *s,
+                                 const float2 *ucl, float2 *y, int nrhs)
+{
+    const FarPlan &F = h->fplan;
+    const int n = h->plan.n;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_far_t_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM)) ||
+            (e = cudaFuncSetAttribute(k_far_y_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM)))
+            return e;
+        attr = true;
+    }
+    const int ntask = (int)F.p1_lo.size();
+    if (ntask > 0)
+        HM_LAUNCH(h, K_FAR1,
+                  (k_far_t_tc<<<ntask, 256, FTC_SMEM, h->stream>>>(h->d_p1_lo, h->d_p1_hi, h->d_p1_ptr, h->d_p1_off,
+                                                                   h->d_p1_ld, h->d_p1_rank, h->d_p1_row, h->d_p1_isv,
+                                                                   U, V, ucl, nrhs, t, s, h->d_err)));
+    float2 *part = (float2 *)h->d_farpart;
+    HM_LAUNCH(h, K_FAR2,
+              (k_far_y_tc<<<h->nl * FAR_PARTS, 256, FTC_SMEM, h->stream>>>(
+                  h->nl, h->d_leaf_ptr, h->d_part_ptr, h->d_seg_kcum, h->d_segs, U, V, t, s, ucl, h->d_cl2new, n, nrhs,
+                  part, h->d_err)));
+    const int64_t len = (int64_t)n * nrhs;
+    HM_LAUNCH(h, K_FAR2, k_far_sum<float2><<<nblk(len, 256), 256, 0, h->stream>>>(len, part, y));
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t far_product(hm_ctx *h, const T *U, const T *V, T *t, T *s, const T *ucl, T *y, int nrhs)
 {
     h->prof.cols[K_FAR1] += nrhs;
     h->prof.cols[K_FAR2] += nrhs;
+    if constexpr (sizeof(T) == 8)
+        if (h->far_kind == 2) return far_tc_launch(h, U, V, t, s, ucl, y, nrhs);
     FarLaunch<T> f{h, U, V, t, s, ucl, y, nrhs};
     return tile_dispatch<T>(nrhs, f);
 }

@@ -72,6 +72,9 @@ struct Plan {
     // forward sweep gathers: row i <- blocks W_ki, k < i; rptr/ridx = k, rcol = column
     // offset of block i inside panel k
     std::vector<int> rptr, ridx, rcol;
+    std::vector<int> rent;       // the S-list entry e of each forward gather entry (block (k, j))
+    std::vector<int64_t> pboff;  // per S-list entry e: offset of block (k, S_k[e]) in the W panels
+                                 // (one more entry: the panels' total)
     // fill-in blocks (Sec. 3.4): entries e of sidx whose pair (k, S_k[e]) is not a near pair
     std::vector<int> fill_e;     // entry index into sidx
     std::vector<int> fill_k;     // its block row k
@@ -188,6 +191,18 @@ struct hm_ctx {
     double2 *d_Ad = nullptr;     // diagonal blocks workspace -> D_k after setup
     double2 *d_W = nullptr;      // coefficient panels W_k (uncompressed)
     double2 *d_Dinv = nullptr;   // D_k^{-1}
+    // the coefficient store the sweeps read: per S-list entry e, block (k, S_k[e]) at
+    // Wc + cboff[e], dense (crank[e] = -1, n_k x n_j column-major) or, for a Sec. 3.4
+    // compressed fill-in block of rank r, its factors P (n_k x r) then Q (n_j x r), W_kj ~ P Q^T.
+    // Without compressed blocks Wc is the panel array itself (cboff = pboff).
+    double2 *d_Wc = nullptr;
+    float2 *d_Wc32 = nullptr;
+    int64_t wc_len = 0;          // entries of Wc when it is its own allocation (0: it aliases W)
+    bool lowrank = false;        // some block is stored as factors
+    int64_t *d_cboff = nullptr, *d_pboff = nullptr;
+    int *d_crank = nullptr, *d_rent = nullptr;
+    std::vector<int64_t> cboff;
+    std::vector<int> crank;
     bool setup_done = false;
     double setup_ms = 0;
     // fill-in compression (Sec. 3.4): block lists and the ranks of the last setup (-1 dense)
@@ -211,6 +226,7 @@ struct hm_ctx {
     bool batch_open = false;   // an hm_batch holds this handle
     hm::SweepTune sweep_tune[2][2][5];   // [FP32][forward][width class]
     int sweep_fixed = 0;                 // a schedule code set by hm_set_sweep_schedule, 0 = tuned
+    int far_kind = 2;                    // complex-FP32 far field: 1 CUDA cores, 2 tensor cores
 };
 
 // Launch wrapper: counts every launch by kernel class and, when profiling is on, brackets
@@ -241,6 +257,7 @@ void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &p
 // kernels (setup.cu / solve.cu): return cudaError_t of the launches
 cudaError_t setup_run(hm_ctx *h, int *bad_block);
 cudaError_t compress_run(hm_ctx *h);
+cudaError_t pack_run(hm_ctx *h);
 cudaError_t op_apply(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
 cudaError_t op_apply32(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
 cudaError_t make_fp32_copies(hm_ctx *h);

@@ -74,17 +74,28 @@ constexpr int TAIL = 4;
 // Next chunk [p, q) of a dependency list walked from p towards pend (step +1 or -1): blocks
 // are added while their staged entries fit the budget; each of the last TAIL dependencies
 // forms a chunk of its own.
+// Low-rank blocks (see lowrank_t) also count their r * nrhs outputs, at most LR_OUT per chunk.
+constexpr int LR_REG = 16;                 // outputs of lowrank_t per thread
+constexpr int LR_OUT = LR_REG * 256;       // per chunk (256 threads)
+
+__device__ __forceinline__ int dep_rank(const int *crk, const int *ent, int b)
+{
+    return crk ? crk[ent ? ent[b] : b] : -1;
+}
+
 template <int TR, int TC>
 __device__ __forceinline__ int next_chunk(int p, int pend, int step, const int *dep, const int *size, int no,
-                                          int nrhs, int budget)
+                                          int nrhs, int budget, const int *crk, const int *ent)
 {
     const int tail0 = pend - TAIL * step;   // first position of the tail
     if ((step > 0 && p >= tail0) || (step < 0 && p <= tail0)) return p + step;
-    int q = p, used = 0, cnt = 0;
+    int q = p, used = 0, cnt = 0, lr = 0;
     while (q != tail0 && cnt < 16) {
-        const int need = stage_need(no, size[dep[q]], nrhs, TR, TC);
-        if (cnt > 0 && used + need > budget) break;
+        const int need = stage_need(no, size[dep[q]], nrhs, TR, TC), r = dep_rank(crk, ent, q);
+        const int lo = r > 0 ? r * nrhs : 0;
+        if (cnt > 0 && (used + need > budget || lr + lo > LR_OUT)) break;
         used += need;
+        lr += lo;
         ++cnt;
         q += step;
     }
@@ -181,16 +192,96 @@ __device__ __forceinline__ void stage_tagged(int count, unsigned epoch, int *err
     }
 }
 
+// A compressed fill-in coefficient block (Sec. 3.4) is stored as P (n_k x r), Q (n_j x r),
+// W_kj ~ P Q^T, and applied as two products: with G the factor on the dependency's side and H
+// the one on the row's side (forward, block W_ko: G = P, H = Q; backward, W_oj: G = Q, H = P),
+// t = G^T y_dep (r x nrhs), then out -= H t.  Staging: H in the block's coefficient slot as an
+// r-long contraction (Ws[l * ldw + row]), G behind it (Ws[r * ldw + q + l * nc]), y_dep as for
+// a dense block; r (ldw + nc) <= nc ldw holds for every compressed block, so it fits the slot.
+// lowrank_t computes every t of a chunk into registers, then (after a barrier) writes each over
+// its block's vector slot (t[l + c * r]), so the chunk's products run as for dense blocks.
+// SPLIT (complex-FP32 sweeps): coefficient blocks packed in wbase (nc * ldw entries each),
+// vector blocks in ybase (nc * nrhs each); otherwise (FP64) block after block in wbase, each
+// its coefficients then its vector block (nc * ldw + nc * ldr entries).
+template <class T, bool SPLIT>
+__device__ void lowrank_t(int p, int q, int step, const int *lidx, const int *size, const int *crk, const int *ent,
+                          T *wbase, T *ybase, int ldw, int ldr, int nrhs)
+{
+    T treg[LR_REG];
+    int u = 0, ng = threadIdx.x, base = 0, ow = 0, oy = 0;
+    for (int b = p; b != q; b += step) {
+        const int nc = size[lidx[b]], r = dep_rank(crk, ent, b);
+        if (r >= 0) {
+            const T *G = wbase + ow + r * ldw, *Y = SPLIT ? ybase + oy : wbase + ow + nc * ldw;
+            const int len = r * nrhs;
+            for (; ng < base + len && u < LR_REG; ng += blockDim.x) {
+                const int o = ng - base, l = o % r, c = o / r;
+                T acc = czero(T());
+                for (int qq = 0; qq < nc; ++qq) acc = cfma(G[qq + l * nc], Y[qq + c * nc], acc);
+                treg[u++] = acc;
+            }
+            base += len;
+        }
+        ow += SPLIT ? nc * ldw : nc * (ldw + ldr);
+        oy += nc * nrhs;
+    }
+    __syncthreads();   // every t read its vector block
+    u = 0;
+    ng = threadIdx.x;
+    base = 0;
+    ow = 0;
+    oy = 0;
+    for (int b = p; b != q; b += step) {
+        const int nc = size[lidx[b]], r = dep_rank(crk, ent, b);
+        if (r >= 0) {
+            T *Y = SPLIT ? ybase + oy : wbase + ow + nc * ldw;
+            const int len = r * nrhs;
+            for (; ng < base + len && u < LR_REG; ng += blockDim.x) Y[ng - base] = treg[u++];
+            base += len;
+        }
+        ow += SPLIT ? nc * ldw : nc * (ldw + ldr);
+        oy += nc * nrhs;
+    }
+    __syncthreads();
+}
+
+// Where dependency b's coefficient block is staged from, and how: copy(dst, src) is the element
+// copy (cp.async or a load and a store) of entry src into the staged entry dst.  Dense: the
+// block M (rows of o, contraction over the dependency's rows) as Ws[qq * ldw + row]; low rank
+// (lowrank_t): H as Ws[l * ldw + row] and G behind it.
+template <class T, bool FWD, class Copy>
+__device__ __forceinline__ void stage_block(int b, int no, int nc, const int *lent, const int64_t *cbo,
+                                            const int *crk, const T *W, T *Ws, int ldw, Copy &&copy)
+{
+    const int e = lent ? lent[b] : b, r = crk[e];
+    const T *base = W + cbo[e];
+    if (r < 0) {
+        if (FWD)   // W_ko: nc x no; M(row, qq) = W_ko(qq, row)
+            for (int x = threadIdx.x; x < nc * no; x += blockDim.x) copy(Ws + (x % nc) * ldw + x / nc, base + x);
+        else       // W_oj: no x nc; M(row, qq) = W_oj(row, qq)
+            for (int x = threadIdx.x; x < nc * no; x += blockDim.x) copy(Ws + (x / no) * ldw + x % no, base + x);
+        return;
+    }
+    // W_kj ~ P Q^T with P (n_k x r) then Q (n_j x r): forward (k = dep, j = o) G = P, H = Q;
+    // backward (k = o, j = dep) H = P, G = Q
+    const T *H = FWD ? base + (int64_t)nc * r : base, *G = FWD ? base : base + (int64_t)no * r;
+    for (int x = threadIdx.x; x < no * r; x += blockDim.x) copy(Ws + (x / no) * ldw + x % no, H + x);
+    for (int x = threadIdx.x; x < nc * r; x += blockDim.x) copy(Ws + r * ldw + x, G + x);
+}
+
 template <class T, int TR, int TC, int NT, bool FWD, bool LL = false>
 __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, const int *boff, const int *lptr,
-                                          const int *lidx, const int *lcol, const int64_t *coff, const T *W,
-                                          const T *x, T *y, int n, int nrhs, int budget, int *flags, int epoch,
-                                          int *err, T *buf, int cut = 0, int *pub = nullptr, uint4 *tag = nullptr)
+                                          const int *lidx, const int *lent, const int64_t *cbo, const int *crk,
+                                          const T *W, const T *x, T *y, int n, int nrhs, int budget, int *flags,
+                                          int epoch, int *err, T *buf, int cut = 0, int *pub = nullptr,
+                                          uint4 *tag = nullptr)
 {
     // LL (complex FP32 only): dependencies are read from, and the result published to, the
     // tagged copy `tag` (same layout as y); no flags, no fence
     // cut > 0: leave the last `cut` dependencies of the walk out (they are added by the
     // chain CTA of a chain-and-helpers sweep) and publish the partial sum on `pub`
+    // Dependency b of the walk is S-list entry lent[b] (forward) or b itself (backward), its
+    // coefficients at W + cbo[e], dense or of rank crk[e] (stage_block, lowrank_t).
     if (!pub) pub = flags;
     const int o = boff[o_blk];
     const int nrt = (no + TR - 1) / TR, ntiles = nrt * ((nrhs + TC - 1) / TC);
@@ -201,6 +292,11 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
     const int step = FWD ? 1 : -1;
     const int pa = FWD ? lptr[o_blk] : lptr[o_blk + 1] - 1,
               pend = (FWD ? lptr[o_blk + 1] : lptr[o_blk] - 1) - cut * step;
+    // contraction length of dependency b's product: its rows, or its rank when compressed
+    auto kdim = [&](int b, int nc) {
+        const int r = dep_rank(crk, lent, b);
+        return r < 0 ? nc : r;
+    };
     if constexpr (LL) {
         // the coefficient blocks of the next chunk are copied (cp.async, no registers held)
         // into the other buffer while the current chunk waits for its vector blocks and
@@ -210,17 +306,9 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
         auto stage_w = [&](int p, int q, T *dst) {
             int off = 0;
             for (int b = p; b != q; b += step) {
-                const int k = lidx[b], nc = size[k];
-                T *Ws = dst + off;
-                if (FWD) {   // W_ko: nc x no at coff[k] + lcol*nc; M(row, qq) = W_ko(qq, row)
-                    const T *src = W + coff[k] + (int64_t)lcol[b] * nc;
-                    for (int e = threadIdx.x; e < nc * no; e += blockDim.x)
-                        cp_async_el(Ws + (e % nc) * ldw + e / nc, src + e);
-                } else {     // W_oj: no x nc at coff[o] + lcol*no; M(row, qq) = W_oj(row, qq)
-                    const T *src = W + coff[o_blk] + (int64_t)lcol[b] * no;
-                    for (int e = threadIdx.x; e < nc * no; e += blockDim.x)
-                        cp_async_el(Ws + (e / no) * ldw + e % no, src + e);
-                }
+                const int nc = size[lidx[b]];
+                stage_block<T, FWD>(b, no, nc, lent, cbo, crk, W, dst + off, ldw,
+                                    [](T *d, const T *src) { cp_async_el(d, src); });
                 off += nc * ldw;
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -235,9 +323,11 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
                     stage_w(q, q2, wbuf(cur ^ 1));
                 }
                 int yoff = 0;
+                bool lr = false;
                 for (int b = p; b != q; b += step) {
                     const int k = lidx[b], nc = size[k], ok = boff[k];
                     T *Ys = ys + yoff;
+                    lr = lr || dep_rank(crk, lent, b) >= 0;
                     stage_tagged((int)(nc * nrhs), (unsigned)epoch, err,
                                  [&](int e) { return tag + ok + e % nc + (int64_t)(e / nc) * n; },
                                  [&](int e, float2 v) { Ys[e] = v; });
@@ -246,12 +336,13 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
                 if (q != pend) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
                 else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
                 __syncthreads();
-                const T *wc = wbuf(cur);
+                T *wc = wbuf(cur);
+                if (lr) lowrank_t<T, true>(p, q, step, lidx, size, crk, lent, wc, ys, ldw, 0, nrhs);
                 int woff = 0;
                 yoff = 0;
                 for (int b = p; b != q; b += step) {
-                    const int nc = size[lidx[b]];
-                    tile_mac<true>(acc, wc + woff, ldw, ys + yoff, 1, nc, nc, nrt, ntiles);
+                    const int nc = size[lidx[b]], kd = kdim(b, nc);
+                    tile_mac<true>(acc, wc + woff, ldw, ys + yoff, 1, kd, kd, nrt, ntiles);
                     woff += nc * ldw;
                     yoff += nc * nrhs;
                 }
@@ -262,21 +353,15 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
         }
     }
     for (int p = pa; !LL && p != pend;) {
-        const int q = next_chunk<TR, TC>(p, pend, step, lidx, size, no, nrhs, budget);
+        const int q = next_chunk<TR, TC>(p, pend, step, lidx, size, no, nrhs, budget, crk, lent);
+        const int ldr = stage_ldr(nrhs, TC);
         // stage the coefficient blocks (static data) before waiting
         int off = 0;
+        bool lr = false;
         for (int b = p; b != q; b += step) {
-            const int k = lidx[b], nc = size[k];
-            T *Ws = buf + off;
-            if (FWD) {   // W_ko: nc x no at coff[k] + lcol*nc; M(row, qq) = W_ko(qq, row)
-                const T *src = W + coff[k] + (int64_t)lcol[b] * nc;
-                stage_copy(nc * no, [&](int e) { return src[e]; },
-                           [&](int e, T v) { Ws[(e % nc) * ldw + e / nc] = v; });
-            } else {     // W_oj: no x nc at coff[o] + lcol*no; M(row, qq) = W_oj(row, qq)
-                const T *src = W + coff[o_blk] + (int64_t)lcol[b] * no;
-                stage_copy(nc * no, [&](int e) { return src[e]; },
-                           [&](int e, T v) { Ws[(e / no) * ldw + e % no] = v; });
-            }
+            const int nc = size[lidx[b]];
+            lr = lr || dep_rank(crk, lent, b) >= 0;
+            stage_block<T, FWD>(b, no, nc, lent, cbo, crk, W, buf + off, ldw, [](T *d, const T *src) { *d = *src; });
             off += stage_need(no, nc, nrhs, TR, TC);
         }
         if (threadIdx.x == 0)
@@ -291,10 +376,11 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
             off += stage_need(no, nc, nrhs, TR, TC);
         }
         __syncthreads();
+        if (lr) lowrank_t<T, false>(p, q, step, lidx, size, crk, lent, buf, buf, ldw, ldr, nrhs);
         off = 0;
         for (int b = p; b != q; b += step) {
-            const int nc = size[lidx[b]];
-            tile_mac<true>(acc, buf + off, ldw, buf + off + nc * ldw, 1, nc, nc, nrt, ntiles);
+            const int nc = size[lidx[b]], kd = kdim(b, nc);
+            tile_mac<true>(acc, buf + off, ldw, buf + off + nc * ldw, 1, kd, kd, nrt, ntiles);
             off += stage_need(no, nc, nrhs, TR, TC);
         }
         __syncthreads();
@@ -419,7 +505,6 @@ __global__ void __launch_bounds__(256, 2) k_sweep_tc(int nb, const int *size, co
         const int e = threadIdx.x + u * blockDim.x;
         xr[u] = e < no * nc ? x[o + e % no + (int64_t)(e / no) * n] : make_float2(0.f, 0.f);
     }
-    const int step = FWD ? 1 : -1;
     const int pa = FWD ? lptr[o_blk] : lptr[o_blk + 1] - 1, pend = FWD ? lptr[o_blk + 1] : lptr[o_blk] - 1;
     tc::Acc acc;
     acc.planes = region;
@@ -537,8 +622,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep_tc(int nb, const int *size, co
 // y = L^{-1} x : y_i = x_i - sum_{k < i, i in S_k} W_ki^T y_k   (Eq. 23)
 template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, const int *boff, const int *rptr,
-                                                   const int *ridx, const int *rcol, const int64_t *coff,
-                                                   const T *W, const T *x, T *y, int n, int nrhs, int G, int gw,
+                                                   const int *ridx, const int *rent, const int64_t *cbo,
+                                                   const int *crk, const T *W, const T *x, T *y, int n, int nrhs, int G, int gw,
                                                    int budget, int *flags, int epoch, int *ticket, int *err,
                                                    uint4 *tag)
 {
@@ -549,7 +634,7 @@ __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, cons
     const int i = s_t / G, g = s_t % G;
     if (i >= nb || held_back(err, i)) return;
     const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
-    sweep_row<T, TR, TC, NT, true, sizeof(T) == 8>(i, size[i], size, boff, rptr, ridx, rcol, coff, W,
+    sweep_row<T, TR, TC, NT, true, sizeof(T) == 8>(i, size[i], size, boff, rptr, ridx, rent, cbo, crk, W,
                                                    x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
                                                    flags + g * nb, epoch, err, (T *)smraw, 0, nullptr,
                                                    tag + (int64_t)c0 * n);
@@ -558,7 +643,7 @@ __global__ void __launch_bounds__(256) k_sweep_fwd(int nb, const int *size, cons
 // y = L^{-T} x : y_k = x_k - sum_{j in S_k} W_kj y_j   (Eq. 24); j walked downwards
 template <class T, int TR, int TC, int NT>
 __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, const int *boff, const int *sptr,
-                                                   const int *sidx, const int *srow, const int64_t *coff,
+                                                   const int *sidx, const int64_t *cbo, const int *crk,
                                                    const T *W, const T *x, T *y, int n, int nrhs, int G, int gw,
                                                    int budget, int *flags, int epoch, int *ticket, int *err,
                                                    uint4 *tag)
@@ -570,7 +655,7 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, cons
     const int k = nb - 1 - s_t / G, g = s_t % G;
     if (k < 0 || held_back(err, k)) return;
     const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
-    sweep_row<T, TR, TC, NT, false, sizeof(T) == 8>(k, size[k], size, boff, sptr, sidx, srow, coff, W,
+    sweep_row<T, TR, TC, NT, false, sizeof(T) == 8>(k, size[k], size, boff, sptr, sidx, nullptr, cbo, crk, W,
                                                     x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
                                                     flags + g * nb, epoch, err, (T *)smraw, 0, nullptr,
                                                     tag + (int64_t)c0 * n);
@@ -749,7 +834,8 @@ __device__ void chain_run(int nb, const int *size, const int *boff, const int *r
 template <class T, int TR, int TC, int NT, bool FWD>
 __global__ void __launch_bounds__(256) k_sweep_ch(int nb, const int *size, const int *boff, const int *lptr,
                                                   const int *lidx, const int *lcol, const int *rec, const int *reccol,
-                                                  const int64_t *coff, const T *W,
+                                                  const int64_t *coff, const int *lent, const int64_t *cbo,
+                                                  const int *crk, const T *W,
                                                   const T *x, T *y, int n, int nrhs, int G, int gw, int budget,
                                                   int *flags, int epoch, int *ticket, int *err)
 {
@@ -770,7 +856,7 @@ __global__ void __launch_bounds__(256) k_sweep_ch(int nb, const int *size, const
     const int qpos = (t - G) / G, b = FWD ? qpos : nb - 1 - qpos;
     if (held_back(err, b)) return;
     const int cut = recent_count<FWD>(b, lptr, lidx);
-    sweep_row<T, TR, TC, NT, FWD>(b, size[b], size, boff, lptr, lidx, lcol, coff, W, x + (int64_t)c0 * n,
+    sweep_row<T, TR, TC, NT, FWD>(b, size[b], size, boff, lptr, lidx, lent, cbo, crk, W, x + (int64_t)c0 * n,
                                   y + (int64_t)c0 * n, n, nc, budget, ffin, epoch, err, (T *)smraw, cut, fpart);
 }
 
@@ -839,7 +925,7 @@ __global__ void __launch_bounds__(256) k_sweep_sr(int nb, int nsr, const int *si
     // external dependencies, in the stored order
     const int pa = xptr[r], pend = xptr[r + 1];
     for (int p = pa; p != pend;) {
-        const int q = next_chunk<TR, TC>(p, pend, 1, xdep, size, no, nc, budget);
+        const int q = next_chunk<TR, TC>(p, pend, 1, xdep, size, no, nc, budget, nullptr, nullptr);
         int off = 0;
         for (int b = p; b != q; ++b) {
             const int k = xdep[b], nq = size[k];
@@ -1041,11 +1127,11 @@ template <class T> struct OpData {
 
 static OpData<double2> data64(hm_ctx *h)
 {
-    return {h->d_W, h->d_Ad, h->d_Dinv, h->d_farU, h->d_farV, h->d_t, h->d_s, h->d_work};
+    return {h->d_Wc, h->d_Ad, h->d_Dinv, h->d_farU, h->d_farV, h->d_t, h->d_s, h->d_work};
 }
 static OpData<float2> data32(hm_ctx *h)
 {
-    return {h->d_W32, h->d_Ad32, h->d_Dinv32, h->d_farU32, h->d_farV32, h->d_t32, h->d_s32, h->d_work32};
+    return {h->d_Wc32, h->d_Ad32, h->d_Dinv32, h->d_farU32, h->d_farV32, h->d_t32, h->d_s32, h->d_work32};
 }
 
 // Widest column batch one sweep launch takes (wider requests are split into slices).
@@ -1078,13 +1164,13 @@ static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, cons
     if (forward)
         HM_LAUNCH(h, K_SWEEP_FWD,
                   (k_sweep_fwd<T, TR, TC, NT><<<grid, 256, smem, h->stream>>>(
-                      P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol, h->d_coff, d.W, x, y, P.n, nrhs, G,
-                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err, h->d_ytag)));
+                      P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rent, h->d_cboff, h->d_crank, d.W, x, y,
+                      P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err, h->d_ytag)));
     else
         HM_LAUNCH(h, K_SWEEP_BWD,
                   (k_sweep_bwd<T, TR, TC, NT><<<grid, 256, smem, h->stream>>>(
-                      P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow, h->d_coff, d.W, x, y, P.n, nrhs, G,
-                      gw, budget, h->d_flags, ep, h->d_ticket, h->d_err, h->d_ytag)));
+                      P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_cboff, h->d_crank, d.W, x, y, P.n, nrhs,
+                      G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err, h->d_ytag)));
     return cudaGetLastError();
 }
 
@@ -1140,12 +1226,14 @@ static cudaError_t sweep_ch_shape(hm_ctx *h, const OpData<T> &d, bool forward, c
         HM_LAUNCH(h, K_SWEEP_FWD,
                   (k_sweep_ch<T, TR, TC, NT, true><<<grid, 256, smem, h->stream>>>(
                       P.nb, h->d_size, h->d_boff, h->d_rptr, h->d_ridx, h->d_rcol, h->d_rec[0], h->d_reccol[0],
-                      h->d_coff, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+                      h->d_coff, h->d_rent, h->d_cboff, h->d_crank, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep,
+                      h->d_ticket, h->d_err)));
     else
         HM_LAUNCH(h, K_SWEEP_BWD,
                   (k_sweep_ch<T, TR, TC, NT, false><<<grid, 256, smem, h->stream>>>(
                       P.nb, h->d_size, h->d_boff, h->d_sptr, h->d_sidx, h->d_srow, h->d_rec[1], h->d_reccol[1],
-                      h->d_coff, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err)));
+                      h->d_coff, (const int *)nullptr, h->d_cboff, h->d_crank, d.W, x, y, P.n, nrhs, G, gw, budget,
+                      h->d_flags, ep, h->d_ticket, h->d_err)));
     return cudaGetLastError();
 }
 
@@ -1241,7 +1329,10 @@ static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x
     SweepTune *tu;
     int slot = 0;
     const int code = sweep_groups(h, sizeof(T) == 8, forward, nrhs, &tu, &slot);
-    const int G = std::min(code & 15, nrhs), sr = code >> 4;
+    const int G = std::min(code & 15, nrhs);
+    // the super-row, chain-and-helpers and tensor-core kinds read the dense panel layout; with
+    // compressed fill-in blocks stored as factors every sweep takes kind 1
+    const int sr = h->lowrank ? 1 : code >> 4;
     const int gw = (nrhs + G - 1) / G;
     if (tu) cudaEventRecord(tu->ev[2 * slot], h->stream);
     if constexpr (sizeof(T) == 8) {

@@ -501,14 +501,20 @@ void plan_order(hm_ctx *h)
     for (int i = 0; i < nl; ++i) P.rptr[i + 1] = P.rptr[i] + cnt[i + 1];
     P.ridx.resize(P.rptr[nl]);
     P.rcol.resize(P.rptr[nl]);
+    P.rent.resize(P.rptr[nl]);
     std::vector<int> fillp(P.rptr.begin(), P.rptr.end() - 1);
     for (int k = 0; k < nl; ++k)
         for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e) {
             int j = P.sidx[e];
             P.ridx[fillp[j]] = k;
             P.rcol[fillp[j]] = P.srow[e];
+            P.rent[fillp[j]] = e;
             fillp[j]++;
         }
+    P.pboff.resize(P.sidx.size() + 1);
+    for (int k = 0; k < nl; ++k)
+        for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e) P.pboff[e] = P.coff[k] + (int64_t)P.srow[e] * P.size[k];
+    P.pboff[P.sidx.size()] = P.coef_entries;
     plan_superrows(P);
 }
 

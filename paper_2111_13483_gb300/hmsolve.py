@@ -60,7 +60,8 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_get_index_map", "hm_plan_order", "hm_plan_fill", "hm_profile", "hm_get_profile",
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
            "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
-           "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm", "hm_plan_order_method"]
+           "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm", "hm_plan_order_method",
+           "hm_set_far_schedule"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -117,6 +118,7 @@ def load(build_if_missing=True):
     L.hm_set_sweep_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
     L.hm_get_profile_cols.argtypes = [vp, ctypes.c_int32, _i64p]
     L.hm_test_hold.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
+    L.hm_set_far_schedule.argtypes = [vp, ctypes.c_int32]
     L.hm_tc_cgemm.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_int64, vp, ctypes.c_int64,
                               vp, ctypes.c_int64, vp]
     _lib = L
@@ -381,6 +383,11 @@ def hm_tc_cgemm(dA, dB, dC, stream=None):
     k, m = dA.shape
     nc = dB.shape[0]
     return load().hm_tc_cgemm(m, k, nc, dA.data_ptr(), m, dB.data_ptr(), k, dC.data_ptr(), m, stream)
+
+
+def hm_set_far_schedule(h, kind=0):
+    """Complex-FP32 far-field products: 1 CUDA cores, 2 tensor cores, 0 default (2)."""
+    h.check(load().hm_set_far_schedule(h.ptr, kind), "hm_set_far_schedule")
 
 
 def hm_get_fill_ranks(h):

@@ -26,6 +26,7 @@ import torch
 
 import paper_2111_13483_gb300 as hm
 from oracle import krylov, ordering, schur
+from refs import truncated_at
 
 pytestmark = pytest.mark.gpu
 H = hm.hmsolve
@@ -107,6 +108,48 @@ def test_7680_operators_64_columns(s7680, prec):
             assert rel(Y[:, c], ref) < tol, (op, c)
             assert elem_ok(Y[:, c], ref, 10 * tol), (op, c)
         for c in range(0, 64, 9):   # batch invariance: each column equals its one-column launch
+            assert np.array_equal(_apply(h, off + op, X[:, c:c + 1])[:, 0], Y[:, c]), (op, c)
+
+
+@pytest.fixture(scope="module")
+def s7680c(sphere7680):
+    """The same sphere with the fill-in blocks compressed at fill_tol 1e-2 (Sec. 3.4), stored
+    and applied as factors."""
+    P = sphere7680
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    F = schur.setup(P, order, fill_tol=1e-2)
+    S = krylov.System(P, F)
+    h64 = hm.hmat_create(P, ordering=1, fill_tol=1e-2, precision=0)
+    hm.precond_setup(h64)
+    h32 = hm.hmat_create(P, ordering=1, fill_tol=1e-2, precision=1)
+    hm.precond_setup(h32)
+    return P, F, S, h64, h32
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_7680_compressed_operators_64_columns(s7680c, prec):
+    P, F, S, h64, h32 = s7680c
+    h = h64 if prec == 0 else h32
+    off = 0 if prec == 0 else H.OP32
+    tol = 1e-10 if prec == 0 else 1e-4
+    if prec == 0:
+        ranks = hm.hmsolve.hm_get_fill_ranks(h)
+        ptr, idx = hm.hm_get_fill(h)
+        expect = [F.rank.get((k, j), -1) for k in range(F.nb) for j in F.S[k]]
+        assert np.array_equal(ranks, expect)
+        assert hm.hmat_stats(h)["coef_entries"] == schur.nnz_coefficients(F) - int(np.sum(F.size))
+    X = _rand(S.n, 64, 51 + prec)
+    refs = [(H.OP_LINV, S.L_inv), (H.OP_LTINV, S.LT_inv), (H.OP_A, S.apply_A)]
+    if prec == 1:   # the FP32 setup's ranks, truncated in FP64 (see truncated_at)
+        Wm = truncated_at(F, h)
+        refs = [(H.OP_LINV, lambda x: S.join(schur.sweep_forward(F, S.split(x), W=Wm))),
+                (H.OP_LTINV, lambda x: S.join(schur.sweep_backward(F, S.split(x), W=Wm)))]
+    for op, f in refs:
+        Y = _apply(h, off + op, X)
+        for c in range(0, 64, 8):
+            assert rel(Y[:, c], f(X[:, c])) < tol, (op, c)
+        for c in (5, 40):
             assert np.array_equal(_apply(h, off + op, X[:, c:c + 1])[:, 0], Y[:, c]), (op, c)
 
 

@@ -11,6 +11,7 @@ import torch
 
 import paper_2111_13483_gb300 as hm
 from oracle import krylov, ordering, schur
+from refs import truncated_at
 
 pytestmark = pytest.mark.gpu
 
@@ -232,6 +233,49 @@ def test_compression_ranks_and_blocks_match_oracle(cfg1_compressed):
     assert st["coef_entries"] < st["coef_entries_dense"]
 
 
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_compressed_operators_match_oracle(cfg1_compressed, nrhs):
+    """Compressed fill-in blocks are stored as their factors (U_r Sigma_r, V_r) and applied as
+    two products; the oracle applies the expanded truncations: equal up to rounding.  The
+    store holds exactly the oracle's Table 6 count of coefficient entries."""
+    P, order, F, S, h = cfg1_compressed
+    st = hm.hmat_stats(h)
+    assert st["coef_entries"] == schur.nnz_coefficients(F) - int(np.sum(F.size))
+    rng = np.random.default_rng(17 + nrhs)
+    X = rng.standard_normal((S.n, nrhs)) + 1j * rng.standard_normal((S.n, nrhs))
+    dx = _dev(X)
+    for op, f in ((hm.hmsolve.OP_LINV, S.L_inv), (hm.hmsolve.OP_LTINV, S.LT_inv), (hm.hmsolve.OP_A, S.apply_A)):
+        dy = torch.empty_like(dx)
+        hm.hm_apply(h, op, dx, dy)
+        Y = _host(dy)
+        for c in range(nrhs):
+            assert rel(Y[:, c], f(X[:, c])) < 1e-10, (op, c)
+
+
+def test_compressed_mixed_operators_and_solve(cfg1_compressed, sphere1920):
+    P, order, F, S, h64 = cfg1_compressed
+    h = hm.hmat_create(sphere1920, ordering=1, fill_tol=1e-2, precision=1)
+    hm.precond_setup(h)
+    ranks32 = hm.hmsolve.hm_get_fill_ranks(h)
+    ranks64 = hm.hmsolve.hm_get_fill_ranks(h64)
+    assert np.mean(ranks32 == ranks64) > 0.95
+    Wm = truncated_at(F, h)
+    rng = np.random.default_rng(19)
+    X = rng.standard_normal((S.n, 5)) + 1j * rng.standard_normal((S.n, 5))
+    refs = ((hm.hmsolve.OP_LINV, lambda x: S.join(schur.sweep_forward(F, S.split(x), W=Wm))),
+            (hm.hmsolve.OP_LTINV, lambda x: S.join(schur.sweep_backward(F, S.split(x), W=Wm))))
+    for op, f in refs:
+        dy = torch.empty_like(_dev(X))
+        hm.hm_apply(h, hm.hmsolve.OP32 + op, _dev(X), dy)
+        Y = _host(dy)
+        for c in range(5):
+            assert rel(Y[:, c], f(X[:, c])) < 1e-4, (op, c)
+    b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
+    x, it, rr, code = hm.solve(h, b, tol=1e-5, restart=30)
+    assert code == 0
+    assert np.linalg.norm(b - S.Z_orig(x)) / np.linalg.norm(b) <= 1.01e-5
+
+
 def test_compressed_solve_matches_oracle(cfg1_compressed):
     P, order, F, S, h = cfg1_compressed
     b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
@@ -352,3 +396,29 @@ def test_sloan_ordering_solve_matches_oracle(prec):
         assert code == 0
         assert np.linalg.norm(b - S.Z_orig(x)) / np.linalg.norm(b) <= 1.01e-5
         assert rel(x, xt) <= 1e-4
+
+
+# ---- the complex-FP32 far field: CUDA cores (kind 1) and tensor cores (kind 2) -------------------
+def test_far_schedules_match_oracle(cfg1, cfg1_mixed):
+    P, order, F, S, h64 = cfg1
+    h = cfg1_mixed
+    rng = np.random.default_rng(13)
+    op = hm.hmsolve.OP32 + hm.hmsolve.OP_ZF
+    for nrhs in (1, 5, 64):
+        X = rng.standard_normal((S.n, nrhs)) + 1j * rng.standard_normal((S.n, nrhs))
+        ref = np.stack([S.far_new(X[:, c]) for c in range(nrhs)], axis=1)
+        res = {}
+        for kind in (1, 2):
+            hm.hmsolve.hm_set_far_schedule(h, kind)
+            dy = torch.empty_like(_dev(X))
+            hm.hm_apply(h, op, _dev(X), dy)
+            res[kind] = _host(dy)
+            for c in range(nrhs):          # FP32 factors and arithmetic against the FP64 oracle
+                assert rel(res[kind][:, c], ref[:, c]) < 1e-5, (kind, nrhs, c)
+        if nrhs > 1:                       # a column alone gives the same bits as in the batch
+            for kind in (1, 2):
+                hm.hmsolve.hm_set_far_schedule(h, kind)
+                dy = torch.empty_like(_dev(X[:, :1]))
+                hm.hm_apply(h, op, _dev(X[:, 3:4]), dy)
+                assert np.array_equal(_host(dy)[:, 0], res[kind][:, 3]), kind
+    hm.hmsolve.hm_set_far_schedule(h, 0)
