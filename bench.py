@@ -79,14 +79,19 @@ def parse():
     ap.add_argument("--cpu-anchor-run", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--ordering", type=int, default=1, choices=[0, 1, 2],
                     help="Algorithm 1 reordering: 0 none, 1 reverse Cuthill-McKee, 2 Sloan")
+    ap.add_argument("--table7", action="store_true",
+                    help="Sec. 5.2 Table 7 style comparison on the workload (FP64): Schur complement vs block "
+                         "Jacobi, t_sp, p, t_mm, t_mp and t_total = t_sm + t_sp + p n (t_mm + t_mp) (Eq. 46) for "
+                         "n = --nrhs right-hand sides; prints one JSON line")
     ap.add_argument("--compare-orderings", action="store_true",
                     help="Sec. 3.3 Tables 3-4 style comparison on the workload: setup ms, coefficient entries, "
                          "operator ms and iterations for no ordering, RCM and Sloan; prints one JSON line")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="0: complex FP64; 1: complex-FP32 operator inside FP64 refinement")
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--serve-requests", type=int, default=64,
-                    help="requests of the serving leg (Poisson arrivals at 0.8x the measured RHS/s); 0 = skip")
+    ap.add_argument("--serve-requests", type=int, default=360,
+                    help="requests of the serving leg (monostatic plane waves, phi in 1-degree steps, Poisson "
+                         "arrivals at 0.8x the measured RHS/s: a steady state of about half a minute); 0 = skip")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving on two resident geometries (sphere30720 + plate29800), 360 requests each, "
                          "offered at 0.5/0.8/1.0x the measured throughput")
@@ -324,6 +329,15 @@ def serving_run(hm, serve, h, P, requests, rate, tol, restart, seed_rhs=2, seed_
     s = serve.latency_summary(reqs)
     s.update({"offered_rps": rate, "achieved_rhs_per_s": requests / wall, "wall_s": wall,
               "not_converged": sum(r.status != 0 for r in reqs), "slots": srv.slots("g")})
+    # steady state: the completions between the 10th and the 90th percentile of completion
+    # times (the ramp-up and the drain at the end left out)
+    done = sorted(r.t_done for r in reqs)
+    a, b = done[len(done) // 10], done[(9 * len(done)) // 10]
+    mid = [r for r in reqs if a <= r.t_done <= b]
+    if b > a and len(mid) > 1:
+        st = serve.latency_summary(mid)
+        st.update({"achieved_rhs_per_s": (len(mid) - 1) / (b - a), "window_s": b - a})
+        s["steady"] = st
     del t0
     return s
 
@@ -776,6 +790,72 @@ def run_compare_orderings(args):
     print(json.dumps(out), flush=True)
 
 
+def run_table7(args):
+    """Sec. 5.2, Table 7 on a workload, in the paper's FP64 arithmetic: for the symmetric
+    Schur-complement preconditioner (fill_tol as given) and for block Jacobi (the near-field
+    diagonal blocks), t_sp = precond_setup, p = mean GMRES(restart) iterations over a few
+    right-hand sides of the bench sweep at the preconditioned tolerance --fp64-tol, the per
+    iteration times of the operator's parts from the library's event profiler (one column):
+    t_mm = far field (+ near field for block Jacobi), t_mpp = block solves and products with D,
+    t_mps = scaling-coefficient sweeps (Schur only), and t_total = t_sm + t_sp + p n (t_mm + t_mp)
+    (Eq. 46) for n = --nrhs right-hand sides, with t_sm = the host build of the H-matrix (EFIE
+    fill and ACA, 0 when the builder's cache held it) plus its upload (hmat_create)."""
+    import torch
+    import paper_2111_13483_gb300 as hm
+    t0 = time.perf_counter()
+    P = load_problem(args.workload, 0, 1)
+    t_build = time.perf_counter() - t0
+    plate = args.workload.startswith("plate")
+    V = rhs_batch(P, args.nrhs, plate)
+    cols = [int(c) for c in np.linspace(0, args.nrhs, 4, endpoint=False)]
+    out = {"workload": args.workload, "n": int(P.n), "rhs_n": args.nrhs, "tol_preconditioned": args.fp64_tol,
+           "restart": args.restart, "host_build_s_this_process": t_build, "preconditioners": {}}
+    for name, pc, ft in (("schur", 0, args.fill_tol), ("block_jacobi", 1, 0.0)):
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        h = hm.hmat_create(P, ordering=args.ordering, fill_tol=ft, precision=0, preconditioner=pc)
+        t_sm = time.perf_counter() - c0
+        hm.precond_setup(h)
+        hm.precond_setup(h)
+        t_sp = hm.hmat_stats(h)["setup_ms"] / 1e3
+        its, solve_s, conv = [], [], []
+        for c in cols:
+            s0 = time.perf_counter()
+            I, it, rr, code = hm.solve(h, V[:, c], tol=args.fp64_tol, restart=args.restart, maxit=20000)
+            solve_s.append(time.perf_counter() - s0)
+            its.append(int(it[0]))
+            conv.append(int(code) == 0)
+        x = torch.randn(1, P.n, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            hm.hm_apply(h, hm.hmsolve.OP_A, x, y)
+        hm.hm_profile(h, 2)
+        hm.hm_profile(h, 1)
+        K = 20
+        for _ in range(K):
+            hm.hm_apply(h, hm.hmsolve.OP_A, x, y)
+        torch.cuda.synchronize()
+        pr = hm.hm_get_profile(h)
+        hm.hm_profile(h, 0)
+        ms = {k: v[2] / K for k, v in pr.items() if v[0]}
+        t_mm = (ms.get("far1", 0) + ms.get("far2", 0) + ms.get("permute", 0) + ms.get("near", 0)) / 1e3
+        t_mpp = ms.get("diag", 0) / 1e3
+        t_mps = (ms.get("sweep_fwd", 0) + ms.get("sweep_bwd", 0)) / 1e3
+        p = float(np.mean(its))
+        st = hm.hmat_stats(h)
+        t_sm += t_build      # the host EFIE fill and ACA build (0 when the builder's cache had it)
+        out["preconditioners"][name] = {
+            "t_sm_s": t_sm, "t_sp_s": t_sp, "p": p, "iters": its, "t_mm_s": t_mm, "t_mpp_s": t_mpp,
+            "t_mps_s": t_mps, "t_mp_s": t_mpp + t_mps, "p_times_tmm_plus_tmp_s": p * (t_mm + t_mpp + t_mps),
+            "t_total_s": t_sm + t_sp + p * args.nrhs * (t_mm + t_mpp + t_mps),
+            "measured_solve_s_per_rhs": float(np.mean(solve_s)), "fill_tol": ft, "converged": conv,
+            "coef_entries": st["coef_entries"] if pc == 0 else 0, "device_bytes": st["device_bytes"]}
+        hm.hmat_destroy(h)
+    s, b = out["preconditioners"]["schur"], out["preconditioners"]["block_jacobi"]
+    out["speedup_total_schur_over_block_jacobi"] = b["t_total_s"] / s["t_total_s"]
+    print(json.dumps(out), flush=True)
+
+
 def run_profile_op(args):
     """A short, deterministic case for ncu captures (no timing of its own)."""
     import torch
@@ -805,6 +885,9 @@ def main():
         return
     if args.compare_orderings:
         run_compare_orderings(args)
+        return
+    if args.table7:
+        run_table7(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -89,7 +89,17 @@ typedef struct {
  *              inside an FP64 refinement loop on Z (FP64 pivots, Arnoldi, residual);
  *   device     CUDA device ordinal;
  *   hbm_budget bytes the handle may allocate on the device, 0 = no limit;
- *   stream     cudaStream_t to order work on, NULL = the library creates one.
+ *   stream     cudaStream_t to order work on, NULL = the library creates one;
+ *   preconditioner  0 = the symmetric near-field Schur complement (Sec. 3, Eq. 28);
+ *              1 = block Jacobi, M = the near-field diagonal blocks Z_kk (the block diagonal
+ *              preconditioner of Sec. 1, a comparison): GMRES on M^{-1} Z x = M^{-1} b with
+ *              the same engine, no coefficients, blocks in the ordering's order; precision 0
+ *              only (HM_EINVAL otherwise);
+ *   compress_in_setup  with fill_tol > 0: 0 = the fill-in coefficient blocks are truncated once
+ *              the elimination is complete and only the sweeps use the truncations; 1 = each is
+ *              truncated as soon as its elimination step forms it, so that the Schur updates of
+ *              that step (and every later block) use it (the abstract's "compressing the fill-in
+ *              blocks in preconditioner computation"; Sec. 3.4 is silent on the point).
  */
 typedef struct {
     int32_t ordering;
@@ -98,6 +108,8 @@ typedef struct {
     int32_t device;
     size_t hbm_budget;
     void *stream;
+    int32_t preconditioner;
+    int32_t compress_in_setup;
 } hm_opts;
 
 typedef struct {
@@ -114,7 +126,7 @@ typedef struct {
     size_t device_bytes;      /* bytes currently allocated on the device by the handle */
 } hm_stats;
 
-/* Fills *o with the defaults: RCM, fill_tol 0, FP64, device 0, no budget, own stream. */
+/* Fills *o with the defaults: RCM, fill_tol 0, FP64, device 0, no budget, own stream, Schur. */
 int hm_default_opts(hm_opts *o);
 
 /*
@@ -285,7 +297,9 @@ int hm_tc_cgemm(int32_t m, int32_t k, int32_t ncols, const void *dA, int64_t lda
 /*
  * How the complex-FP32 far-field product (Z_F u of Sec. 2, Eq. 11, inside the operator of a
  * precision 1 handle) computes its block products: kind 1 = register-tiled FMAs on the CUDA
- * cores, kind 2 = the tensor-core micro-kernel of hm_tc_cgemm; 0 = the default (2).  Both
+ * cores, kind 2 = the tensor-core micro-kernel of hm_tc_cgemm; 0 = the default (1: at 64
+ * columns on the 30,720-unknown sphere kind 2 took 3.22 against 3.47 ms, at one column 2.07
+ * against 0.80 ms, and the choice must not depend on the width).  Both
  * sum every output's terms in a fixed order, each its own; the FP64 far field always runs on
  * the CUDA cores.  HM_EINVAL for other values.
  */

@@ -125,6 +125,53 @@ class System:
         return self.to_orig(self.LT_inv(xt))
 
 
+class _Blocks:
+    """Order and sizes of the leaf blocks (what System needs of a factor)."""
+
+    def __init__(self, prob, order):
+        self.order = np.asarray(order)
+        self.size = np.array([prob.leaf_ptr[t + 1] - prob.leaf_ptr[t] for t in self.order], dtype=np.int64)
+        self.nb = len(self.order)
+
+
+class BlockJacobi(System):
+    """The block-diagonal preconditioner of the near-field diagonal blocks, M = diag(Z_kk),
+    the low-setup-cost comparison the paper names in Sec. 1 beside the null-field scaling:
+    GMRES on M^{-1} Z x = M^{-1} b (left preconditioned, the same GMRES as for Eq. 28), with
+    the blocks in the given leaf order and no transformation (x~ = x).  Z x is the H-matrix
+    product: near blocks as stored plus the far factors."""
+
+    def __init__(self, prob, order):
+        F = _Blocks(prob, order)
+        super().__init__(prob, F)
+        lp = prob.leaf_ptr
+        self.M = []
+        for t in F.order:
+            b = int(np.nonzero((prob.near_t == t) & (prob.near_s == t))[0][0])
+            m = lp[t + 1] - lp[t]
+            blk = prob.near_data[prob.near_off[b]:prob.near_off[b] + m * m].reshape(m, m).T
+            self.M.append(blk.copy())
+        self.lu = [sla.lu_factor(B) for B in self.M]
+
+    def M_solve(self, x):
+        v = self.split(x)
+        return self.join([sla.lu_solve(self.lu[k], v[k]) for k in range(self.F.nb)])
+
+    def Z_new(self, x):
+        u = np.zeros(x.shape, dtype=np.complex128)
+        u[self.new2cl] = x
+        return (self.near_cluster(u) + self.far_cluster(u))[self.new2cl]
+
+    def apply_A(self, x):
+        return self.M_solve(self.Z_new(x))
+
+    def rhs(self, b_orig):
+        return self.M_solve(self.to_new(b_orig))
+
+    def solution(self, xt):
+        return self.to_orig(xt)
+
+
 def givens(a, b):
     """(c, s, rho) with [c s; -conj(s) c] [a; b] = [rho; 0], c real."""
     if a == 0:

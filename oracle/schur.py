@@ -67,10 +67,17 @@ def near_blocks_in_order(prob, order):
     return A
 
 
-def setup(prob, order, fill_tol=1e-2, max_steps=None):
+def setup(prob, order, fill_tol=1e-2, max_steps=None, compress_in_setup=False):
     """The preconditioner of Sec. 3 for block order ``order`` (Algorithm 1 output).
     ``max_steps`` stops after that many elimination steps (a timing sample; the factor is
-    then incomplete and only its first steps are valid)."""
+    then incomplete and only its first steps are valid).
+
+    Fill-in compression (Sec. 3.4) has two readings.  Default (after the factorisation):
+    every fill-in coefficient block is truncated once the elimination is complete, and only
+    the sweeps use the truncations.  ``compress_in_setup`` (the abstract's "compressing the
+    fill-in blocks in preconditioner computation"): at elimination step k the fill-in blocks
+    W_kj of the new panel are truncated as soon as they are formed, and the Schur updates of
+    that step (and so every later pivot block and panel) use the truncations."""
     nb = len(order)
     size = np.array([prob.leaf_ptr[order[p] + 1] - prob.leaf_ptr[order[p]] for p in range(nb)], dtype=np.int64)
     A = near_blocks_in_order(prob, order)
@@ -88,6 +95,10 @@ def setup(prob, order, fill_tol=1e-2, max_steps=None):
         F.D.append(Dk)
         F.lu.append(lu)
         Wk = {j: sla.lu_solve(lu, A[(j, k)].T) for j in S[k]}      # W_kj = D_k^{-1} A_kj
+        if compress_in_setup and fill_tol > 0:
+            for j in S[k]:
+                if (j, k) not in near_pairs:
+                    Wk[j] = compress_block(Wk[j], fill_tol)[0]
         for ii, i in enumerate(S[k]):
             Aik = A[(i, k)]
             for j in S[k][:ii + 1]:                                 # i >= j

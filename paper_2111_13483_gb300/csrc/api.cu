@@ -153,7 +153,9 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
     else hm_default_opts(&h->opts);
     int st;
     if (h->opts.ordering < 0 || h->opts.ordering > 2 || h->opts.fill_tol < 0 || h->opts.precision < 0 ||
-        h->opts.precision > 1) {
+        h->opts.precision > 1 || h->opts.preconditioner < 0 || h->opts.preconditioner > 1 ||
+        h->opts.compress_in_setup < 0 || h->opts.compress_in_setup > 1 ||
+        (h->opts.preconditioner == 1 && h->opts.precision != 0)) {
         delete h;
         return HM_EINVAL;
     }
@@ -254,6 +256,32 @@ int precond_setup(hm_handle h)
     Plan &P = h->plan;
     cudaError_t e;
     const bool mixed = h->opts.precision == 1;
+    if (h->opts.preconditioner == 1) {   // block Jacobi: D_k = Z_kk and its inverse only
+        if (!h->d_Dinv && ((e = h->arena.alloc((void **)&h->d_Dinv, sizeof(double2) * P.diag_entries)) ||
+                           (e = h->arena.alloc((void **)&h->d_Ad, sizeof(double2) * P.diag_entries))))
+            return cuda_fail(h, e, "precond_setup allocation");
+        cudaEvent_t b0, b1;
+        cudaEventCreate(&b0);
+        cudaEventCreate(&b1);
+        cudaEventRecord(b0, h->stream);
+        int bad = -1;
+        e = block_jacobi_setup(h, &bad);
+        cudaEventRecord(b1, h->stream);
+        cudaEventSynchronize(b1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, b0, b1);
+        cudaEventDestroy(b0);
+        cudaEventDestroy(b1);
+        if (e) return cuda_fail(h, e, "precond_setup");
+        if (bad >= 0) {
+            h->err = "diagonal block " + std::to_string(bad) + " (solve order; leaf " + std::to_string(P.order[bad]) +
+                     ") is numerically singular";
+            return HM_ESINGULAR;
+        }
+        h->setup_ms = ms;
+        h->setup_done = true;
+        return HM_OK;
+    }
     if (!h->d_Dinv) {   // factors: FP64, or FP32 (with D_k^{-1} in both) for the mixed setup
         if ((e = h->arena.alloc((void **)&h->d_Dinv, sizeof(double2) * P.diag_entries)) ||
             (mixed ? ((e = h->arena.alloc((void **)&h->d_W32, sizeof(float2) * P.coef_entries)) ||
@@ -432,6 +460,10 @@ int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out)
     }
     const Plan &P = h->plan;
     if (k < 0 || k >= P.nb || what < 0 || what > 3) return HM_EINVAL;
+    if (h->opts.preconditioner == 1 && what >= 2) {
+        h->err = "hm_get_block: the block-Jacobi preconditioner has no coefficient blocks";
+        return HM_ESTATE;
+    }
     cudaSetDevice(h->dev);
     const bool mixed = h->opts.precision == 1;
     const void *src;
@@ -531,7 +563,7 @@ int hm_test_hold(hm_handle h, int32_t block, int64_t wait_ns)
 int hm_set_far_schedule(hm_handle h, int32_t kind)
 {
     if (!h || kind < 0 || kind > 2) return HM_EINVAL;
-    h->far_kind = kind == 0 ? 2 : kind;
+    h->far_kind = kind == 0 ? 1 : kind;
     return HM_OK;
 }
 

@@ -42,7 +42,7 @@ __device__ __forceinline__ float2 conjd(float2 a) { return make_float2(a.x, -a.y
 template <class TC>
 __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, const int *fill_k, const int *size,
                                                   const int *sidx, const int *srow, const int64_t *coff, TC *W,
-                                                  double tol, int *rank_out)
+                                                  double tol, int *rank_out, bool expand = false)
 {
     typedef typename Real<TC>::type R;
     extern __shared__ unsigned char smraw[];
@@ -178,7 +178,18 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
     }
     __syncthreads();
     const int r = s_rank;
-    if (r >= 0) {
+    if (r >= 0 && expand) {   // the truncation itself, in place (used by the later Schur updates)
+        for (int x = threadIdx.x; x < m * n; x += blockDim.x) {
+            const int row = x % m, c = x / m;
+            TC acc = czero(TC());
+            for (int l = 0; l < r; ++l) {
+                const int o = ord[l];
+                acc = tr ? cfma(V[o * 64 + row], conjd(A[o * 64 + c]), acc)
+                         : cfma(A[o * 64 + row], conjd(V[o * 64 + c]), acc);
+            }
+            Wb[x] = acc;
+        }
+    } else if (r >= 0) {
         // W ~ sum over the r largest of a_o conj(v_o)^T (W = A V^H), or of v_o conj(a_o)^T in the
         // transposed case (W = (A V^H)^H = V A^H): P(:, l) and Q(:, l) from the l-th largest
         TC *Pb = Wb, *Qb = Wb + (int64_t)m * r;
@@ -268,6 +279,30 @@ cudaError_t pack_run(hm_ctx *h)
     if ((e = cudaGetLastError())) return e;
     return cudaStreamSynchronize(h->stream);
 }
+
+// Compression during the setup: the fill-in blocks of panel k truncated in place, before the
+// Schur updates of step k read them (hm_opts.compress_in_setup).
+template <class TC> cudaError_t compress_step(hm_ctx *h, int k, TC *W)
+{
+    const Plan &P = h->plan;
+    const int f0 = P.fill_ptr[k], nf = P.fill_ptr[k + 1] - f0;
+    if (nf == 0 || !(h->opts.fill_tol > 0)) return cudaSuccess;
+    cudaError_t e;
+    if (!h->d_fill_rank && (e = h->arena.alloc((void **)&h->d_fill_rank, sizeof(int) * P.fill_e.size()))) return e;
+    const size_t smem = sizeof(TC) * 2 * 64 * 64;
+    static bool attr = false;
+    if (!attr) {
+        if ((e = cudaFuncSetAttribute(k_compress<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        attr = true;
+    }
+    HM_LAUNCH(h, K_COMPRESS,
+              k_compress<TC><<<nf, 256, smem, h->stream>>>(nf, h->d_fill_e + f0, h->d_fill_k + f0, h->d_size, h->d_sidx,
+                                                           h->d_srow, h->d_coff, W, h->opts.fill_tol,
+                                                           h->d_fill_rank + f0, true));
+    return cudaGetLastError();
+}
+template cudaError_t compress_step<double2>(hm_ctx *, int, double2 *);
+template cudaError_t compress_step<float2>(hm_ctx *, int, float2 *);
 
 cudaError_t compress_run(hm_ctx *h)
 {

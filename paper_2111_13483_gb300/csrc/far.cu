@@ -205,15 +205,16 @@ __global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, cons
 // ---- complex FP32 on the tensor cores ------------------------------------------------------
 // The same two phases with the block products on the tensor-core micro-kernel of tc.cuh
 // (TF32 operands split into a rounded part and a remainder, FP32 accumulation in tensor
-// memory), contraction chunks of tc::KC: the coefficient rows of the next chunk are copied
-// with cp.async into the other raw buffer while the current chunk's vector rows are loaded into
-// registers; once the previous chunk's MMAs have finished both are split into the operand
-// planes and thread 0 issues the chunk's MMAs.  Fixed chunk order, so every output sums its
-// terms in one order whatever the number of right-hand sides.
-constexpr int FTC_LD = 64;                          // raw coefficients: raw[kk * FTC_LD + row]
-constexpr int FTC_RAW = tc::KC * FTC_LD * 8;         // bytes of one raw buffer
+// memory), streamed in chunks of tc::KC2 contraction entries through a three-deep pipeline:
+// the raw coefficient and vector entries of chunk c+1 are copied with cp.async while chunk c is
+// split into one stage of operand planes and the MMAs of chunk c-1 run on the other stage.
+// Fixed chunk order, so every output sums its terms in one order whatever the number of
+// right-hand sides.
+constexpr int FTC_LD = 64;                                   // raw[kk * FTC_LD + row or column]
+constexpr int FTC_RAW = tc::KC2 * FTC_LD * 8;                // one raw buffer (8 KB)
+constexpr int FTC_REGION = 2 * tc::STAGE2 + 4 * FTC_RAW;     // planes, then raw A and B x 2
 constexpr unsigned long long FTC_WAIT_NS = 2000000000ull;
-constexpr size_t FTC_SMEM = tc::REGION_BYTES + 2 * FTC_RAW + 1024;
+constexpr size_t FTC_SMEM = (FTC_REGION > tc::REGION_BYTES ? FTC_REGION : tc::REGION_BYTES) + 1024;
 
 // Phase 1: task -> up to 64 factor columns (rows of the product) contracted over [lo, hi)
 __global__ void __launch_bounds__(256, 2) k_far_t_tc(const int *task_lo, const int *task_hi, const int *task_ptr,
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(256, 2) k_far_t_tc(const int *task_lo, const i
     __shared__ int s_item[64], s_l[64];
     __shared__ const float2 *s_src[64];
     __shared__ int s_R;
-    __shared__ uint64_t s_mbar;
+    __shared__ uint64_t s_mbar[2];
     __shared__ uint32_t s_tmem;
     const int task = blockIdx.x;
     const int lo = task_lo[task], hi = task_hi[task], i0 = task_ptr[task], i1 = task_ptr[task + 1];
@@ -244,48 +245,48 @@ __global__ void __launch_bounds__(256, 2) k_far_t_tc(const int *task_lo, const i
     const int R = s_R;
     if (R == 0) return;
     unsigned char *region = tc::align1024(smraw);
-    float2 *raw[2] = {(float2 *)(region + tc::REGION_BYTES), (float2 *)(region + tc::REGION_BYTES + FTC_RAW)};
-    tc::Acc acc;
+    float2 *rawA = (float2 *)(region + 2 * tc::STAGE2), *rawB = rawA + 2 * tc::KC2 * FTC_LD;
+    tc::Acc2 acc;
     acc.planes = region;
-    acc.mbar = &s_mbar;
+    acc.mbar = s_mbar;
     acc.tslot = &s_tmem;
     acc.open(R, nrhs);
-    auto prefetch = [&](int c0, int buf) {
-        const int kl = min(tc::KC, hi - c0);
+    const int nch = (hi - lo + tc::KC2 - 1) / tc::KC2;
+    auto fetch = [&](int c) {   // raw entries of chunk c into raw buffer c & 1
+        const int c0 = lo + c * tc::KC2, kl = min(tc::KC2, hi - c0), b = c & 1;
+        float2 *ra = rawA + b * tc::KC2 * FTC_LD, *rb = rawB + b * tc::KC2 * FTC_LD;
         for (int e = threadIdx.x; e < kl * R; e += blockDim.x) {
             const int kk = e % kl, rr = e / kl;
-            cp_async_el(raw[buf] + kk * FTC_LD + rr, s_src[rr] + (c0 - lo + kk));
+            cp_async_el(ra + kk * FTC_LD + rr, s_src[rr] + (c0 - lo + kk));
         }
+        const float2 *uc = u + (int64_t)c0 * nrhs;
+        for (int e = threadIdx.x; e < kl * nrhs; e += blockDim.x) cp_async_el(rb + (e / nrhs) * FTC_LD + e % nrhs, uc + e);
         cp_async_commit();
     };
-    if (lo < hi) prefetch(lo, 0);
-    for (int c0 = lo, it = 0; c0 < hi; c0 += tc::KC, ++it) {
-        const int kl = min(tc::KC, hi - c0), cnt = kl * nrhs;
-        float2 v[8];
-        const float2 *uc = u + (int64_t)c0 * nrhs;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = threadIdx.x + q * blockDim.x;
-            if (e < cnt) v[q] = uc[e];
-        }
-        cp_async_wait<0>();
-        __syncthreads();
-        if (c0 + tc::KC < hi) prefetch(c0 + tc::KC, (it + 1) & 1);
-        acc.wait(err, FTC_WAIT_NS);
-        const float2 *rw = raw[it & 1];
+    if (nch > 0) fetch(0);
+    for (int c = 0; c < nch; ++c) {
+        const int st = c & 1, kl = min(tc::KC2, hi - (lo + c * tc::KC2));
+        if (c + 1 < nch) {
+            fetch(c + 1);
+            cp_async_wait<1>();
+        } else
+            cp_async_wait<0>();
+        __syncthreads();                       // chunk c's raw entries are visible
+        acc.wait(st, err, FTC_WAIT_NS);        // the MMAs of chunk c - 2 have left stage st
+        const float2 *ra = rawA + st * tc::KC2 * FTC_LD, *rb = rawB + st * tc::KC2 * FTC_LD;
         for (int e = threadIdx.x; e < acc.m8 * kl; e += blockDim.x) {
             const int r = e % acc.m8, kk = e / acc.m8;
-            acc.put_a(r, kk, r < R ? rw[kk * FTC_LD + r] : make_float2(0.f, 0.f));
+            acc.put_a(st, r, kk, r < R ? ra[kk * FTC_LD + r] : make_float2(0.f, 0.f));
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = threadIdx.x + q * blockDim.x;
-            if (e < cnt) acc.put_b(e % nrhs, e / nrhs, v[q]);
+        for (int e = threadIdx.x; e < acc.p * kl; e += blockDim.x) {
+            const int col = e % acc.p, kk = e / acc.p;
+            acc.put_b(st, col, kk, col < nrhs ? rb[kk * FTC_LD + col] : make_float2(0.f, 0.f));
         }
-        acc.zero_pad(kl);
-        acc.issue(kl);
+        acc.zero_pad(st, kl);
+        acc.issue(st, kl);
     }
-    acc.wait(err, FTC_WAIT_NS);
+    acc.wait(0, err, FTC_WAIT_NS);
+    acc.wait(1, err, FTC_WAIT_NS);
     float *dsm = (float *)region;
     const bool any = acc.drain(dsm);
     for (int e = threadIdx.x; e < R * nrhs; e += blockDim.x) {
@@ -296,40 +297,45 @@ __global__ void __launch_bounds__(256, 2) k_far_t_tc(const int *task_lo, const i
     acc.close();
 }
 
-// Phase 2: CTA = (leaf, part); chunks of whole segments up to tc::KC entries
+// Phase 2: CTA = (leaf, part); the part's segments streamed in chunks of tc::KC2 entries (a
+// segment may be split between chunks)
 struct FarTcChunk {
-    const float2 *f[tc::KC];   // coefficient entry kk of row i: f[kk][i * fi[kk]]
-    int fi[tc::KC];
-    const float2 *y[tc::KC];   // vector entry kk of column r: y[kk][r]
-    int kl, next;
+    const float2 *f[tc::KC2];   // coefficient entry kk of row i: f[kk][i * fi[kk]]
+    int fi[tc::KC2];
+    const float2 *y[tc::KC2];   // vector entry kk of column r: y[kk][r]
+    int kl;
 };
 
-// warp 0: the chunk of segments starting at p (those whose stacked length fits tc::KC)
-__device__ __forceinline__ void far_tc_chunk(int p, int w1, const int *kcum, const FarSegD *segs, const float2 *U,
+struct FarTcWalk {
+    int q, koff;   // next segment and its first entry not yet taken
+};
+
+// thread 0: the next chunk of the part's segments [w.q, w1)
+__device__ __forceinline__ void far_tc_chunk(FarTcWalk &w, int w1, const FarSegD *segs, const float2 *U,
                                              const float2 *V, const float2 *t, const float2 *s, const float2 *u,
                                              int nrhs, FarTcChunk &c)
 {
-    const int lane = threadIdx.x & 31, q = p + lane;
-    const int k0 = p < w1 ? kcum[p] : 0;
-    const bool fit = p < w1 && q < w1 && kcum[q + 1] - k0 <= tc::KC;
-    const unsigned m = __ballot_sync(0xffffffffu, fit);
-    const int cnt = __popc(m);
-    if (fit) {
-        const FarSegD g = segs[q];
-        const int kb = kcum[q] - k0;
+    int kl = 0;
+    while (w.q < w1 && kl < tc::KC2) {
+        const FarSegD g = segs[w.q];
         const float2 *F = ((g.src & 1) ? V : U) + g.foff;
         const int ys = g.src >> 1;
         const float2 *Yb = (ys == 0 ? t : (ys == 1 ? s : u)) + g.yrow * nrhs;
-        for (int k = 0; k < g.len; ++k) {
-            c.f[kb + k] = F + (int64_t)k * g.fk;
-            c.fi[kb + k] = g.fi;
-            c.y[kb + k] = Yb + (int64_t)k * nrhs;
+        const int take = min(g.len - w.koff, tc::KC2 - kl);
+        for (int k = 0; k < take; ++k) {
+            const int kk = w.koff + k;
+            c.f[kl + k] = F + (int64_t)kk * g.fk;
+            c.fi[kl + k] = g.fi;
+            c.y[kl + k] = Yb + (int64_t)kk * nrhs;
+        }
+        kl += take;
+        w.koff += take;
+        if (w.koff == g.len) {
+            ++w.q;
+            w.koff = 0;
         }
     }
-    if (lane == 0) {
-        c.kl = cnt > 0 ? kcum[p + cnt] - k0 : 0;
-        c.next = p + cnt;
-    }
+    c.kl = kl;
 }
 
 __global__ void __launch_bounds__(256, 2) k_far_y_tc(int nl, const int *leaf_ptr, const int *part_ptr,
@@ -339,8 +345,8 @@ __global__ void __launch_bounds__(256, 2) k_far_y_tc(int nl, const int *leaf_ptr
                                                      float2 *part, int *err)
 {
     extern __shared__ unsigned char smraw[];
-    __shared__ FarTcChunk s_ch[2];
-    __shared__ uint64_t s_mbar;
+    __shared__ FarTcChunk s_ch[3];
+    __shared__ uint64_t s_mbar[2];
     __shared__ uint32_t s_tmem;
     const int l = blockIdx.x / FAR_PARTS, pp = blockIdx.x % FAR_PARTS;
     if (l >= nl) return;
@@ -352,50 +358,57 @@ __global__ void __launch_bounds__(256, 2) k_far_y_tc(int nl, const int *leaf_ptr
         return;
     }
     unsigned char *region = tc::align1024(smraw);
-    float2 *raw[2] = {(float2 *)(region + tc::REGION_BYTES), (float2 *)(region + tc::REGION_BYTES + FTC_RAW)};
-    tc::Acc acc;
+    float2 *rawA = (float2 *)(region + 2 * tc::STAGE2), *rawB = rawA + 2 * tc::KC2 * FTC_LD;
+    tc::Acc2 acc;
     acc.planes = region;
-    acc.mbar = &s_mbar;
+    acc.mbar = s_mbar;
     acc.tslot = &s_tmem;
-    if (threadIdx.x < 32) far_tc_chunk(p0, w1, kcum, segs, U, V, t, s, u, nrhs, s_ch[0]);
-    acc.open(ni, nrhs);   // synchronises: s_ch[0] is visible
-    auto prefetch = [&](int buf) {
-        const FarTcChunk &c = s_ch[buf];
-        for (int e = threadIdx.x; e < c.kl * ni; e += blockDim.x) {
+    FarTcWalk w{p0, 0};
+    if (threadIdx.x == 0) {
+        far_tc_chunk(w, w1, segs, U, V, t, s, u, nrhs, s_ch[0]);
+        far_tc_chunk(w, w1, segs, U, V, t, s, u, nrhs, s_ch[1]);
+    }
+    acc.open(ni, nrhs);   // synchronises: s_ch[0], s_ch[1] are visible
+    (void)kcum;
+    auto fetch = [&](int c) {
+        const FarTcChunk &ch = s_ch[c % 3];
+        const int b = c & 1;
+        float2 *ra = rawA + b * tc::KC2 * FTC_LD, *rb = rawB + b * tc::KC2 * FTC_LD;
+        for (int e = threadIdx.x; e < ch.kl * ni; e += blockDim.x) {
             const int i = e % ni, kk = e / ni;
-            cp_async_el(raw[buf] + kk * FTC_LD + i, c.f[kk] + (int64_t)i * c.fi[kk]);
+            cp_async_el(ra + kk * FTC_LD + i, ch.f[kk] + (int64_t)i * ch.fi[kk]);
         }
+        for (int e = threadIdx.x; e < ch.kl * nrhs; e += blockDim.x)
+            cp_async_el(rb + (e / nrhs) * FTC_LD + e % nrhs, ch.y[e / nrhs] + e % nrhs);
         cp_async_commit();
     };
-    prefetch(0);
-    for (int cur = 0; s_ch[cur].kl > 0; cur ^= 1) {
-        const FarTcChunk &c = s_ch[cur];
-        const int kl = c.kl, cnt = kl * nrhs;
-        if (threadIdx.x < 32) far_tc_chunk(c.next, w1, kcum, segs, U, V, t, s, u, nrhs, s_ch[cur ^ 1]);
-        float2 v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = threadIdx.x + q * blockDim.x;
-            if (e < cnt) v[q] = c.y[e / nrhs][e % nrhs];
-        }
-        cp_async_wait<0>();
-        __syncthreads();   // raw[cur] landed everywhere; s_ch[cur ^ 1] written
-        if (s_ch[cur ^ 1].kl > 0) prefetch(cur ^ 1);
-        acc.wait(err, FTC_WAIT_NS);
-        const float2 *rw = raw[cur];
+    fetch(0);
+    for (int c = 0; s_ch[c % 3].kl > 0; ++c) {
+        const int st = c & 1, kl = s_ch[c % 3].kl;
+        const bool more = s_ch[(c + 1) % 3].kl > 0;
+        if (more) {
+            fetch(c + 1);
+            cp_async_wait<1>();
+        } else
+            cp_async_wait<0>();
+        __syncthreads();                       // chunk c's raw entries are visible
+        // thread 0: the sources of chunk c + 2 (its buffer held chunk c - 1, no longer read)
+        if (threadIdx.x == 0) far_tc_chunk(w, w1, segs, U, V, t, s, u, nrhs, s_ch[(c + 2) % 3]);
+        acc.wait(st, err, FTC_WAIT_NS);        // the MMAs of chunk c - 2 have left stage st
+        const float2 *ra = rawA + st * tc::KC2 * FTC_LD, *rb = rawB + st * tc::KC2 * FTC_LD;
         for (int e = threadIdx.x; e < acc.m8 * kl; e += blockDim.x) {
             const int r = e % acc.m8, kk = e / acc.m8;
-            acc.put_a(r, kk, r < ni ? rw[kk * FTC_LD + r] : make_float2(0.f, 0.f));
+            acc.put_a(st, r, kk, r < ni ? ra[kk * FTC_LD + r] : make_float2(0.f, 0.f));
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = threadIdx.x + q * blockDim.x;
-            if (e < cnt) acc.put_b(e % nrhs, e / nrhs, v[q]);
+        for (int e = threadIdx.x; e < acc.p * kl; e += blockDim.x) {
+            const int col = e % acc.p, kk = e / acc.p;
+            acc.put_b(st, col, kk, col < nrhs ? rb[kk * FTC_LD + col] : make_float2(0.f, 0.f));
         }
-        acc.zero_pad(kl);
-        acc.issue(kl);
+        acc.zero_pad(st, kl);
+        acc.issue(st, kl);                     // barrier inside: s_ch[(c + 2) % 3] is visible after it
     }
-    acc.wait(err, FTC_WAIT_NS);
+    acc.wait(0, err, FTC_WAIT_NS);
+    acc.wait(1, err, FTC_WAIT_NS);
     float *dsm = (float *)region;
     const bool any = acc.drain(dsm);
     for (int e = threadIdx.x; e < ni * nrhs; e += blockDim.x) {

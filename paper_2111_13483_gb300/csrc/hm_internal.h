@@ -78,6 +78,7 @@ struct Plan {
     // fill-in blocks (Sec. 3.4): entries e of sidx whose pair (k, S_k[e]) is not a near pair
     std::vector<int> fill_e;     // entry index into sidx
     std::vector<int> fill_k;     // its block row k
+    std::vector<int> fill_ptr;   // row k's fill-in blocks are fill_e[fill_ptr[k] .. fill_ptr[k+1])
     // super-rows of SWEEP_SR consecutive blocks in sweep order (index 0 forward, 1 backward):
     // xptr/xdep = the union of the members' dependency blocks outside the super-row, in the
     // order the sweep adds them; xoff[e * SWEEP_SR + s] = column of member s's coefficient
@@ -226,7 +227,7 @@ struct hm_ctx {
     bool batch_open = false;   // an hm_batch holds this handle
     hm::SweepTune sweep_tune[2][2][5];   // [FP32][forward][width class]
     int sweep_fixed = 0;                 // a schedule code set by hm_set_sweep_schedule, 0 = tuned
-    int far_kind = 2;                    // complex-FP32 far field: 1 CUDA cores, 2 tensor cores
+    int far_kind = 1;                    // complex-FP32 far field: 1 CUDA cores, 2 tensor cores
 };
 
 // Launch wrapper: counts every launch by kernel class and, when profiling is on, brackets
@@ -256,8 +257,10 @@ void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &p
 
 // kernels (setup.cu / solve.cu): return cudaError_t of the launches
 cudaError_t setup_run(hm_ctx *h, int *bad_block);
+cudaError_t block_jacobi_setup(hm_ctx *h, int *bad_block);
 cudaError_t compress_run(hm_ctx *h);
 cudaError_t pack_run(hm_ctx *h);
+template <class TC> cudaError_t compress_step(hm_ctx *h, int k, TC *W);
 cudaError_t op_apply(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
 cudaError_t op_apply32(hm_ctx *h, int op, const double2 *x, double2 *y, int nrhs);
 cudaError_t make_fp32_copies(hm_ctx *h);

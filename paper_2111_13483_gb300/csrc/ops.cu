@@ -1468,6 +1468,23 @@ static cudaError_t op_chain(hm_ctx *h, const OpData<T> &d, int op, const T *x, T
     const int n = h->plan.n;
     T *w0 = d.work, *w1 = d.work + (size_t)n * nrhs, *w2 = d.work + (size_t)2 * n * nrhs;
     cudaError_t e;
+    if constexpr (sizeof(T) == 16) {
+        if (h->opts.preconditioner == 1) {   // block Jacobi: no coefficients, L = I
+            switch (op) {
+            case 0:   // A x = D^{-1} (Z_N + Z_F) x, D = diag(Z_kk)
+                if ((e = far_apply<T>(h, d, x, w1, nrhs, w2))) return e;   // w2: cluster-order copy of x
+                HM_LAUNCH(h, K_NEAR,
+                          k_near_mv<<<h->nl, 128, 0, h->stream>>>(h->nl, h->d_leaf_ptr, h->d_nptr, h->d_nent,
+                                                                  h->d_near_t, h->d_near_s, h->d_near_off, h->d_near,
+                                                                  w2, h->d_cl2new, n, nrhs, w1));
+                return diag<T>(h, d, 1, w1, (const T *)nullptr, y, nrhs);
+            case 1:
+            case 2:
+                return cudaMemcpyAsync(y, x, sizeof(T) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, h->stream);
+            default: break;
+            }
+        }
+    }
     switch (op) {
     case 0:   // A x = D^{-1} [D x + L^{-1} Z_F L^{-T} x]
         if ((e = sweep<T>(h, d, false, x, w0, nrhs))) return e;

@@ -452,12 +452,15 @@ void plan_order(hm_ctx *h)
         std::sort(nk.begin(), nk.end());
         P.fill_e.clear();
         P.fill_k.clear();
-        for (int k = 0; k < nl; ++k)
+        P.fill_ptr.assign(nl + 1, 0);
+        for (int k = 0; k < nl; ++k) {
             for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e)
                 if (!std::binary_search(nk.begin(), nk.end(), (int64_t)P.sidx[e] * nl + k)) {
                     P.fill_e.push_back(e);
                     P.fill_k.push_back(k);
                 }
+            P.fill_ptr[k + 1] = (int)P.fill_e.size();
+        }
     }
     // layouts
     P.srow.resize(P.sidx.size());

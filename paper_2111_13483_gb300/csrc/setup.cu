@@ -44,11 +44,12 @@ template <class S>
 __global__ void k_scatter_near(int n_near, const int *near_t, const int *near_s, const int64_t *near_off,
                                const double2 *near, const int *leaf_ptr, const int *pos, const int *sptr,
                                const int *sidx, const int *srow, const int *M, const int64_t *coff,
-                               const int64_t *doff, S *A, S *Ad, int *err)
+                               const int64_t *doff, S *A, S *Ad, int *err, bool diag_only = false)
 {
     int b = blockIdx.x;
     if (b >= n_near) return;
     int t = near_t[b], s = near_s[b];
+    if (diag_only && t != s) return;
     int m = leaf_ptr[t + 1] - leaf_ptr[t], n = leaf_ptr[s + 1] - leaf_ptr[s];
     const double2 *B = near + near_off[b];
     int i = pos[t], j = pos[s];
@@ -87,9 +88,10 @@ __global__ void k_scatter_near(int n_near, const int *near_t, const int *near_s,
 // the pivot's row; one pass eliminates (four fused multiply-adds per entry) and writes the
 // new row c.
 template <class S>
-__global__ void __launch_bounds__(256) k_pivot_inverse(int k, const int *size, const int64_t *doff, const S *Ad,
+__global__ void __launch_bounds__(256) k_pivot_inverse(int kbase, const int *size, const int64_t *doff, const S *Ad,
                                                        double2 *Dinv, float2 *Dinv32, int *err)
 {
+    const int k = kbase + blockIdx.x;   // one block per CTA (block Jacobi inverts all at once)
     extern __shared__ double2 sm[];
     const int n = size[k];
     const int ld = n + 1;                      // padded
@@ -488,6 +490,7 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
             HM_LAUNCH(h, K_PANEL,
                       k_panel<S><<<(Mk + 63) / 64, 256, panel_smem, st>>>(k, h->d_size, h->d_M, h->d_coff, h->d_doff,
                                                                           DinvS, A, W));
+            if (h->opts.compress_in_setup && (e = compress_step<S>(h, k, W))) return e;
             if constexpr (sizeof(S) == 8) {
                 const int gb = upd_group(ns, nsm);
                 HM_LAUNCH(h, K_UPDATE,
@@ -509,6 +512,35 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
     if ((e = cudaStreamSynchronize(st))) return e;
     if (herr == 0x7fffffff) return cudaErrorInvalidValue;   // plan / pattern mismatch
     if (herr > 0) *bad_block = herr - 1;
+    return cudaSuccess;
+}
+
+// Block Jacobi (Sec. 1's block diagonal preconditioner): D_k = Z_kk, all inverted at once.
+cudaError_t block_jacobi_setup(hm_ctx *h, int *bad_block)
+{
+    Plan &P = h->plan;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    *bad_block = -1;
+    if ((e = cudaMemsetAsync(h->d_Ad, 0, sizeof(double2) * P.diag_entries, st))) return e;
+    if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st))) return e;
+    HM_LAUNCH(h, K_SCATTER,
+              k_scatter_near<double2><<<(int)h->near_t.size(), 128, 0, st>>>(
+                  (int)h->near_t.size(), h->d_near_t, h->d_near_s, h->d_near_off, h->d_near, h->d_leaf_ptr, h->d_pos,
+                  h->d_sptr, h->d_sidx, h->d_srow, h->d_M, h->d_coff, h->d_doff, (double2 *)nullptr, h->d_Ad, h->d_err,
+                  true));
+    const size_t inv_smem = sizeof(double2) * (64 * 65 + 128);
+    if ((e = cudaFuncSetAttribute(k_pivot_inverse<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)inv_smem)))
+        return e;
+    HM_LAUNCH(h, K_PIVOT,
+              k_pivot_inverse<double2><<<P.nb, 256, inv_smem, st>>>(0, h->d_size, h->d_doff, h->d_Ad, h->d_Dinv,
+                                                                    nullptr, h->d_err));
+    if ((e = cudaGetLastError())) return e;
+    int herr = 0;
+    if ((e = cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    if (herr > 0 && herr != 0x7fffffff) *bad_block = herr - 1;
     return cudaSuccess;
 }
 

@@ -313,6 +313,164 @@ struct Acc {
     }
 };
 
+// Two-stage variant for streamed products (the far field): the operand planes of chunk c+1 are
+// written while the MMAs of chunk c still read the other stage.  Chunks of KC2 contraction
+// entries; stage s at planes + s * STAGE2 (A'hi, A'lo, B'hi, B'lo, KC2 entries each), one
+// mbarrier per stage.  Same operand layout, split and accumulation order as Acc, so a product
+// gives the same result whatever the number of columns.
+constexpr int KC2 = 16;
+constexpr int A_PLANE2 = AROWS * KC2 * 4;     // 8 KB
+constexpr int B_PLANE2 = 128 * KC2 * 4;       // 8 KB
+constexpr int STAGE2 = 2 * A_PLANE2 + 2 * B_PLANE2;
+
+struct Acc2 {
+    unsigned char *planes;   // 2 * STAGE2 bytes, 1024-byte aligned
+    uint64_t *mbar;          // 2 mbarriers
+    uint32_t *tslot;
+    uint32_t tmem = 0;
+    uint32_t parity[2] = {0, 0};
+    bool pending[2] = {false, false};
+    bool any = false;
+    int m8 = 8, p = 8;
+
+    __device__ unsigned char *ahi(int s) const { return planes + s * STAGE2; }
+    __device__ unsigned char *alo(int s) const { return planes + s * STAGE2 + A_PLANE2; }
+    __device__ unsigned char *bhi(int s) const { return planes + s * STAGE2 + 2 * A_PLANE2; }
+    __device__ unsigned char *blo(int s) const { return planes + s * STAGE2 + 2 * A_PLANE2 + B_PLANE2; }
+
+    __device__ void open(int m, int c)
+    {
+        m8 = (m + 7) & ~7;
+        p = (c + 7) & ~7;
+        if (threadIdx.x < 32) tmem_alloc(tslot);
+        if (threadIdx.x == 0) {
+            mbar_init(mbar);
+            mbar_init(mbar + 1);
+        }
+        fence_before();
+        __syncthreads();
+        fence_after();
+        tmem = *tslot;
+    }
+
+    // all threads: stage s may be written again once its MMAs have finished
+    __device__ void wait(int s, int *err, unsigned long long bound)
+    {
+        if (!pending[s]) return;
+        if (!mbar_try(mbar + s, parity[s])) {
+            const unsigned long long t0 = gtimer_tc();
+            while (!mbar_try(mbar + s, parity[s]))
+                if (gtimer_tc() - t0 > bound) {
+                    if (err) atomicCAS(err, 0, ERR_TIMEOUT);
+                    break;
+                }
+        }
+        parity[s] ^= 1u;
+        pending[s] = false;
+        fence_after();
+    }
+
+    __device__ __forceinline__ void put_a(int s, int row, int k, float2 v) const
+    {
+        uint32_t h, l;
+        split(v.x, h, l);
+        *(uint32_t *)(ahi(s) + kmaj(row, k, AROWS)) = h;
+        *(uint32_t *)(alo(s) + kmaj(row, k, AROWS)) = l;
+        split(v.y, h, l);
+        *(uint32_t *)(ahi(s) + kmaj(m8 + row, k, AROWS)) = h;
+        *(uint32_t *)(alo(s) + kmaj(m8 + row, k, AROWS)) = l;
+    }
+
+    __device__ __forceinline__ void put_b(int s, int col, int k, float2 v) const
+    {
+        uint32_t h, l;
+        const int rows = 2 * p;
+        split(v.x, h, l);
+        *(uint32_t *)(bhi(s) + kmaj(col, k, rows)) = h;
+        *(uint32_t *)(blo(s) + kmaj(col, k, rows)) = l;
+        split(v.y, h, l);
+        *(uint32_t *)(bhi(s) + kmaj(p + col, k, rows)) = h;
+        *(uint32_t *)(blo(s) + kmaj(p + col, k, rows)) = l;
+    }
+
+    __device__ void zero_pad(int s, int klen) const
+    {
+        const int k8 = (klen + 7) & ~7, np = k8 - klen, ra = 2 * m8, rb = 2 * p;
+        for (int e = threadIdx.x; e < np * (ra + rb); e += blockDim.x) {
+            const int k = klen + e % np, r = e / np;
+            if (r < ra) {
+                *(uint32_t *)(ahi(s) + kmaj(r, k, AROWS)) = 0u;
+                *(uint32_t *)(alo(s) + kmaj(r, k, AROWS)) = 0u;
+            } else {
+                *(uint32_t *)(bhi(s) + kmaj(r - ra, k, rb)) = 0u;
+                *(uint32_t *)(blo(s) + kmaj(r - ra, k, rb)) = 0u;
+            }
+        }
+    }
+
+    // all threads after writing stage s: thread 0 issues its MMAs, committed to mbar[s]
+    __device__ void issue(int s, int klen)
+    {
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0 && klen > 0) {
+            fence_after();
+            const int rb = 2 * p, steps = (klen + 7) >> 3;
+            const uint32_t id = idesc_tf32(AROWS, rb);
+            const uint32_t a0 = smem_u32(ahi(s)), a1 = smem_u32(alo(s)), b0 = smem_u32(bhi(s)), b1 = smem_u32(blo(s));
+            const uint32_t alb = AROWS * 16, blb = rb * 16;
+            for (int t = 0; t < steps; ++t) {
+                const uint32_t ao = t * 2 * alb, bo = t * 2 * blb;
+                mma(tmem, sdesc(a1 + ao, alb, 128), sdesc(b0 + bo, blb, 128), id, any ? 1u : 0u);
+                any = true;
+                mma(tmem, sdesc(a0 + ao, alb, 128), sdesc(b1 + bo, blb, 128), id, 1u);
+                mma(tmem, sdesc(a0 + ao, alb, 128), sdesc(b0 + bo, blb, 128), id, 1u);
+            }
+            commit(mbar + s);
+        }
+        any = any || klen > 0;
+        pending[s] = pending[s] || klen > 0;
+    }
+
+    __device__ bool drain(float *dsm) const
+    {
+        if (!any) return false;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3;
+        const int nw = blockDim.x >> 5, halves = nw >= 8 ? 2 : 1, h = warp >> 2;
+        const int rb = 2 * p, ld = rb + 1, row = q * 32 + lane;
+        if (q * 32 < 2 * m8 && h < halves) {
+            const int c0 = h * (rb / halves), c1 = c0 + rb / halves;
+            for (int c = c0; c < c1; c += 8) {
+                float v[8];
+                tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                if (row < 2 * m8)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) dsm[row * ld + c + i] = v[i];
+            }
+        }
+        fence_before();
+        __syncthreads();
+        return true;
+    }
+
+    __device__ __forceinline__ float2 entry(const float *dsm, int row, int col) const
+    {
+        const int ld = 2 * p + 1;
+        return make_float2(dsm[row * ld + col] - dsm[(m8 + row) * ld + p + col],
+                           dsm[row * ld + p + col] + dsm[(m8 + row) * ld + col]);
+    }
+
+    __device__ void close()
+    {
+        fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            fence_after();
+            tmem_dealloc(tmem);
+        }
+    }
+};
+
 // shared memory a kernel using Acc needs beyond its own: the region, 1024-byte aligned
 constexpr size_t SMEM_BYTES = REGION_BYTES + 1024;
 

@@ -44,7 +44,8 @@ class hm_desc(ctypes.Structure):
 
 class hm_opts(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("fill_tol", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+                ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t), ("stream", ctypes.c_void_p),
+                ("preconditioner", ctypes.c_int32), ("compress_in_setup", ctypes.c_int32)]
 
 
 class hm_stats(ctypes.Structure):
@@ -149,7 +150,8 @@ class Handle:
             raise HMError(code, "%s: %s" % (what, hm_last_error(self)))
 
 
-def hmat_create(prob, ordering=1, fill_tol=0.0, precision=0, device=0, hbm_budget=0, stream=None):
+def hmat_create(prob, ordering=1, fill_tol=0.0, precision=0, device=0, hbm_budget=0, stream=None, preconditioner=0,
+                compress_in_setup=0):
     """``prob`` provides perm, leaf_ptr, near_t/near_s/near_off/near_data and
     far_r0/far_r1/far_c0/far_c1/far_rank/far_uoff/far_voff/far_U/far_V (numpy)."""
     L = load()
@@ -181,6 +183,8 @@ def hmat_create(prob, ordering=1, fill_tol=0.0, precision=0, device=0, hbm_budge
     L.hm_default_opts(ctypes.byref(o))
     o.ordering, o.fill_tol, o.precision, o.device, o.hbm_budget = ordering, fill_tol, precision, device, hbm_budget
     o.stream = stream
+    o.preconditioner = preconditioner
+    o.compress_in_setup = compress_in_setup
     h = ctypes.c_void_p()
     code = L.hmat_create(ctypes.byref(d), ctypes.byref(o), ctypes.byref(h))
     if code != HM_OK:
@@ -386,7 +390,7 @@ def hm_tc_cgemm(dA, dB, dC, stream=None):
 
 
 def hm_set_far_schedule(h, kind=0):
-    """Complex-FP32 far-field products: 1 CUDA cores, 2 tensor cores, 0 default (2)."""
+    """Complex-FP32 far-field products: 1 CUDA cores, 2 tensor cores, 0 default (1)."""
     h.check(load().hm_set_far_schedule(h.ptr, kind), "hm_set_far_schedule")
 
 

@@ -44,11 +44,11 @@ def test_traffic_record_lookup(tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("cols, bound", [(64 * 10, "alu"), (1 * 10, "hbm")])
 def test_roofline_bound_follows_intensity(cols, bound):
-    # ten complex-FP32 sweep launches over a 1e6-entry panel; n = 1000
+    # ten complex-FP32 sweep launches over 1e6 stored coefficient entries (of 1.5e6 dense); n = 1000
     nnzL, n, launches = 1_000_000, 1000, 10
     prof = {"sweep_fwd": (launches, launches, 20.0, cols), "dots": (5, 5, 1.0, 5)}
-    fs = {"nnzL": nnzL, "update_flops": 1.0, "update_launches": 1}
-    cls, r = bench.roofline(prof, fs, {"far_entries": 0}, n, 1)
+    fs = {"nnzL": 1_500_000, "update_flops": 1.0, "update_launches": 1}
+    cls, r = bench.roofline(prof, fs, {"far_entries": 0, "coef_entries": nnzL}, n, 1)
     assert cls == "sweep_fwd" and r["bound"] == bound
     flops = 8.0 * nnzL * cols
     bytes_ = 8.0 * (nnzL * launches + 2.0 * n * cols)

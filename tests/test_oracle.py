@@ -342,3 +342,77 @@ def test_sloan_disconnected_components():
     assert sorted(o.tolist()) == list(range(6))
     assert o.tolist()[:3] == [0, 3, 5]      # component of node 0 first, then {1, 2}, then {4}
     assert o.tolist()[3:] == [1, 2, 4]
+
+
+# ---- block-Jacobi comparison preconditioner (Sec. 1: the block diagonal preconditioner) --------
+def test_block_jacobi_operator_is_dense_M_inverse_Z():
+    """M^{-1} (Z_N + Z_F) with M = the near-field diagonal blocks, against its dense form."""
+    rng = np.random.default_rng(21)
+    sizes = [3, 5, 4, 2, 6]
+    pairs = [(0, 0), (0, 1), (1, 1), (1, 2), (2, 2), (2, 3), (3, 3), (3, 4), (4, 4)]
+    far = [((0, 2), 0.3 * (rng.standard_normal((3, 4)) + 1j * rng.standard_normal((3, 4))))]
+    p, Z, ZF = block_problem(sizes, pairs, rng, far=far)
+    order = np.array([2, 0, 4, 1, 3])
+    S = krylov.BlockJacobi(p, order)
+    lp = p.leaf_ptr
+    Mdense = np.zeros_like(Z)
+    for t in range(5):
+        Mdense[lp[t]:lp[t + 1], lp[t]:lp[t + 1]] = Z[lp[t]:lp[t + 1], lp[t]:lp[t + 1]]
+    x = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    y = S.apply_A(S.to_new(x))                       # in the block order
+    ref = np.linalg.solve(Mdense, (Z + ZF) @ x)      # in the original order
+    assert np.linalg.norm(S.to_orig(y) - ref) / np.linalg.norm(ref) < 1e-12
+    b = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    xs, it, rr, ok = krylov.solve(S, b, tol=1e-13, restart=30)
+    assert ok and np.linalg.norm(xs - np.linalg.solve(Z + ZF, b)) / np.linalg.norm(xs) < 1e-11
+
+
+def test_block_jacobi_exact_on_block_diagonal_systems():
+    """No off-diagonal near blocks and no far field: M = Z, so one Arnoldi step."""
+    rng = np.random.default_rng(22)
+    sizes = [4, 3, 5]
+    p, Z, ZF = block_problem(sizes, [(0, 0), (1, 1), (2, 2)], rng)
+    S = krylov.BlockJacobi(p, np.array([1, 2, 0]))
+    b = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    x, it, rr, ok = krylov.solve(S, b, tol=1e-12, restart=10)
+    assert ok and it == 1
+    assert np.linalg.norm(x - np.linalg.solve(Z, b)) / np.linalg.norm(x) < 1e-12
+
+
+# ---- Sec. 3.4 read as compression during the setup (the abstract's reading) ---------------------
+def test_compression_in_setup_changes_exactly_the_later_updates():
+    """Star 0-1, 0-2: eliminating block 0 couples 1 and 2, so W_12 is a fill-in block.  With
+    the compression during setup, W_12 is truncated before the update of step 1 uses it:
+    D_0, D_1, W_01, W_02 equal the post-factorisation reading's, and
+    D_2(setup) - D_2(after) = A_21 (W_12 - trunc(W_12)), with A_21 = D_1 W_12 (the symmetric
+    update's left factor), bounded by ||A_21|| fill_tol ||W_12||."""
+    rng = np.random.default_rng(31)
+    sizes = [4, 6, 5]
+    p, Z, ZF = block_problem(sizes, [(0, 0), (0, 1), (0, 2), (1, 1), (2, 2)], rng, diag_boost=6.0)
+    order = np.array([0, 1, 2])
+    tol = 0.3
+    Fa = schur.setup(p, order, fill_tol=tol)
+    Fb = schur.setup(p, order, fill_tol=tol, compress_in_setup=True)
+    assert Fa.S[1] == [2] and (2, 1) not in Fa.near_pairs           # W_12 is a fill-in block
+    for k in (0, 1):
+        assert np.allclose(Fa.D[k], Fb.D[k], rtol=0, atol=1e-13)
+    for key in ((0, 1), (0, 2)):
+        assert np.array_equal(Fa.W[key], Fb.W[key])
+    W12 = Fa.W[(1, 2)]
+    T12, r = schur.compress_block(W12, tol)
+    assert 0 <= r < min(W12.shape)                                   # the truncation bites
+    assert np.allclose(Fb.W[(1, 2)], T12, rtol=0, atol=1e-13)
+    A21 = Fa.D[1] @ W12
+    dD = Fb.D[2] - Fa.D[2]
+    assert np.linalg.norm(dD - (A21.T @ (W12 - T12))) <= 1e-12 * np.linalg.norm(dD)
+    assert np.linalg.norm(dD) <= np.linalg.norm(A21) * tol * np.linalg.norm(W12) * 1.0001
+
+
+def test_compression_in_setup_zero_tolerance_is_exact(sphere480):
+    P = sphere480
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    Fa = schur.setup(P, order, fill_tol=0.0)
+    Fb = schur.setup(P, order, fill_tol=0.0, compress_in_setup=True)
+    for k in range(Fa.nb):
+        assert np.array_equal(Fa.D[k], Fb.D[k])
