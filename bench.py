@@ -76,6 +76,8 @@ def parse():
                     help="right-hand sides of the plain FP64 one-at-a-time solve measured beside the headline "
                          "(Eq. 28 GMRES to a preconditioned residual of --fp64-tol); 0 = skip")
     ap.add_argument("--fp64-tol", type=float, default=1e-4)
+    ap.add_argument("--fp64-fill-tol", type=float, default=None,
+                    help="fill_tol of the FP64 one-RHS leg (default: --fill-tol)")
     ap.add_argument("--cpu-anchor-run", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--ordering", type=int, default=1, choices=[0, 1, 2],
                     help="Algorithm 1 reordering: 0 none, 1 reverse Cuthill-McKee, 2 Sloan")
@@ -95,6 +97,9 @@ def parse():
     ap.add_argument("--serve-full", action="store_true",
                     help="serving on two resident geometries (sphere30720 + plate29800), 360 requests each, "
                          "offered at 0.5/0.8/1.0x the measured throughput")
+    ap.add_argument("--build", default="host", choices=["host", "gpu"],
+                    help="where the H-matrix comes from: the generator's host build (cached) or the GPU "
+                         "EFIE fill and ACA (Sec. 2, Eqs. 7, 9-10)")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--profile-op", type=int, default=0,
                     help="profiling case: set up the workload, then apply the operator of Eq. 28 this many "
@@ -103,7 +108,9 @@ def parse():
                     help="columns re-solved with the FP64 path at tol 1e-10 to state the relative solution error "
                          "of the measured (mixed) solutions; 0 = skip")
     ap.add_argument("--schedule", default="0,0",
-                    help="sweep schedule 'groups,kind' for --profile-op (0,0 = tuned)")
+                    help="sweep schedule 'groups,kind[,tile]' for --profile-op (0,0 = tuned)")
+    ap.add_argument("--far-schedule", type=int, default=0,
+                    help="complex-FP32 far-field kind for --profile-op: 1 CUDA cores, 2 tensor cores, 0 default")
     return ap.parse_args()
 
 
@@ -152,7 +159,15 @@ def rhs_batch(P, B, plate=False):
     return np.stack(cols, axis=1)
 
 
-def load_problem(name, rank, world):
+def load_problem(name, rank, world, build="host"):
+    """The workload's H-matrix: from the seeded generator's host build (cached on disk), or
+    built on this rank's GPU (hm_efie_fill / hm_efie_far; timings in P.build_timings)."""
+    if build == "gpu":
+        import torch
+        from paper_2111_13483_gb300 import hmatrix
+        P, t = hmatrix.build_problem(name, device=torch.cuda.current_device())
+        P.build_timings = t
+        return P
     import efie_problem as ep
     if world > 1:
         import torch.distributed as td
@@ -298,19 +313,28 @@ def sweep_code_digest(texts=None):
 
 
 def traffic_record(cls, workload, precision):
-    """Measured DRAM bytes per launch of `cls` from a profile summary, if it was taken on the
-    current code of that kernel (sweep_code_digest; else None): (bytes, columns, source file)."""
+    """Measured DRAM traffic of `cls` from a profile summary taken on the current code of that
+    kernel (sweep_code_digest; else None).  A record measured on the workload itself gives the
+    bytes of one launch; one measured on a smaller case of the same kernel gives the ratio of
+    measured to algorithmic bytes, to be scaled by the algorithmic bytes of this workload's
+    launch.  Returns (bytes or None, ratio or None, columns, source file, measured-on)."""
     import glob
     digest = sweep_code_digest()
+    best = None
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             if not line.startswith("traffic-record:"):
                 continue
             kv = dict(t.split("=", 1) for t in line.split()[1:])
-            if (kv.get("class") == cls and kv.get("workload") == workload and int(kv.get("precision", -1)) == precision
-                    and kv.get("source") == digest):
-                return int(kv["bytes"]), int(kv["columns"]), os.path.relpath(path, ROOT)
-    return None
+            if kv.get("class") != cls or int(kv.get("precision", -1)) != precision or kv.get("source") != digest:
+                continue
+            rec = (int(kv["bytes"]) if "bytes" in kv else None, float(kv["ratio"]) if "ratio" in kv else None,
+                   int(kv["columns"]), os.path.relpath(path, ROOT), kv.get("workload"))
+            if kv.get("workload") == workload and rec[0] is not None:
+                return rec
+            if rec[1] is not None:
+                best = rec
+    return best
 
 
 def serving_run(hm, serve, h, P, requests, rate, tol, restart, seed_rhs=2, seed_arr=1, plate=False):
@@ -514,7 +538,9 @@ def bench_config(args, P, world=1):
                         % (args.nrhs, "xz-plane phi sweep, HH" if plate else "theta 90 deg, phi sweep, VV",
                            args.restart, args.fill_tol, ORDERINGS[args.ordering], args.tol, args.fp64_tol),
             "nrhs_per_step": args.nrhs, "parallelism": "replicas x%d" % world,
-            "l2": "inputs larger than L2 (H-matrix %.2f GB resident)" % hmat_gb}
+            "l2": "inputs larger than L2 (H-matrix %.2f GB resident)" % hmat_gb,
+            "hmatrix_build": "GPU EFIE fill + ACA" if getattr(args, "build", "host") == "gpu"
+                             else "seeded generator (host)"}
 
 
 def run_reference(args):
@@ -552,7 +578,7 @@ def run_ours(args):
         import torch.distributed as td
         td.init_process_group("nccl")
     import paper_2111_13483_gb300 as hm
-    P = load_problem(args.workload, rank, world)
+    P = load_problem(args.workload, rank, world, args.build)
     B = args.nrhs
     plate = args.workload.startswith("plate")
     Vh = rhs_batch(P, B, plate)
@@ -603,11 +629,19 @@ def run_ours(args):
     iters = np.concatenate(iters_all[-args.steps:])
     cls, roof = roofline(prof, fs, stats, P.n, args.precision)
     tr = traffic_record(cls, args.workload, args.precision)
-    if tr is not None:
-        roof["traffic"] = tr[0]
-        roof["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one %d-column launch (%s); "
-                                "bytes_per_launch above is the algorithmic count at the mean columns per launch"
-                                % (tr[1], tr[2]))
+    if tr is not None and cls in ("sweep_fwd", "sweep_bwd"):
+        E = 8.0 if args.precision == 1 else 16.0
+        alg = E * (stats["coef_entries"] + 2.0 * P.n * tr[2])       # one tr[2]-column launch
+        if tr[0] is not None:
+            roof["traffic"] = tr[0]
+            roof["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one %d-column launch (%s); "
+                                    "algorithmic bytes of that launch %.0f" % (tr[2], tr[3], alg))
+        else:
+            roof["traffic"] = tr[1] * alg
+            roof["traffic_note"] = ("scaled: ncu dram__bytes_read.sum + dram__bytes_write.sum over algorithmic bytes = "
+                                    "%.3f on a %d-column launch of the same kernel on %s (%s), times this workload's "
+                                    "algorithmic bytes of a %d-column launch (%.0f)"
+                                    % (tr[1], tr[2], tr[4], tr[3], tr[2], alg))
 
     # ---- the plain FP64 form: setup, one RHS at a time, and the error of both forms --------
     cols = sorted(set(int(c) for c in np.linspace(0, B, max(args.error_check, args.fp64_rhs, 1),
@@ -633,7 +667,8 @@ def run_ours(args):
         if args.fp64_rhs > 0:
             # the paper's arithmetic: FP64 setup (fill_tol as the headline) and GMRES(restart)
             # to a preconditioned residual of fp64_tol, one right-hand side per solve
-            g = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=0, device=local,
+            ft64 = args.fill_tol if args.fp64_fill_tol is None else args.fp64_fill_tol
+            g = hm.hmat_create(P, ordering=args.ordering, fill_tol=ft64, precision=0, device=local,
                                stream=stream.cuda_stream)
             hm.precond_setup(g)           # first call allocates the factors
             hm.precond_setup(g)
@@ -656,7 +691,7 @@ def run_ours(args):
             per = float(np.mean(ms1)) / 1e3
             solve_only = 1.0 / per
             with_setup = B / (setup64 / 1e3 + B * per)
-            fp64 = {"setup_ms": setup64, "tol_preconditioned": args.fp64_tol, "fill_tol": args.fill_tol,
+            fp64 = {"setup_ms": setup64, "tol_preconditioned": args.fp64_tol, "fill_tol": ft64,
                     "columns": fcols, "iters": its1, "solve_ms_per_rhs": [float(m) for m in ms1],
                     "rhs_per_s_solve_only": solve_only,
                     "rhs_per_s_with_setup": with_setup,
@@ -742,6 +777,7 @@ def run_ours(args):
             "kernel_ms_per_step": {k: v[2] / args.steps for k, v in prof.items() if v[0]},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck, "serving": serving,
             "error_vs_fp64": err,
+            "matrix_build_s": getattr(P, "build_timings", None),
             "stats": {k: stats[k] for k in ("n", "n_blocks", "near_entries", "far_entries", "fill_blocks",
                                             "coef_entries", "diag_entries", "bandwidth", "setup_gflop")}}
     s = json.dumps(line)
@@ -758,7 +794,7 @@ def run_compare_orderings(args):
     bench batch)."""
     import torch
     import paper_2111_13483_gb300 as hm
-    P = load_problem(args.workload, 0, 1)
+    P = load_problem(args.workload, 0, 1, args.build)
     plate = args.workload.startswith("plate")
     V = rhs_batch(P, args.nrhs, plate)
     op = hm.hmsolve.OP32 + hm.hmsolve.OP_A if args.precision == 1 else hm.hmsolve.OP_A
@@ -798,18 +834,21 @@ def run_table7(args):
     iteration times of the operator's parts from the library's event profiler (one column):
     t_mm = far field (+ near field for block Jacobi), t_mpp = block solves and products with D,
     t_mps = scaling-coefficient sweeps (Schur only), and t_total = t_sm + t_sp + p n (t_mm + t_mp)
-    (Eq. 46) for n = --nrhs right-hand sides, with t_sm = the host build of the H-matrix (EFIE
-    fill and ACA, 0 when the builder's cache held it) plus its upload (hmat_create)."""
+    (Eq. 46) for n = --nrhs right-hand sides, with t_sm = the build of the H-matrix (geometry,
+    EFIE fill and ACA: on the GPU with --build gpu; on the host otherwise, 0 when the builder's
+    cache held it) plus its upload (hmat_create)."""
     import torch
     import paper_2111_13483_gb300 as hm
     t0 = time.perf_counter()
-    P = load_problem(args.workload, 0, 1)
+    P = load_problem(args.workload, 0, 1, args.build)
     t_build = time.perf_counter() - t0
     plate = args.workload.startswith("plate")
     V = rhs_batch(P, args.nrhs, plate)
     cols = [int(c) for c in np.linspace(0, args.nrhs, 4, endpoint=False)]
     out = {"workload": args.workload, "n": int(P.n), "rhs_n": args.nrhs, "tol_preconditioned": args.fp64_tol,
-           "restart": args.restart, "host_build_s_this_process": t_build, "preconditioners": {}}
+           "restart": args.restart, "build": args.build, "build_s_this_process": t_build, "preconditioners": {}}
+    if args.build == "gpu":
+        out["gpu_build"] = P.build_timings
     for name, pc, ft in (("schur", 0, args.fill_tol), ("block_jacobi", 1, 0.0)):
         torch.cuda.synchronize()
         c0 = time.perf_counter()
@@ -843,7 +882,7 @@ def run_table7(args):
         t_mps = (ms.get("sweep_fwd", 0) + ms.get("sweep_bwd", 0)) / 1e3
         p = float(np.mean(its))
         st = hm.hmat_stats(h)
-        t_sm += t_build      # the host EFIE fill and ACA build (0 when the builder's cache had it)
+        t_sm += t_build      # the EFIE fill and ACA build (host: 0 when the builder's cache had it)
         out["preconditioners"][name] = {
             "t_sm_s": t_sm, "t_sp_s": t_sp, "p": p, "iters": its, "t_mm_s": t_mm, "t_mpp_s": t_mpp,
             "t_mps_s": t_mps, "t_mp_s": t_mpp + t_mps, "p_times_tmm_plus_tmp_s": p * (t_mm + t_mpp + t_mps),
@@ -860,11 +899,12 @@ def run_profile_op(args):
     """A short, deterministic case for ncu captures (no timing of its own)."""
     import torch
     import paper_2111_13483_gb300 as hm
-    P = load_problem(args.workload, 0, 1)
+    P = load_problem(args.workload, 0, 1, args.build)
     h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision)
     hm.precond_setup(h)
-    g, k = (int(v) for v in args.schedule.split(","))
-    hm.hmsolve.hm_set_sweep_schedule(h, g, k)
+    sched = [int(v) for v in args.schedule.split(",")]
+    hm.hmsolve.hm_set_sweep_schedule(h, *sched)
+    hm.hmsolve.hm_set_far_schedule(h, args.far_schedule)
     x = torch.randn(args.nrhs, P.n, dtype=torch.complex128, device="cuda")
     y = torch.empty_like(x)
     op = hm.hmsolve.OP32 + hm.hmsolve.OP_A if args.precision == 1 else hm.hmsolve.OP_A

@@ -259,14 +259,22 @@ int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
  * from shared memory, while one helper CTA per block row adds all older dependencies;
  * 4 = one CTA per block row with the block products on the tensor cores (complex-FP32
  * sweeps of a precision 1 handle: TF32 operands split into a rounded part and a remainder,
- * FP32 accumulation; the FP64 sweeps take kind 1 for it).  Kinds 1-3 give bitwise the same
- * result, and kind 4 gives bitwise the same result for every number of groups.  (0, 0) --
- * the default -- lets the library time kind 1 with 1, 2 and 4 groups on its first calls of
- * each width and keep the fastest.
- * Kinds 2 and 3 apply to groups of at most 16 columns (kind 1 otherwise).  HM_EINVAL for
- * other values.
+ * FP32 accumulation; the FP64 sweeps take kind 1 for it); 5 and 6 = one CTA per block row in
+ * thread-block clusters of 8 and 16 CTAs (16 where the device fits them, else 8) that take
+ * consecutive block rows, a row reading the results of earlier rows of its cluster from their
+ * shared memory (complex-FP32 sweeps; the FP64 sweeps take kind 1 for them).  Kinds 1-3, 5
+ * and 6 give bitwise the same result, and kind 4 gives bitwise the same result for every
+ * number of groups.  (0, 0) -- the default -- lets the library time kind 1 with 1, 2 and 4
+ * groups and each tile, and (complex FP32) kinds 5 and 6 with 1 and 2 groups, on its first
+ * calls of each width and keep the fastest.
+ * Kinds 2 and 3 apply to groups of at most 16 columns (kind 1 otherwise).  With compressed
+ * fill-in blocks (fill_tol > 0) kinds 2-4 take kind 1.  `tile` (kind 1) selects the
+ * register tile of each thread -- rows x columns x tiles per thread -- for groups of 5-16
+ * columns: 0 = 2 x 2 x 1, 1 = 1 x 2 x 2, 2 = 1 x 1 x 4; for 17-64 columns: 0 = 2 x 4 x 2,
+ * 1 = 2 x 2 x 4, 2 = 1 x 4 x 4 (1 x 1 x 1 up to 4 columns); every tile adds an output's terms
+ * in the same order, so all give bitwise the same result.  HM_EINVAL for other values.
  */
-int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind);
+int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind, int32_t tile);
 
 /*
  * Test hook for the bounded device-side waits of the sweeps (Eqs. 23, 24; the paper has no
@@ -410,6 +418,63 @@ int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int3
 int hm_plan_far(int32_t n, int32_t n_leaves, const int32_t *leaf_ptr, int32_t n_far, const int32_t *far_r0,
                 const int32_t *far_r1, const int32_t *far_c0, const int32_t *far_c1, const int32_t *far_rank,
                 const int64_t *far_uoff, const int64_t *far_voff, int32_t what, int64_t *out, int64_t *count);
+
+/*
+ * The inputs of the solve computed on the device from the mesh (Sec. 2): Galerkin EFIE
+ * entries of RWG functions (Eq. 7) and ACA factors of admissible blocks (Eqs. 9-10).  No
+ * handle; each call uploads the mesh, runs its kernels on the legacy default stream of
+ * `device` and returns when the outputs are in host memory.  All pointers are host pointers,
+ * caller-owned, read (or written) during the call only.
+ *
+ * Mesh: nv vertices V (nv x 3 doubles), nt triangles T (nt x 3 vertex indices), nb RWG
+ * functions; tri (nb x 2) the T+ and T- triangle of each, free_v (nb x 2) the vertex of T+
+ * and of T- opposite the common edge (the edge length is taken from T+).  Entries use
+ * G = e^{-jkR}/R with wavenumber k and impedance eta0 (time factor e^{+jwt}):
+ *   Z(m, n) = (j k eta0 / 4 pi) [ <f_m, G f_n> - k^-2 <div f_m, G div f_n> ],
+ * Radon's 7-point rule on both triangles; triangle pairs with centroid distance below
+ * max(r_abs, c_rel (h_p + h_q) / 2) (h the longest edge) or p == q use singularity extraction
+ * with the closed-form 1/R and rho/R integrals.  Blocks: block b has the RWG rows
+ * ridx[rptr[b] .. rptr[b+1]-1] and columns cidx[cptr[b] .. cptr[b+1]-1] (rptr[0] = cptr[0]
+ * = 0, every block at least 1 x 1, indices in 0 .. nb-1).
+ *
+ * Blocks are processed in chunks whose device scratch stays within scratch_bytes (0 = 1 GiB;
+ * a single block larger than that gets a chunk of its own); the results do not depend on it.
+ *
+ * Errors: HM_EINVAL on any bad argument (indices out of range, empty blocks, inconsistent
+ * offsets, k <= 0, eps outside (0, 1), scratch_bytes < 0); HM_ENOMEM if a device allocation
+ * fails; HM_ECUDA on another CUDA error (message on stderr).
+ */
+
+/*
+ * Dense blocks: block b is written column-major (m_b x n_b, hm_c128) at out + off[b];
+ * off has nblk + 1 entries with off[0] = 0 and off[b+1] - off[b] = m_b n_b.  mirror = 1: a
+ * block whose row list equals its column list is made exactly symmetric, its lower triangle a
+ * copy of its upper one (the symmetric storage of Sec. 3.2); mirror = 0: every entry computed.
+ */
+int hm_efie_fill(int32_t nv, const double *V, int32_t nt, const int32_t *T, int32_t nb, const int32_t *tri,
+                 const int32_t *free_v, double k, double eta0, double r_abs, double c_rel, int32_t nblk,
+                 const int64_t *rptr, const int32_t *ridx, const int64_t *cptr, const int32_t *cidx, int32_t mirror,
+                 const int64_t *off, hm_c128 *out, int64_t scratch_bytes, int32_t device);
+
+/*
+ * Admissible blocks in the layout hm_desc takes for its far field: partially pivoted ACA
+ * (first row 0, column pivot = argmax of the residual row's moduli over unused columns, ties to
+ * the lowest index, next row = argmax |u_k| over unused rows, a zero residual row moving to
+ * the lowest unused row, stop when |u_k| |v_k| <= eps ||A_k||_F), then re-compression (QR of
+ * both factors, SVD of the small core, the smallest rank with a Frobenius tail <= eps times the
+ * whole).  Per block: rank[b] = r >= 0 with U (m_b x r) at U + uoff[b] and V (n_b x r) at
+ * Vf + voff[b], block = U V^T; or rank[b] = -1 with the dense block (m_b x n_b) at U + uoff[b]
+ * -- when the ACA rank reached min(m_b, n_b, floor(m_b n_b / (m_b + n_b)) + 1, 64) without the
+ * stop rule, or when r (m_b + n_b) >= m_b n_b.  Column-major; blocks follow each other in
+ * block order in U and in Vf.  need[0], need[1] (always written) are the entries of U and Vf
+ * the layout takes; if they exceed cap_u or cap_v the call still writes rank and returns
+ * HM_ENOMEM (U, Vf, uoff, voff then undefined).
+ */
+int hm_efie_far(int32_t nv, const double *V, int32_t nt, const int32_t *T, int32_t nb, const int32_t *tri,
+                const int32_t *free_v, double k, double eta0, double r_abs, double c_rel, int32_t nblk,
+                const int64_t *rptr, const int32_t *ridx, const int64_t *cptr, const int32_t *cidx, double eps,
+                int32_t *rank, int64_t *uoff, int64_t *voff, int64_t cap_u, hm_c128 *U, int64_t cap_v, hm_c128 *Vf,
+                int64_t *need, int64_t scratch_bytes, int32_t device);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhmsolve.so")
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "setup.cu", "compress.cu", "ops.cu", "far.cu", "gmres.cu", "noalloc.cu", "tcprod.cu",
+SOURCES = ["api.cu", "setup.cu", "compress.cu", "ops.cu", "far.cu", "gmres.cu", "noalloc.cu", "tcprod.cu", "efie.cu",
            "planner.cpp"]
 
 

@@ -532,15 +532,16 @@ int hm_get_block(hm_handle h, int32_t what, int32_t k, hm_c128 *out)
     return HM_OK;
 }
 
-int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind)
+int hm_set_sweep_schedule(hm_handle h, int32_t groups, int32_t kind, int32_t tile)
 {
     if (!h) return HM_EINVAL;
     if (groups == 0 && kind == 0) {
         h->sweep_fixed = 0;
         return HM_OK;
     }
-    if ((groups != 1 && groups != 2 && groups != 4) || kind < 1 || kind > 4) return HM_EINVAL;
-    h->sweep_fixed = groups | (kind << 4);
+    if ((groups != 1 && groups != 2 && groups != 4) || kind < 1 || kind > 6 || tile < 0 || tile > 2)
+        return HM_EINVAL;
+    h->sweep_fixed = groups | (kind << 4) | (tile << 8);
     return HM_OK;
 }
 

@@ -9,35 +9,19 @@
 // (r (n_k + n_j) < n_k n_j entries, so they fit), and its rank is recorded; pack_run then
 // gathers every block -- dense, or its factors -- into the compact store the sweeps read.
 //
-// One CTA per fill-in block: one-sided (Hestenes) Jacobi SVD in shared memory of A = W when
-// n_k >= n_j and of A = W^H otherwise, so that A never has more columns than rows (surplus
-// columns of a wide block could never become mutually orthogonal: they would keep rotating
-// at rounding level).  Column pairs are rotated in round-robin order (each round pairs every
-// column once; the eight warps take the pairs of a round in parallel), each rotation the
-// complex Jacobi rotation that makes the two columns orthogonal, accumulated into V.  With u
-// the unit roundoff, a pair is skipped once its coupling |a_p^H a_q| is below
-// sqrt(rows) u |a_p| |a_q| (orthogonal to working precision) or below u^2 ||W||_F^2 (both
-// columns at the rounding level of the block); sweeps repeat until no pair needs a
-// rotation.  Then sigma_i = ||a_i||, A ~ sum over the r largest of a_i v_i^H.
+// One CTA per fill-in block: the one-sided Jacobi SVD of jacobi.cuh in shared memory, of
+// A = W when n_k >= n_j and of A = W^H otherwise, so that A never has more columns than rows
+// (surplus columns of a wide block could never become mutually orthogonal: they would keep
+// rotating at rounding level); the rounding floor of the skip rule is u^2 ||W||_F^2.  Then
+// sigma_i = ||a_i||, A ~ sum over the r largest of a_i v_i^H.
 #include <cmath>
 
 #include "cplx.cuh"
 #include "hm_internal.h"
+#include "jacobi.cuh"
 
 namespace hm {
 
-namespace {
-
-template <class T> struct Prec;
-// unit roundoff of the rotation arithmetic
-template <> struct Prec<double2> { static __device__ double eps() { return 1.1102230246251565e-16; } };
-template <> struct Prec<float2> { static __device__ float eps() { return 5.9604645e-8f; } };
-
-
-__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ float2 conjd(float2 a) { return make_float2(a.x, -a.y); }
-
-}  // namespace
 
 template <class TC>
 __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, const int *fill_k, const int *size,
@@ -65,7 +49,7 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
         const int r = x % m, c = x / m;
         const TC w = Wb[x];
         fro2 += w.x * w.x + w.y * w.y;
-        if (tr) A[r * 64 + c] = conjd(w);
+        if (tr) A[r * 64 + c] = jconj(w);
         else A[c * 64 + r] = w;
     }
     for (int x = threadIdx.x; x < nc * nc; x += blockDim.x) {
@@ -77,102 +61,12 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
     __syncthreads();
     fro2 = 0;
     for (int w = 0; w < 8; ++w) fro2 += s_part[w];
-    const R floor2 = Prec<TC>::eps() * Prec<TC>::eps() * fro2;   // rounding level of the block
-    const R ctol = sqrt(R(nr)) * Prec<TC>::eps();                 // orthogonality reached
-    const int np = (nc + 1) & ~1;   // players of the round robin (one dummy when nc is odd)
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        if (threadIdx.x == 0) s_rot = 0;
-        __syncthreads();
-        for (int t = 0; t < np - 1; ++t) {
-            for (int pi = wp; pi < np / 2; pi += 8) {
-                int p, q;
-                if (pi == 0) {
-                    p = t;
-                    q = np - 1;
-                } else {
-                    p = (t + pi) % (np - 1);
-                    q = (t - pi + np - 1) % (np - 1);
-                }
-                if (p >= nc || q >= nc) continue;
-                TC *ap = A + p * 64, *aq = A + q * 64;
-                R al = 0, be = 0;
-                TC ga = czero(TC());
-                for (int r = lane; r < nr; r += 32) {
-                    const TC x = ap[r], y = aq[r];
-                    al += x.x * x.x + x.y * x.y;
-                    be += y.x * y.x + y.y * y.y;
-                    ga.x += x.x * y.x + x.y * y.y;   // conj(x) y
-                    ga.y += x.x * y.y - x.y * y.x;
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(0xffffffffu, al, o);
-                    be += __shfl_xor_sync(0xffffffffu, be, o);
-                    ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
-                    ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
-                }
-                const R g = sqrt(ga.x * ga.x + ga.y * ga.y);
-                if (!(g > ctol * sqrt(al * be)) || !(g > floor2)) continue;
-                const R zeta = (be - al) / (2 * g);
-                const R tt = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-                const R cs = R(1) / sqrt(R(1) + tt * tt), sn = cs * tt;
-                TC ph;   // conj(gamma) / |gamma|
-                ph.x = ga.x / g;
-                ph.y = -ga.y / g;
-                for (int r = lane; r < nr; r += 32) {
-                    const TC x = ap[r];
-                    const TC y = cmul(ph, aq[r]);
-                    ap[r].x = cs * x.x - sn * y.x;
-                    ap[r].y = cs * x.y - sn * y.y;
-                    aq[r].x = sn * x.x + cs * y.x;
-                    aq[r].y = sn * x.y + cs * y.y;
-                }
-                TC *vp = V + p * 64, *vq = V + q * 64;
-                for (int r = lane; r < nc; r += 32) {
-                    const TC x = vp[r];
-                    const TC y = cmul(ph, vq[r]);
-                    vp[r].x = cs * x.x - sn * y.x;
-                    vp[r].y = cs * x.y - sn * y.y;
-                    vq[r].x = sn * x.x + cs * y.x;
-                    vq[r].y = sn * x.y + cs * y.y;
-                }
-                if (lane == 0) s_rot = 1;
-            }
-            __syncthreads();
-        }
-        if (!s_rot) break;
-        __syncthreads();
-    }
-    // singular values: column norms
-    for (int c = wp; c < nc; c += 8) {
-        R s2 = 0;
-        for (int r = lane; r < nr; r += 32) s2 += A[c * 64 + r].x * A[c * 64 + r].x + A[c * 64 + r].y * A[c * 64 + r].y;
-        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        if (lane == 0) sig[c] = s2;   // squared
-    }
+    const R floor2 = JacobiEps<TC>::u() * JacobiEps<TC>::u() * fro2;   // rounding level of the block
+    jacobi_sweeps<TC, 64>(A, V, nr, nc, floor2, &s_rot);
+    column_norms2<TC, 64>(A, nr, nc, sig);   // singular values squared
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int c = 0; c < nc; ++c) ord[c] = c;
-        for (int a = 1; a < nc; ++a) {     // descending by sigma^2 (stable)
-            const int v = ord[a];
-            int b = a - 1;
-            while (b >= 0 && sig[ord[b]] < sig[v]) {
-                ord[b + 1] = ord[b];
-                --b;
-            }
-            ord[b + 1] = v;
-        }
-        // suffix sums of the sorted sigma^2 (smallest first, no cancellation); smallest r with
-        // sqrt(sum_{i >= r} sigma_i^2) <= tol * sqrt(total)
-        double suf[65];
-        suf[nc] = 0.0;
-        for (int i = nc - 1; i >= 0; --i) suf[i] = suf[i + 1] + (double)sig[ord[i]];
-        const double thr = tol * sqrt(suf[0]);
-        int r = nc;
-        for (int i = 0; i <= nc; ++i)
-            if (sqrt(suf[i]) <= thr) {
-                r = i;
-                break;
-            }
+        int r = truncation_rank(sig, ord, nc, tol);
         if ((int64_t)r * (m + n) >= (int64_t)m * n) r = -1;
         s_rank = r;
     }
@@ -184,8 +78,8 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
             TC acc = czero(TC());
             for (int l = 0; l < r; ++l) {
                 const int o = ord[l];
-                acc = tr ? cfma(V[o * 64 + row], conjd(A[o * 64 + c]), acc)
-                         : cfma(A[o * 64 + row], conjd(V[o * 64 + c]), acc);
+                acc = tr ? cfma(V[o * 64 + row], jconj(A[o * 64 + c]), acc)
+                         : cfma(A[o * 64 + row], jconj(V[o * 64 + c]), acc);
             }
             Wb[x] = acc;
         }
@@ -199,7 +93,7 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
         }
         for (int x = threadIdx.x; x < n * r; x += blockDim.x) {
             const int c = x % n, o = ord[x / n];
-            Qb[x] = conjd(tr ? A[o * 64 + c] : V[o * 64 + c]);
+            Qb[x] = jconj(tr ? A[o * 64 + c] : V[o * 64 + c]);
         }
     }
     if (threadIdx.x == 0) rank_out[f] = r;

@@ -138,9 +138,9 @@ struct FarPlan {
 // result) and the fastest per column is kept.
 constexpr int SWEEP_GMAX = 4;
 struct SweepTune {
-    int ncand = 0, trial = 0, best = 0;   // candidate code: groups | blocks per CTA << 4
-    int cand[6] = {}, width[6] = {};
-    cudaEvent_t ev[12] = {};
+    int ncand = 0, trial = 0, best = 0;   // candidate code: groups | kind << 4 | tile shape << 8
+    int cand[16] = {}, width[16] = {};
+    cudaEvent_t ev[32] = {};
 };
 
 }  // namespace hm

@@ -192,6 +192,87 @@ __device__ __forceinline__ void stage_tagged(int count, unsigned epoch, int *err
     }
 }
 
+// ---- cluster-chained complex-FP32 sweeps (schedule kinds 5 and 6) -------------------------
+// The C CTAs of a thread-block cluster take C consecutive tickets, i.e. consecutive block rows
+// of the sweep order (C / G rows of each of the G column groups).  A finished row stays in its
+// CTA's shared memory (the result buffer of sweep_row) beside a ready word holding the launch
+// epoch; a later row of the same cluster and group reads that dependency through distributed
+// shared memory instead of waiting for its tagged words to reach L2.  Every CTA of the cluster
+// waits at a cluster barrier before it exits, so those buffers stay readable.  The sums and
+// their order are those of kind 1: the values read are the same FP32 numbers.
+struct CLink {
+    int t0, G, g, nb;   // the cluster's first ticket; groups, this CTA's group; blocks
+    unsigned buf;       // shared-window address of the result buffer (same in every CTA)
+    unsigned flag;      // shared-window address of the ready word
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every CTA of the cluster
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_map(unsigned a, unsigned rank)
+{
+    unsigned d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(rank));
+    return d;
+}
+__device__ __forceinline__ unsigned ld_cluster_u32(unsigned a)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ float2 ld_cluster_f2(unsigned a)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ void st_cluster_u32(unsigned a, unsigned v)
+{
+    asm volatile("st.relaxed.cluster.shared::cta.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// Ys[e] <- entry e of the finished block of cluster CTA `rank` (count entries, its result
+// buffer's layout), once its ready word carries this launch's epoch; a thread with no entry
+// does not wait.  The wait is bounded like every other (ERR_TIMEOUT), and ends early once
+// another wait has expired.
+__device__ void cluster_stage(int count, unsigned epoch, int *err, unsigned rank, const CLink &lk, float2 *Ys)
+{
+    if ((int)threadIdx.x >= count) return;
+    const unsigned fl = cluster_map(lk.flag, rank), bs = cluster_map(lk.buf, rank);
+    if (ld_cluster_u32(fl) != epoch) {
+        const unsigned long long t0 = gtimer();
+        for (;;) {
+            if (*(volatile int *)err) return;
+            __nanosleep(20);
+            if (ld_cluster_u32(fl) == epoch) break;
+            if (gtimer() - t0 > wait_bound(err)) {
+                atomicCAS(err, 0, ERR_TIMEOUT);
+                return;
+            }
+        }
+    }
+    fence_cluster();   // acquire: the entries were written before the ready word (release)
+    for (int e = threadIdx.x; e < count; e += blockDim.x) Ys[e] = ld_cluster_f2(bs + 8u * (unsigned)e);
+}
+
 // A compressed fill-in coefficient block (Sec. 3.4) is stored as P (n_k x r), Q (n_j x r),
 // W_kj ~ P Q^T, and applied as two products: with G the factor on the dependency's side and H
 // the one on the row's side (forward, block W_ko: G = P, H = Q; backward, W_oj: G = Q, H = P),
@@ -269,13 +350,15 @@ __device__ __forceinline__ void stage_block(int b, int no, int nc, const int *le
     for (int x = threadIdx.x; x < nc * r; x += blockDim.x) copy(Ws + r * ldw + x, G + x);
 }
 
-template <class T, int TR, int TC, int NT, bool FWD, bool LL = false>
+template <class T, int TR, int TC, int NT, bool FWD, bool LL = false, bool CLU = false>
 __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, const int *boff, const int *lptr,
                                           const int *lidx, const int *lent, const int64_t *cbo, const int *crk,
                                           const T *W, const T *x, T *y, int n, int nrhs, int budget, int *flags,
                                           int epoch, int *err, T *buf, int cut = 0, int *pub = nullptr,
-                                          uint4 *tag = nullptr)
+                                          uint4 *tag = nullptr, CLink lk = CLink{})
 {
+    // CLU (with LL): dependencies finished by an earlier CTA of the same cluster are read from
+    // its shared memory (cluster_stage), and the result's ready word is raised for the later ones
     // LL (complex FP32 only): dependencies are read from, and the result published to, the
     // tagged copy `tag` (same layout as y); no flags, no fence
     // cut > 0: leave the last `cut` dependencies of the walk out (they are added by the
@@ -328,9 +411,18 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
                     const int k = lidx[b], nc = size[k], ok = boff[k];
                     T *Ys = ys + yoff;
                     lr = lr || dep_rank(crk, lent, b) >= 0;
-                    stage_tagged((int)(nc * nrhs), (unsigned)epoch, err,
-                                 [&](int e) { return tag + ok + e % nc + (int64_t)(e / nc) * n; },
-                                 [&](int e, float2 v) { Ys[e] = v; });
+                    bool local = false;
+                    if constexpr (CLU) {
+                        const int tk = (FWD ? k : lk.nb - 1 - k) * lk.G + lk.g;   // the producer's ticket
+                        if (tk >= lk.t0) {
+                            cluster_stage((int)(nc * nrhs), (unsigned)epoch, err, (unsigned)(tk - lk.t0), lk, Ys);
+                            local = true;
+                        }
+                    }
+                    if (!local)
+                        stage_tagged((int)(nc * nrhs), (unsigned)epoch, err,
+                                     [&](int e) { return tag + ok + e % nc + (int64_t)(e / nc) * n; },
+                                     [&](int e, float2 v) { Ys[e] = v; });
                     yoff += nc * nrhs;
                 }
                 if (q != pend) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
@@ -392,6 +484,12 @@ __device__ __forceinline__ void sweep_row(int o_blk, int no, const int *size, co
         // 32 consecutive rows of a column); y follows
         tile_store(acc, buf, 1, no, no, nrhs, nrt, ntiles);   // buf[r * no + row]
         __syncthreads();
+        if constexpr (CLU) {
+            if (threadIdx.x == 0) {   // release: the barrier orders every thread's entries first
+                fence_cluster();
+                st_cluster_u32(lk.flag, (unsigned)epoch);
+            }
+        }
         for (int e = threadIdx.x; e < no * nrhs; e += blockDim.x) {
             const float2 v = buf[e];
             tag[o + e % no + (int64_t)(e / no) * n] =
@@ -659,6 +757,40 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(int nb, const int *size, cons
                                                     x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
                                                     flags + g * nb, epoch, err, (T *)smraw, 0, nullptr,
                                                     tag + (int64_t)c0 * n);
+}
+
+// Cluster-chained complex-FP32 sweeps (kinds 5, 6; see CLink): the cluster's first CTA takes
+// C tickets at once, every CTA of the cluster takes its own from them, and all wait at a
+// cluster barrier before exiting.  FWD as k_sweep_fwd (lptr/lidx/lent = rptr/ridx/rent), else
+// as k_sweep_bwd (sptr/sidx).
+template <int TR, int TC, int NT, bool FWD>
+__global__ void __launch_bounds__(256) k_sweep_cl(int nb, const int *size, const int *boff, const int *lptr,
+                                                  const int *lidx, const int *lent, const int64_t *cbo,
+                                                  const int *crk, const float2 *W, const float2 *x, float2 *y, int n,
+                                                  int nrhs, int G, int gw, int budget, int *flags, int epoch,
+                                                  int *ticket, int *err, uint4 *tag)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ int s_t;
+    __shared__ unsigned s_ready;
+    const unsigned cr = cluster_rank();
+    if (threadIdx.x == 0) {
+        s_ready = 0;   // launch epochs start at 1
+        if (cr == 0) s_t = atomicAdd(ticket, (int)cluster_size());
+    }
+    cluster_sync();
+    const int t0 = (int)ld_cluster_u32(cluster_map(smem_addr(&s_t), 0));
+    const int t = t0 + (int)cr, pos = t / G, g = t % G;
+    const int o = FWD ? pos : nb - 1 - pos;
+    if (pos < nb && !held_back(err, o)) {
+        const int c0 = g * gw, nc = max(0, min(gw, nrhs - c0));
+        const CLink lk{t0, G, g, nb, smem_addr(smraw), smem_addr(&s_ready)};
+        sweep_row<float2, TR, TC, NT, FWD, true, true>(o, size[o], size, boff, lptr, lidx, lent, cbo, crk, W,
+                                                       x + (int64_t)c0 * n, y + (int64_t)c0 * n, n, nc, budget,
+                                                       flags + g * nb, epoch, err, (float2 *)smraw, 0, nullptr,
+                                                       tag + (int64_t)c0 * n, lk);
+    }
+    cluster_sync();   // the finished rows stay readable until every CTA of the cluster is done
 }
 
 // Chain-and-helpers sweep.  The dependencies of block row b are split: the `recent` ones,
@@ -1174,6 +1306,94 @@ static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, cons
     return cudaGetLastError();
 }
 
+// Cluster-chained launch (complex FP32): the shared memory of sweep_shape, clusters of C CTAs
+// (8, or 16 where the device allows it), the grid rounded up to whole clusters.  Both kernels
+// of a tile shape get the shared-memory limit of the shape's widest group (maxw) once.
+template <int TR, int TC, int NT> static size_t sweep_cl_smem(int w)
+{
+    return sizeof(float2) * (size_t)(2 * SW_WCAP + 64 * stage_ldr(w, TC));
+}
+template <int TR, int TC, int NT> static void sweep_cl_attrs(int maxw)
+{
+    static bool done = false;
+    if (done) return;
+    for (auto k : {k_sweep_cl<TR, TC, NT, true>, k_sweep_cl<TR, TC, NT, false>}) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_cl_smem<TR, TC, NT>(maxw));
+        cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
+    done = true;
+}
+
+template <int TR, int TC, int NT>
+static cudaError_t sweep_cl_shape(hm_ctx *h, const OpData<float2> &d, bool forward, const float2 *x, float2 *y,
+                                  int nrhs, int G, int gw, int ep, int maxw, int C)
+{
+    Plan &P = h->plan;
+    sweep_cl_attrs<TR, TC, NT>(maxw);
+    const int budget = 2 * SW_WCAP + 64 * stage_ldr(gw, TC);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(((int64_t)P.nb * G + C - 1) / C * C));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sweep_cl_smem<TR, TC, NT>(gw);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (forward)
+        HM_LAUNCH(h, K_SWEEP_FWD,
+                  e = cudaLaunchKernelEx(&cfg, k_sweep_cl<TR, TC, NT, true>, P.nb, (const int *)h->d_size,
+                                         (const int *)h->d_boff, (const int *)h->d_rptr, (const int *)h->d_ridx,
+                                         (const int *)h->d_rent, (const int64_t *)h->d_cboff,
+                                         (const int *)h->d_crank, d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep,
+                                         h->d_ticket, h->d_err, h->d_ytag));
+    else
+        HM_LAUNCH(h, K_SWEEP_BWD,
+                  e = cudaLaunchKernelEx(&cfg, k_sweep_cl<TR, TC, NT, false>, P.nb, (const int *)h->d_size,
+                                         (const int *)h->d_boff, (const int *)h->d_sptr, (const int *)h->d_sidx,
+                                         (const int *)nullptr, (const int64_t *)h->d_cboff, (const int *)h->d_crank,
+                                         d.W, x, y, P.n, nrhs, G, gw, budget, h->d_flags, ep, h->d_ticket, h->d_err,
+                                         h->d_ytag));
+    if (e) return e;
+    return cudaGetLastError();
+}
+
+// Largest cluster (16 or 8 CTAs; 0: neither) with which a cluster-chained sweep of the tile
+// shape fits the device at the shape's widest group (maxw); asked once per shape.
+template <int TR, int TC, int NT>
+static int sweep_cl_max(int maxw)
+{
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    sweep_cl_attrs<TR, TC, NT>(maxw);
+    cached = 0;
+    for (int C = 16; C >= 8; C /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = sweep_cl_smem<TR, TC, NT>(maxw);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_sweep_cl<TR, TC, NT, true>, &cfg) == cudaSuccess &&
+            nclusters > 0) {
+            cached = C;
+            break;
+        }
+        cudaGetLastError();
+    }
+    return cached;
+}
+
 // Super-row launch: (TR, TC, NT) = (1, 1, 2) up to 4 columns per group, else (2, 2, 2) up to 16.
 template <class T, int TR, int TC, int NT>
 static cudaError_t sweep_sr_shape(hm_ctx *h, const OpData<T> &d, bool forward, const T *x, T *y, int nrhs, int G,
@@ -1274,7 +1494,7 @@ static int sweep_groups(hm_ctx *h, bool fp32, bool forward, int nrhs, SweepTune 
     if (h->sweep_fixed) return h->sweep_fixed;
     SweepTune &t = h->sweep_tune[fp32][forward][width_class(nrhs)];
     if (t.best) return t.best;
-    if (t.ncand == 0)
+    if (t.ncand == 0) {
         for (int G = 1; G <= SWEEP_GMAX; G *= 2) {
             const int gw = (nrhs + G - 1) / G;
             if (G > 1 && gw < 4) continue;
@@ -1282,9 +1502,20 @@ static int sweep_groups(hm_ctx *h, bool fp32, bool forward, int nrhs, SweepTune 
             // sums but measured slower on every width, and so did the tensor-core kind for the
             // complex-FP32 sweeps (8.7 against 6.1 ms per 64-column launch on the 30,720-unknown
             // sphere: its chunks of 32 are staged and multiplied one after the other); they stay
-            // selectable
-            t.cand[t.ncand++] = G | (1 << 4);
+            // selectable.  Each group width tries its register-tile shapes (sweep_tile_shapes):
+            // the same sums, more or fewer threads busy on small block rows.
+            for (int tv = 0; tv < (gw > 4 ? 3 : 1); ++tv) t.cand[t.ncand++] = G | (1 << 4) | (tv << 8);
         }
+        // complex FP32: the cluster-chained kinds with 1 or 2 groups (8 or 16 CTAs per cluster)
+        for (int G = 1; fp32 && G <= 2; G *= 2) {
+            const int gw = (nrhs + G - 1) / G;
+            if (G > 1 && gw < 4) continue;
+            const int cmax = gw <= 4 ? sweep_cl_max<1, 1, 1>(4)
+                                     : gw <= 16 ? sweep_cl_max<2, 2, 1>(16) : sweep_cl_max<2, 4, 2>(64);
+            if (cmax >= 8) t.cand[t.ncand++] = G | (5 << 4);
+            if (cmax >= 16) t.cand[t.ncand++] = G | (6 << 4);
+        }
+    }
     if (t.ncand == 1) return t.best = t.cand[0];
     if (t.trial < t.ncand) {
         if (!t.ev[0])
@@ -1329,15 +1560,28 @@ static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x
     SweepTune *tu;
     int slot = 0;
     const int code = sweep_groups(h, sizeof(T) == 8, forward, nrhs, &tu, &slot);
-    const int G = std::min(code & 15, nrhs);
+    const int G = std::min(code & 15, nrhs), tv = (code >> 8) & 3;
     // the super-row, chain-and-helpers and tensor-core kinds read the dense panel layout; with
-    // compressed fill-in blocks stored as factors every sweep takes kind 1
-    const int sr = h->lowrank ? 1 : code >> 4;
+    // compressed fill-in blocks stored as factors they take kind 1 (the cluster kinds read both)
+    const int kind = (code >> 4) & 15;
+    const int sr = h->lowrank && kind < 5 ? 1 : kind;
     const int gw = (nrhs + G - 1) / G;
     if (tu) cudaEventRecord(tu->ev[2 * slot], h->stream);
     if constexpr (sizeof(T) == 8) {
         if (sr == 4) {
             e = sweep_tc_launch(h, d, forward, x, y, nrhs, G, gw, ep);
+            if (tu) cudaEventRecord(tu->ev[2 * slot + 1], h->stream);
+            return e;
+        }
+        if (sr == 5 || sr == 6) {
+            // kind 6 asks for clusters of 16 (non-portable): 8 where the device cannot fit them
+            int C = 8;
+            if (sr == 6)
+                C = (gw <= 4 ? sweep_cl_max<1, 1, 1>(4)
+                             : gw <= 16 ? sweep_cl_max<2, 2, 1>(16) : sweep_cl_max<2, 4, 2>(64)) >= 16 ? 16 : 8;
+            if (gw <= 4) e = sweep_cl_shape<1, 1, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 4, C);
+            else if (gw <= 16) e = sweep_cl_shape<2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16, C);
+            else e = sweep_cl_shape<2, 4, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 64, C);
             if (tu) cudaEventRecord(tu->ev[2 * slot + 1], h->stream);
             return e;
         }
@@ -1349,9 +1593,16 @@ static cudaError_t sweep(hm_ctx *h, const OpData<T> &d, bool forward, const T *x
         if (gw <= 4) e = sweep_sr_shape<T, 1, 1, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
         else e = sweep_sr_shape<T, 2, 2, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
     } else if (gw <= 4) e = sweep_shape<T, 1, 1, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 4);
-    else if constexpr (sizeof(T) == 16) e = sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
-    else {
-        if (gw <= 16) e = sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
+    else if (gw <= 16 || sizeof(T) == 16) {
+        // register-tile shapes (TR, TC, NT) for up to 16 columns per group: every one covers a
+        // 64 x 16 output block with 256 threads
+        if (tv == 1) e = sweep_shape<T, 1, 2, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
+        else if (tv == 2) e = sweep_shape<T, 1, 1, 4>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
+        else e = sweep_shape<T, 2, 2, 1>(h, d, forward, x, y, nrhs, G, gw, ep, 16);
+    } else if constexpr (sizeof(T) == 8) {
+        // up to 64 columns per group (complex FP32): 64 x 64 output blocks
+        if (tv == 1) e = sweep_shape<T, 2, 2, 4>(h, d, forward, x, y, nrhs, G, gw, ep, 64);
+        else if (tv == 2) e = sweep_shape<T, 1, 4, 4>(h, d, forward, x, y, nrhs, G, gw, ep, 64);
         else e = sweep_shape<T, 2, 4, 2>(h, d, forward, x, y, nrhs, G, gw, ep, 64);
     }
     if (tu) cudaEventRecord(tu->ev[2 * slot + 1], h->stream);

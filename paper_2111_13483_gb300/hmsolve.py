@@ -62,7 +62,7 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
            "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
            "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm", "hm_plan_order_method",
-           "hm_set_far_schedule"]
+           "hm_set_far_schedule", "hm_efie_fill", "hm_efie_far"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -116,12 +116,17 @@ def load(build_if_missing=True):
     L.hm_batch_step.argtypes = [vp, _i32p, _i32p, _i32p]
     L.hm_batch_result.argtypes = [vp, ctypes.c_int32, vp, _i32p, _f64p]
     L.hm_batch_close.argtypes = [vp]
-    L.hm_set_sweep_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    L.hm_set_sweep_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.hm_get_profile_cols.argtypes = [vp, ctypes.c_int32, _i64p]
     L.hm_test_hold.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
     L.hm_set_far_schedule.argtypes = [vp, ctypes.c_int32]
     L.hm_tc_cgemm.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_int64, vp, ctypes.c_int64,
                               vp, ctypes.c_int64, vp]
+    mesh = [ctypes.c_int32, _f64p, ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, ctypes.c_double,
+            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _i64p, _i32p, _i64p, _i32p]
+    L.hm_efie_fill.argtypes = mesh + [ctypes.c_int32, _i64p, vp, ctypes.c_int64, ctypes.c_int32]
+    L.hm_efie_far.argtypes = mesh + [ctypes.c_double, _i32p, _i64p, _i64p, ctypes.c_int64, vp, ctypes.c_int64, vp,
+                                     _i64p, ctypes.c_int64, ctypes.c_int32]
     _lib = L
     return L
 
@@ -368,10 +373,10 @@ def hm_far_apply_noalloc(h, dx, dy):
     return load().hm_far_apply_noalloc(h.ptr, dx.data_ptr(), dy.data_ptr(), dx.shape[0])
 
 
-def hm_set_sweep_schedule(h, groups=0, kind=0):
+def hm_set_sweep_schedule(h, groups=0, kind=0, tile=0):
     """Pins the sweep schedule (column groups 1/2/4; kind 1 row per CTA, 2 two rows, 3 chain +
-    helpers); (0, 0) = tuned."""
-    h.check(load().hm_set_sweep_schedule(h.ptr, groups, kind), "hm_set_sweep_schedule")
+    helpers, 4 tensor cores; tile shape 0-2 of kind 1); (0, 0) = tuned."""
+    h.check(load().hm_set_sweep_schedule(h.ptr, groups, kind, tile), "hm_set_sweep_schedule")
 
 
 def hm_test_hold(h, block=-1, wait_ns=0):
@@ -467,3 +472,73 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Mesh:
+    """The mesh arguments of hm_efie_fill / hm_efie_far: vertices, triangles, and per RWG
+    function its T+ / T- triangles and their free vertices."""
+
+    def __init__(self, V, T, tri, free, k, eta0, r_abs=0.2, c_rel=3.0):
+        self.V = np.ascontiguousarray(V, dtype=np.float64)
+        self.T = np.ascontiguousarray(T, dtype=np.int32)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.free = np.ascontiguousarray(free, dtype=np.int32)
+        self.k, self.eta0, self.r_abs, self.c_rel = float(k), float(eta0), float(r_abs), float(c_rel)
+
+    def args(self):
+        return [len(self.V), _p(self.V, _f64p), len(self.T), _p(self.T, _i32p), len(self.tri), _p(self.tri, _i32p),
+                _p(self.free, _i32p), self.k, self.eta0, self.r_abs, self.c_rel]
+
+
+def _block_lists(rows_list, cols_list):
+    rptr = np.zeros(len(rows_list) + 1, dtype=np.int64)
+    cptr = np.zeros(len(cols_list) + 1, dtype=np.int64)
+    rptr[1:] = np.cumsum([len(r) for r in rows_list])
+    cptr[1:] = np.cumsum([len(c) for c in cols_list])
+    ridx = np.ascontiguousarray(np.concatenate(rows_list) if len(rows_list) else np.zeros(0), dtype=np.int32)
+    cidx = np.ascontiguousarray(np.concatenate(cols_list) if len(cols_list) else np.zeros(0), dtype=np.int32)
+    return rptr, ridx, cptr, cidx
+
+
+def hm_efie_fill(mesh, rows_list, cols_list, mirror=0, device=0, scratch_bytes=0):
+    """Dense blocks of Eq. 7 (RWG index lists per block); returns (flat complex128, offsets)."""
+    L = load()
+    rptr, ridx, cptr, cidx = _block_lists(rows_list, cols_list)
+    off = np.zeros(len(rows_list) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(r) * len(c) for r, c in zip(rows_list, cols_list)])
+    out = np.empty(int(off[-1]), dtype=np.complex128)
+    code = L.hm_efie_fill(*mesh.args(), len(rows_list), _p(rptr, _i64p), _p(ridx, _i32p), _p(cptr, _i64p),
+                          _p(cidx, _i32p), mirror, _p(off, _i64p), out.ctypes.data if len(out) else None,
+                          scratch_bytes, device)
+    if code != HM_OK:
+        raise HMError(code, "hm_efie_fill failed (details on stderr)")
+    return out, off
+
+
+def hm_efie_far(mesh, rows_list, cols_list, eps, device=0, cap=None, scratch_bytes=0):
+    """ACA + re-compression of admissible blocks; returns (rank, uoff, voff, U, V) in the
+    layout of hm_desc's far field (rank -1: the dense block at U[uoff])."""
+    L = load()
+    nb = len(rows_list)
+    rptr, ridx, cptr, cidx = _block_lists(rows_list, cols_list)
+    rank = np.zeros(nb, dtype=np.int32)
+    uoff = np.zeros(nb, dtype=np.int64)
+    voff = np.zeros(nb, dtype=np.int64)
+    need = np.zeros(2, dtype=np.int64)
+    if cap is None:   # a first guess: rank 12 factors for every block
+        m = np.diff(rptr)
+        n = np.diff(cptr)
+        cap = (int(np.sum(np.minimum(m * n, 12 * m))), int(np.sum(np.minimum(m * n, 12 * n))))
+    for _ in range(2):
+        U = np.empty(max(cap[0], 1), dtype=np.complex128)
+        V = np.empty(max(cap[1], 1), dtype=np.complex128)
+        code = L.hm_efie_far(*mesh.args(), nb, _p(rptr, _i64p), _p(ridx, _i32p), _p(cptr, _i64p), _p(cidx, _i32p),
+                             eps, _p(rank, _i32p), _p(uoff, _i64p), _p(voff, _i64p), cap[0], U.ctypes.data, cap[1],
+                             V.ctypes.data, _p(need, _i64p), scratch_bytes, device)
+        if code == HM_ENOMEM and (need[0] > cap[0] or need[1] > cap[1]):
+            cap = (int(need[0]), int(need[1]))
+            continue
+        if code != HM_OK:
+            raise HMError(code, "hm_efie_far failed (details on stderr)")
+        return rank, uoff, voff, U[:need[0]], V[:need[1]]
+    raise HMError(HM_ENOMEM, "hm_efie_far: factor storage")

@@ -130,3 +130,55 @@ def test_create_rejects_malformed_descriptions(hm, breakage):
     with pytest.raises(hm.HMError) as ei:
         hm.hmat_create(p)
     assert ei.value.code == hm.HM_EINVAL
+
+
+@pytest.mark.parametrize("breakage", ["row_index", "col_index", "empty_block", "mirror", "triangle", "free_vertex",
+                                      "wavenumber", "eps"])
+def test_efie_calls_reject_bad_arguments_before_any_device_work(hm, breakage):
+    """hm_efie_fill / hm_efie_far validate every index and size on the host (HM_EINVAL) before
+    touching a device, so these run without a GPU."""
+    import efie_problem as ep
+    import efie_problem.builder as B
+    H = hm
+    P = ep.build("plate_tiny")
+    V, T, tri, free = P.rwg.V, P.rwg.T.copy(), P.rwg.tri.copy(), P.rwg.free.copy()
+    k, rows, cols, mirror, eps = B.K0, [np.array([0, 1])], [np.array([2])], 0, 1e-3
+    if breakage == "row_index":
+        rows = [np.array([0, P.n])]
+    elif breakage == "col_index":
+        cols = [np.array([-1])]
+    elif breakage == "empty_block":
+        rows = [np.zeros(0, np.int32)]
+    elif breakage == "mirror":
+        mirror = 2
+    elif breakage == "triangle":
+        tri[0, 1] = len(T)
+    elif breakage == "free_vertex":
+        free[3, 0] = len(V)
+    elif breakage == "wavenumber":
+        k = 0.0
+    elif breakage == "eps":
+        eps = 1.5
+    mesh = H.Mesh(V, T, tri, free, k, B.ETA0)
+    with pytest.raises(hm.HMError) as ei:
+        if breakage == "eps":
+            H.hm_efie_far(mesh, rows, cols, eps)
+        else:
+            H.hm_efie_fill(mesh, rows, cols, mirror=mirror)
+    assert ei.value.code == H.HM_EINVAL
+    if breakage not in ("mirror", "eps"):
+        with pytest.raises(hm.HMError) as ei:
+            H.hm_efie_far(mesh, rows, cols, 1e-3)
+        assert ei.value.code == H.HM_EINVAL
+
+
+def test_efie_calls_accept_no_blocks(hm):
+    import efie_problem as ep
+    import efie_problem.builder as B
+    H = hm
+    P = ep.build("plate_tiny")
+    mesh = H.Mesh(P.rwg.V, P.rwg.T, P.rwg.tri, P.rwg.free, B.K0, B.ETA0)
+    out, off = H.hm_efie_fill(mesh, [], [])
+    assert len(out) == 0 and list(off) == [0]
+    rank, uoff, voff, U, Vf = H.hm_efie_far(mesh, [], [], 1e-3)
+    assert len(rank) == 0 and len(U) == 0 and len(Vf) == 0

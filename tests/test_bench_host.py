@@ -30,13 +30,16 @@ def test_traffic_record_lookup(tmp_path, monkeypatch):
     _tree(tmp_path, code, [
         "traffic-record: class=sweep_fwd workload=sphere30720 precision=1 columns=64 bytes=123 source=%s" % digest,
         "traffic-record: class=sweep_bwd workload=sphere30720 precision=1 columns=64 bytes=456 source=0000",
+        "traffic-record: class=sweep_fwd workload=sphere7680 precision=0 columns=16 ratio=1.25 source=%s" % digest,
     ])
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     got = bench.traffic_record("sweep_fwd", "sphere30720", 1)
-    assert got is not None and got[0] == 123 and got[1] == 64 and got[2] == os.path.join("profiles", "k.md")
+    assert got is not None and got[0] == 123 and got[2] == 64 and got[3] == os.path.join("profiles", "k.md")
     assert bench.traffic_record("sweep_bwd", "sphere30720", 1) is None      # taken on other code
-    assert bench.traffic_record("sweep_fwd", "sphere30720", 0) is None      # other precision
-    assert bench.traffic_record("sweep_fwd", "plate29800", 1) is None       # other workload
+    assert bench.traffic_record("sweep_fwd", "plate29800", 1) is None       # bytes of another workload
+    # a ratio measured on a smaller case serves any workload of the same kernel and precision
+    got = bench.traffic_record("sweep_fwd", "sphere30720", 0)
+    assert got[0] is None and got[1] == 1.25 and got[2] == 16 and got[4] == "sphere7680"
     # a comment edit of the kernel source keeps the record valid
     (tmp_path / "paper_2111_13483_gb300" / "csrc" / "ops.cu").write_text("// edited\n" + code)
     assert bench.traffic_record("sweep_fwd", "sphere30720", 1)[0] == 123

@@ -98,6 +98,38 @@ def test_unpublished_block_times_out_and_handle_recovers(handle):
         assert np.array_equal(dy.cpu().numpy(), ref[op]), op
 
 
+def test_cluster_sweeps_time_out_and_recover(handle):
+    """The same with the cluster-chained sweeps (kind 5): a held row's in-cluster consumers
+    give up on its ready word in shared memory, the others on its tagged words."""
+    P, h, prec = handle
+    nb = h.n_leaves
+    rng = np.random.default_rng(6)
+    dx = torch.from_numpy(rng.standard_normal((2, P.n)) + 1j * rng.standard_normal((2, P.n))).cuda()
+    off = H.OP32 if prec == 1 else 0
+    # rows whose result a later row of the same cluster (one group: sweep positions 0-7) reads:
+    # forward, k in 1..6 with a row of S_k at most 7; backward, j >= nb - 7 in S_k of some
+    # k >= nb - 8 below it
+    sptr, sidx = H.hm_get_fill(h)
+    S = [set(sidx[sptr[k]:sptr[k + 1]].tolist()) for k in range(nb)]
+    fwd = next(k for k in range(1, 7) if any(j <= 7 for j in S[k]))
+    bwd = next(j for j in range(nb - 2, nb - 8, -1) if any(j in S[k] for k in range(max(nb - 8, 0), j)))
+    try:
+        H.hm_set_sweep_schedule(h, 1, 5, 0)
+        for op, held in ((H.OP_LINV, 0), (H.OP_LINV, fwd), (H.OP_LTINV, nb - 1), (H.OP_LTINV, bwd)):
+            dy = torch.empty_like(dx)
+            hm.hm_apply(h, off + op, dx, dy)
+            ref = dy.cpu().numpy()
+            H.hm_test_hold(h, held, 10_000_000)
+            with pytest.raises(hm.HMError) as ei:
+                hm.hm_apply(h, off + op, dx, dy)
+            assert ei.value.code == H.HM_ETIMEOUT, (op, held)
+            H.hm_test_hold(h, -1, 0)
+            hm.hm_apply(h, off + op, dx, dy)
+            assert np.array_equal(dy.cpu().numpy(), ref), (op, held)
+    finally:
+        H.hm_set_sweep_schedule(h, 0, 0)
+
+
 def test_solve_times_out_then_succeeds(handle):
     P, h, prec = handle
     V = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])

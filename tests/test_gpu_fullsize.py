@@ -259,3 +259,23 @@ def test_30720_mixed_operators_and_solve(s30720):
     I, its, rr, code = hm.solve(h32, b, tol=1e-5, restart=30)
     assert code == 0 and rr[0] <= 1e-5
     assert np.linalg.norm(b - S.Z_orig(I)) / np.linalg.norm(b) <= 1.01e-5
+
+
+@pytest.mark.parametrize("nrhs", [16, 64])
+def test_7680_cluster_sweeps_bitwise_equal_compressed_mixed(s7680c, nrhs):
+    """The cluster-chained sweeps (kinds 5, 6) at the benchmark's widths on a problem with more
+    CTAs than resident slots and compressed fill-in blocks: bitwise the one-row-per-CTA result."""
+    P, F, S, h64, h32 = s7680c
+    X = _rand(S.n, nrhs, 71)
+    try:
+        for op in (H.OP32 + H.OP_LINV, H.OP32 + H.OP_LTINV):
+            ref = None
+            for sched in ((2, 1, 0), (1, 5, 0), (2, 5, 0), (4, 5, 0), (1, 6, 0), (2, 6, 0)):
+                H.hm_set_sweep_schedule(h32, *sched)
+                Y = _apply(h32, op, X)
+                if ref is None:
+                    ref = Y
+                else:
+                    assert np.array_equal(Y, ref), (sched, op)
+    finally:
+        H.hm_set_sweep_schedule(h32, 0, 0)

@@ -287,8 +287,10 @@ def test_compressed_solve_matches_oracle(cfg1_compressed):
 
 # ---- sweep schedules: (groups, kind) choices that give bitwise the same sweeps ------------------
 # kind 1: one block row per CTA, 2: two-row super-rows, 3: chain CTA + helpers (CUDA cores,
-# the same summation order); kind 4: complex FP32 on the tensor cores (its own fixed order,
-# bitwise the same for every column grouping; FP64 sweeps take kind 1 for it)
+# the same summation order), 5 / 6: one block row per CTA in clusters of 8 / 16 CTAs that read
+# their in-cluster dependencies through distributed shared memory (complex FP32; the same
+# summation order; FP64 sweeps take kind 1 for them); kind 4: complex FP32 on the tensor cores
+# (its own fixed order, bitwise the same for every column grouping; FP64 sweeps take kind 1)
 @pytest.mark.parametrize("prec", [0, 1])
 def test_sweep_schedules_bitwise_equal(cfg1, cfg1_mixed, prec):
     P, order, F, S, h64 = cfg1
@@ -296,8 +298,8 @@ def test_sweep_schedules_bitwise_equal(cfg1, cfg1_mixed, prec):
     ops = (hm.hmsolve.OP_LINV, hm.hmsolve.OP_LTINV, hm.hmsolve.OP_A)
     if prec == 1:
         ops = tuple(hm.hmsolve.OP32 + o for o in ops)
-    families = [[(g, k) for g in (1, 2, 4) for k in (1, 2, 3)]]
-    tc = [(g, 4) for g in (1, 2, 4)]
+    families = [[(g, k, 0) for g in (1, 2, 4) for k in (1, 2, 3, 5, 6)] + [(g, 1, t) for g in (1, 2, 4) for t in (1, 2)]]
+    tc = [(g, 4, 0) for g in (1, 2, 4)]
     if prec == 0:
         families[0] += tc
     else:
