@@ -75,9 +75,12 @@ def parse():
     ap.add_argument("--fp64-rhs", type=int, default=4,
                     help="right-hand sides of the plain FP64 one-at-a-time solve measured beside the headline "
                          "(Eq. 28 GMRES to a preconditioned residual of --fp64-tol); 0 = skip")
-    ap.add_argument("--fp64-tol", type=float, default=1e-4)
-    ap.add_argument("--fp64-fill-tol", type=float, default=None,
-                    help="fill_tol of the FP64 one-RHS leg (default: --fill-tol)")
+    ap.add_argument("--fp64-tol", type=float, default=1e-6,
+                    help="preconditioned residual of the FP64 forms (the one-RHS leg; --table7): 1e-6 with "
+                         "fill_tol 0 puts the FP64 solutions within 1e-4 of the solution of Z I = V, the bar "
+                         "the mixed path is held to")
+    ap.add_argument("--fp64-fill-tol", type=float, default=0.0,
+                    help="fill_tol of the FP64 one-RHS leg (0: exact factors, so that it solves Z I = V)")
     ap.add_argument("--cpu-anchor-run", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--ordering", type=int, default=1, choices=[0, 1, 2],
                     help="Algorithm 1 reordering: 0 none, 1 reverse Cuthill-McKee, 2 Sloan")
@@ -97,6 +100,9 @@ def parse():
     ap.add_argument("--serve-full", action="store_true",
                     help="serving on two resident geometries (sphere30720 + plate29800), 360 requests each, "
                          "offered at 0.5/0.8/1.0x the measured throughput")
+    ap.add_argument("--rhs", default="sweep", choices=["sweep", "random"],
+                    help="right-hand sides: the monostatic phi sweep, or directions uniform on the sphere "
+                         "with random polarisation (seed 3)")
     ap.add_argument("--build", default="host", choices=["host", "gpu"],
                     help="where the H-matrix comes from: the generator's host build (cached) or the GPU "
                          "EFIE fill and ACA (Sec. 2, Eqs. 7, 9-10)")
@@ -104,6 +110,9 @@ def parse():
     ap.add_argument("--profile-op", type=int, default=0,
                     help="profiling case: set up the workload, then apply the operator of Eq. 28 this many "
                          "times to --nrhs columns (complex FP32 when --precision 1) and exit; no bench line")
+    ap.add_argument("--profile-build", action="store_true",
+                    help="profiling case: build the workload's H-matrix on the GPU (EFIE fill and ACA, Sec. 2) "
+                         "twice, print the timings of the second and exit; no bench line")
     ap.add_argument("--error-check", type=int, default=4,
                     help="columns re-solved with the FP64 path at tol 1e-10 to state the relative solution error "
                          "of the measured (mixed) solutions; 0 = skip")
@@ -141,12 +150,26 @@ def replica_value(B, steps, world, ms_total):
     return B * steps * world / (ms_total / 1e3)
 
 
-def rhs_batch(P, B, plate=False):
+def rhs_batch(P, B, plate=False, mode="sweep", seed=3):
     """Monostatic plane waves, phi_j = 360 j / B: theta = 90 deg with VV (theta-hat)
     polarisation; for a plate (in the xy plane) the same sweep in the xz plane, i.e. the
     plate standing upright, with HH polarisation (y-hat, tangential at every angle: an
-    edge-on VV wave would not excite the plate)."""
+    edge-on VV wave would not excite the plate).  mode "random": B waves arriving from
+    directions uniform on the sphere (theta = arccos U(-1, 1), phi = U(0, 2 pi)), polarised at
+    an angle psi = U(0, pi) from theta-hat towards phi-hat (default_rng(seed))."""
     cols = []
+    if mode == "random":
+        rng = np.random.default_rng(seed)
+        th = np.arccos(rng.uniform(-1.0, 1.0, B))
+        ph = rng.uniform(0.0, 2.0 * np.pi, B)
+        psi = rng.uniform(0.0, np.pi, B)
+        for j in range(B):
+            st, ct, sp, cp = np.sin(th[j]), np.cos(th[j]), np.sin(ph[j]), np.cos(ph[j])
+            khat = -np.array([st * cp, st * sp, ct])
+            that = np.array([ct * cp, ct * sp, -st])
+            phat = np.array([-sp, cp, 0.0])
+            cols.append(P.plane_wave(khat, np.cos(psi[j]) * that + np.sin(psi[j]) * phat))
+        return np.stack(cols, axis=1)
     for j in range(B):
         ph = 2.0 * np.pi * j / B
         if plate:
@@ -265,13 +288,16 @@ def roofline(prof, fs, stats, n, precision):
     alu_peak = FP32_PEAK_TFLOPS if precision == 1 else FP64_PEAK_TFLOPS
     alu_src = ("derived: 152 SMs x %d %s FMA/clk x 2 flop x 2.07 GHz" % ((128, "FP32") if precision == 1 else (2, "FP64")))
 
-    def entry(flops, bytes_, extra):
-        # flops, bytes_: totals over the class's timed launches
+    def entry(flops, bytes_, extra, bound=None):
+        # flops, bytes_: totals over the class's timed launches; bound: fixed, else the one the
+        # intensity selects against the ridge
         ridge = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
         d = {"avg_launch_ms": ms / max(timed, 1), "launches": launches, "rhs_columns": cols,
              "flops_per_launch": flops / max(launches, 1), "bytes_per_launch": bytes_ / max(launches, 1),
-             "intensity_flop_per_byte": flops / max(bytes_, 1.0), "traffic": None}
-        if flops / max(bytes_, 1.0) > ridge:
+             "intensity_flop_per_byte": flops / max(bytes_, 1.0), "traffic": None,
+             "alu_achieved_tflops": flops / t_s / 1e12, "alu_peak_tflops": alu_peak,
+             "alu_frac": flops / t_s / 1e12 / alu_peak, "alu_peak_source": alu_src}
+        if bound == "alu" or (bound is None and flops / max(bytes_, 1.0) > ridge):
             d.update({"bound": "alu", "achieved": flops / t_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                       "frac": flops / t_s / 1e12 / alu_peak, "peak_source": alu_src})
         else:
@@ -283,17 +309,20 @@ def roofline(prof, fs, stats, n, precision):
     if cls == "update":
         return cls, entry(fs["update_flops"] * launches / fs["update_launches"],
                           E * fs["nnzL"] * 3.0 * launches / fs["update_launches"], {})
+    # the solve's operator (sweeps, far field) against HBM bandwidth, the bound the scope table
+    # fixes for it (matrix bytes read once per launch); the FP32-ALU figures ride along
     if cls in ("sweep_fwd", "sweep_bwd"):
         # per launch: the stored coefficients once (dense blocks, and the factors of the
         # compressed fill-in blocks: each stored entry is one complex MAC per column), the input
         # and output vectors of its columns
         ce = stats["coef_entries"]
         return cls, entry(8.0 * ce * cols, E * (ce * launches + 2.0 * n * cols),
-                          {"coef_entries": ce, "coef_entries_dense": fs["nnzL"]})
+                          {"coef_entries": ce, "coef_entries_dense": fs["nnzL"]}, bound="hbm")
     if cls in ("far1", "far2"):
         # far2 counts two launches per product (partial products + their sum)
         per = launches if cls == "far1" else launches / 2
-        return cls, entry(8.0 * stats["far_entries"] * cols, E * (stats["far_entries"] * per + 2.0 * n * cols), {})
+        return cls, entry(8.0 * stats["far_entries"] * cols, E * (stats["far_entries"] * per + 2.0 * n * cols), {},
+                          bound="hbm")
     return cls, entry(0.0, 16.0 * n * max(cols, 1) * 2, {})
 
 
@@ -535,7 +564,9 @@ def bench_config(args, P, world=1):
                         "GMRES(%d), fill_tol %g, %s ordering; solutions within 1e-4 of the FP64 solution: the "
                         "mixed-precision path stops at ||V - Z I||/||V|| <= %g, the FP64 forms at a preconditioned "
                         "residual of %g"
-                        % (args.nrhs, "xz-plane phi sweep, HH" if plate else "theta 90 deg, phi sweep, VV",
+                        % (args.nrhs, "directions uniform on the sphere, random polarisation (seed 3)"
+                           if getattr(args, "rhs", "sweep") == "random"
+                           else "xz-plane phi sweep, HH" if plate else "theta 90 deg, phi sweep, VV",
                            args.restart, args.fill_tol, ORDERINGS[args.ordering], args.tol, args.fp64_tol),
             "nrhs_per_step": args.nrhs, "parallelism": "replicas x%d" % world,
             "l2": "inputs larger than L2 (H-matrix %.2f GB resident)" % hmat_gb,
@@ -581,7 +612,7 @@ def run_ours(args):
     P = load_problem(args.workload, rank, world, args.build)
     B = args.nrhs
     plate = args.workload.startswith("plate")
-    Vh = rhs_batch(P, B, plate)
+    Vh = rhs_batch(P, B, plate, args.rhs)
     stream = torch.cuda.current_stream()
     h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision, device=local,
                        stream=stream.cuda_stream)
@@ -796,7 +827,7 @@ def run_compare_orderings(args):
     import paper_2111_13483_gb300 as hm
     P = load_problem(args.workload, 0, 1, args.build)
     plate = args.workload.startswith("plate")
-    V = rhs_batch(P, args.nrhs, plate)
+    V = rhs_batch(P, args.nrhs, plate, args.rhs)
     op = hm.hmsolve.OP32 + hm.hmsolve.OP_A if args.precision == 1 else hm.hmsolve.OP_A
     out = {"workload": args.workload, "precision": args.precision, "fill_tol": args.fill_tol, "orderings": {}}
     for o in (0, 1, 2):
@@ -843,7 +874,7 @@ def run_table7(args):
     P = load_problem(args.workload, 0, 1, args.build)
     t_build = time.perf_counter() - t0
     plate = args.workload.startswith("plate")
-    V = rhs_batch(P, args.nrhs, plate)
+    V = rhs_batch(P, args.nrhs, plate, args.rhs)
     cols = [int(c) for c in np.linspace(0, args.nrhs, 4, endpoint=False)]
     out = {"workload": args.workload, "n": int(P.n), "rhs_n": args.nrhs, "tol_preconditioned": args.fp64_tol,
            "restart": args.restart, "build": args.build, "build_s_this_process": t_build, "preconditioners": {}}
@@ -922,6 +953,13 @@ def main():
         return
     if args.profile_op > 0:
         run_profile_op(args)
+        return
+    if args.profile_build:
+        import torch
+        from paper_2111_13483_gb300 import hmatrix
+        hmatrix.build_problem(args.workload, device=torch.cuda.current_device())
+        P, t = hmatrix.build_problem(args.workload, device=torch.cuda.current_device())
+        print(json.dumps({"workload": args.workload, "gpu_build_s": t, "stats": P.stats()}), flush=True)
         return
     if args.compare_orderings:
         run_compare_orderings(args)

@@ -265,8 +265,7 @@ int hm_far_apply_noalloc(hm_handle h, const void *dx, void *dy, int32_t nrhs);
  * shared memory (complex-FP32 sweeps; the FP64 sweeps take kind 1 for them).  Kinds 1-3, 5
  * and 6 give bitwise the same result, and kind 4 gives bitwise the same result for every
  * number of groups.  (0, 0) -- the default -- lets the library time kind 1 with 1, 2 and 4
- * groups and each tile, and (complex FP32) kinds 5 and 6 with 1 and 2 groups, on its first
- * calls of each width and keep the fastest.
+ * groups and each tile on its first calls of each width and keep the fastest.
  * Kinds 2 and 3 apply to groups of at most 16 columns (kind 1 otherwise).  With compressed
  * fill-in blocks (fill_tol > 0) kinds 2-4 take kind 1.  `tile` (kind 1) selects the
  * register tile of each thread -- rows x columns x tiles per thread -- for groups of 5-16
@@ -464,7 +463,7 @@ int hm_efie_fill(int32_t nv, const double *V, int32_t nt, const int32_t *T, int3
  * both factors, SVD of the small core, the smallest rank with a Frobenius tail <= eps times the
  * whole).  Per block: rank[b] = r >= 0 with U (m_b x r) at U + uoff[b] and V (n_b x r) at
  * Vf + voff[b], block = U V^T; or rank[b] = -1 with the dense block (m_b x n_b) at U + uoff[b]
- * -- when the ACA rank reached min(m_b, n_b, floor(m_b n_b / (m_b + n_b)) + 1, 64) without the
+ * -- when the ACA rank reached min(m_b, n_b, floor(m_b n_b / (m_b + n_b)) + 1, 256) without the
  * stop rule, or when r (m_b + n_b) >= m_b n_b.  Column-major; blocks follow each other in
  * block order in U and in Vf.  need[0], need[1] (always written) are the entries of U and Vf
  * the layout takes; if they exceed cap_u or cap_v the call still writes rank and returns

@@ -29,12 +29,13 @@
 // over unused rows; a zero residual row moves to the lowest unused row; stop when
 // |u_k| |v_k| <= eps ||A_k||_F with the recursive norm update.  A row touches only
 // 2 x (column triangles) pairs, so rows and columns are integrated one test point per thread
-// (7 threads per pair).  The rank is capped at min(m, n, floor(m n / (m + n)) + 1, 64); a block
-// that reaches the cap without meeting the stop rule is filled densely.  Re-compression (second
-// kernel, one CTA per block): U = Q_U R_U and V = Q_V R_V by Gram-Schmidt applied twice, the
-// one-sided Jacobi SVD of R_U R_V^T, truncation to the smallest rank whose singular-value tail
-// is <= eps times the Frobenius norm; a block whose truncated factors are not smaller than the
-// block (r (m + n) >= m n) is filled densely.
+// (7 threads per pair).  The rank is capped at min(m, n, floor(m n / (m + n)) + 1, 256); a
+// block that reaches the cap without meeting the stop rule is filled densely.  Re-compression
+// (one CTA per block): U = Q_U R_U and V = Q_V R_V by Gram-Schmidt applied twice, the one-sided
+// Jacobi SVD of R_U R_V^T (in shared memory up to rank 64, in global scratch above), truncation
+// to the smallest rank whose singular-value tail is <= eps times the Frobenius norm; a block
+// whose truncated factors are not smaller than the block (r (m + n) >= m n) is filled densely.
+// Dense blocks are cut into tiles of at most 128 x 64 RWG functions, one CTA each.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -50,10 +51,12 @@ namespace {
 
 constexpr int NQ = 7;
 constexpr int NPV = 8;         // values per triangle pair: I0, Ir (3), Irp (3), Irr
-constexpr int ACA_RCAP = 64;   // rank cap of the on-device ACA
+constexpr int ACA_RCAP = 256;  // rank cap of the on-device ACA
+constexpr int RC_SMALL = 64;   // ranks re-compressed with their work arrays in shared memory
 constexpr int NT = 256;        // threads per CTA
 constexpr size_t CHUNK_BYTES = size_t(1) << 30;   // default device scratch per launch
 constexpr int NONE = 0x7fffffff;
+constexpr int FILL_TR = 128, FILL_TC = 64;   // largest dense tile (RWG rows x columns) of one CTA
 
 __constant__ double c_qw[NQ];
 
@@ -246,22 +249,19 @@ template <class PV> __device__ double2 assemble(const Mesh &M, int m, int n, PV 
 }
 
 // ---------------------------------------------------------------------------------------
-// dense blocks: one CTA per block; block list[x], its pair scratch at pairs + poff[x]
-// (NPV x ntr x ntc, value-major), its entries at out + ooff[x] (column-major).  A block with
-// sym[list[x]] set (rows and columns the same list) takes its lower triangle from the upper
-// one: entry (i, j), i > j, is computed as entry (j, i), so the block is exactly symmetric.
-__global__ void __launch_bounds__(NT) k_efie_fill(Mesh M, Blocks B, int nlist, const int *list, const int64_t *poff,
-                                                  double2 *pairs, const int64_t *ooff, double2 *out,
-                                                  const unsigned char *sym)
+// dense tiles: one CTA per tile x of B (at most FILL_TR x FILL_TC RWG functions), its pair
+// scratch at pairs + poff[x] (NPV x ntr x ntc, value-major), its entry (i, j) at
+// out[ooff[x] + i + j ld[x]] (a column-major piece of its block)
+__global__ void __launch_bounds__(NT, 2) k_efie_fill(Mesh M, Blocks B, int ntile, const int64_t *poff, double2 *pairs,
+                                                     const int64_t *ooff, const int *ld, double2 *out)
 {
-    const int x = blockIdx.x;
-    if (x >= nlist) return;
-    const int b = list[x];
+    const int b = blockIdx.x;
+    if (b >= ntile) return;
     const int m = (int)(B.rptr[b + 1] - B.rptr[b]), n = (int)(B.cptr[b + 1] - B.cptr[b]);
     const int ntr = (int)(B.trptr[b + 1] - B.trptr[b]), ntc = (int)(B.tcptr[b + 1] - B.tcptr[b]);
     const int *Tr = B.tridx + B.trptr[b], *Tc = B.tcidx + B.tcptr[b];
     const int64_t P = (int64_t)ntr * ntc;
-    double2 *pb = pairs + poff[x];
+    double2 *pb = pairs + poff[b];
     for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
         double2 o[NPV];
         pair_values(M, Tr[i % ntr], Tc[i / ntr], o);
@@ -270,19 +270,28 @@ __global__ void __launch_bounds__(NT) k_efie_fill(Mesh M, Blocks B, int nlist, c
     __syncthreads();
     const int *R = B.ridx + B.rptr[b], *C = B.cidx + B.cptr[b];
     const int *rl = B.rloc + 2 * B.rptr[b], *cl = B.cloc + 2 * B.cptr[b];
-    double2 *ob = out + ooff[x];
-    const bool mirror = sym[b] != 0;
+    double2 *ob = out + ooff[b];
+    const int64_t ldo = ld[b];
     for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
-        int i = (int)(e % m), j = (int)(e / m);
-        if (mirror && i > j) {
-            const int t = i;
-            i = j;
-            j = t;
-        }
+        const int i = (int)(e % m), j = (int)(e / m);
         const int r0 = rl[2 * i], r1 = rl[2 * i + 1], c0 = cl[2 * j], c1 = cl[2 * j + 1];
-        ob[e] = assemble(M, R[i], C[j], [&](int s, int t, int v) {
+        ob[i + j * ldo] = assemble(M, R[i], C[j], [&](int s, int t, int v) {
             return pb[v * P + (int64_t)(s ? r1 : r0) + (int64_t)ntr * (t ? c1 : c0)];
         });
+    }
+}
+
+// blocks whose rows and columns are the same list (x-th at out + off[x], mm[x] x mm[x]): the
+// lower triangle becomes a copy of the upper one, so the block is exactly symmetric
+__global__ void k_mirror(int nsym, const int64_t *off, const int *mm, double2 *out)
+{
+    const int x = blockIdx.x;
+    if (x >= nsym) return;
+    const int64_t m = mm[x];
+    double2 *o = out + off[x];
+    for (int64_t e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int64_t i = e % m, j = e / m;
+        if (i > j) o[i + j * m] = o[j + i * m];
     }
 }
 
@@ -360,7 +369,7 @@ __device__ __forceinline__ int aca_cap(int m, int n)
 }
 
 // partially pivoted ACA of block b0 + blockIdx.x (Eqs. 9-10): U (m x cap), V (n x cap)
-__global__ void __launch_bounds__(NT) k_efie_aca(Mesh M, Blocks B, int b0, int nchunk, double eps, AcaWork W)
+__global__ void __launch_bounds__(NT, 2) k_efie_aca(Mesh M, Blocks B, int b0, int nchunk, double eps, AcaWork W)
 {
     __shared__ double s_red[NT / 32], s_v[NT / 32];
     __shared__ int s_i[NT / 32];
@@ -534,23 +543,16 @@ __device__ void cgs2(double2 *X, int rows, int cols, double2 *s_h, double2 *s_rc
     __syncthreads();
 }
 
-// re-compression of the ACA factors of block b0 + blockIdx.x: the truncated factors go to the
-// block's slots in Uo (m x r') and Vo (n x r'), the rank r' (or -1: store dense) to W.rank
-__global__ void __launch_bounds__(NT) k_aca_recompress(int b0, int nchunk, const int64_t *rptr, const int64_t *cptr,
-                                                        double eps, AcaWork W, double2 *Uo, double2 *Vo)
+// re-compression of the ACA factors (rank r) of block b: the truncated factors go to the
+// block's slots in Uo (m x r') and Vo (n x r'), the rank r' (or -1: store dense) to W.rank.
+// SA, SV: LD x LD work arrays (shared memory for LD = 64, global scratch for the larger ranks)
+template <int LD>
+__device__ void recompress(int b, int r, int m, int n, double eps, AcaWork &W, double2 *Uo, double2 *Vo, double2 *SA,
+                           double2 *SV)
 {
-    constexpr int LD = ACA_RCAP;
-    extern __shared__ unsigned char smraw[];
-    double2 *SA = (double2 *)smraw;   // LD x LD: R_U R_V^T, then its rotated columns
-    double2 *SV = SA + LD * LD;       // LD x LD: R_U (upper) and R_V^T (strict lower), then V_J
     __shared__ double2 s_h[LD], s_rc[LD], s_dv[LD];
     __shared__ double s_red[NT / 32], sig[LD];
     __shared__ int ord[LD], s_rot, s_rank;
-    const int lb = blockIdx.x, b = b0 + lb;
-    if (lb >= nchunk) return;
-    const int r = W.rank[b];
-    if (r <= 0) return;   // a zero block (rank 0) or the cap reached (-1): nothing to compress
-    const int m = (int)(rptr[b + 1] - rptr[b]), n = (int)(cptr[b + 1] - cptr[b]);
     double2 *U = W.U + W.uoff[b], *V = W.V + W.voff[b];
     cgs2(U, m, r, s_h, s_rc, s_red, [&](int i, int c, double2 x) { SV[c * LD + i] = x; });
     cgs2(V, n, r, s_h, s_rc, s_red, [&](int i, int c, double2 x) {
@@ -576,7 +578,7 @@ __global__ void __launch_bounds__(NT) k_aca_recompress(int b0, int nchunk, const
     column_norms2<double2, LD>(SA, r, r, sig);
     __syncthreads();
     if (threadIdx.x == 0) {
-        int rr = truncation_rank(sig, ord, r, eps);
+        int rr = truncation_rank<double, LD>(sig, ord, r, eps);
         if ((int64_t)rr * (m + n) >= (int64_t)m * n) rr = -1;
         s_rank = rr;
     }
@@ -598,6 +600,34 @@ __global__ void __launch_bounds__(NT) k_aca_recompress(int b0, int nchunk, const
         }
     }
     if (threadIdx.x == 0) W.rank[b] = rr;
+}
+
+// blocks b0 + blockIdx.x of rank 1 .. 64, with their work arrays in shared memory
+__global__ void __launch_bounds__(NT) k_aca_recompress(int b0, int nchunk, const int64_t *rptr, const int64_t *cptr,
+                                                        double eps, AcaWork W, double2 *Uo, double2 *Vo)
+{
+    extern __shared__ unsigned char smraw[];
+    const int lb = blockIdx.x, b = b0 + lb;
+    if (lb >= nchunk) return;
+    const int r = W.rank[b];
+    // a zero block (rank 0), the cap reached (-1), or a rank for k_aca_recompress_big
+    if (r <= 0 || r > RC_SMALL) return;
+    const int m = (int)(rptr[b + 1] - rptr[b]), n = (int)(cptr[b + 1] - cptr[b]);
+    double2 *SA = (double2 *)smraw;
+    recompress<RC_SMALL>(b, r, m, n, eps, W, Uo, Vo, SA, SA + RC_SMALL * RC_SMALL);
+}
+
+// blocks list[x] of rank 65 .. ACA_RCAP, each with 2 ACA_RCAP^2 entries of global scratch
+__global__ void __launch_bounds__(NT) k_aca_recompress_big(int nlist, const int *list, const int64_t *rptr,
+                                                            const int64_t *cptr, double eps, AcaWork W, double2 *Uo,
+                                                            double2 *Vo, double2 *scratch)
+{
+    const int x = blockIdx.x;
+    if (x >= nlist) return;
+    const int b = list[x], r = W.rank[b];
+    const int m = (int)(rptr[b + 1] - rptr[b]), n = (int)(cptr[b + 1] - cptr[b]);
+    double2 *SA = scratch + (int64_t)x * 2 * ACA_RCAP * ACA_RCAP;
+    recompress<ACA_RCAP>(b, r, m, n, eps, W, Uo, Vo, SA, SA + ACA_RCAP * ACA_RCAP);
 }
 
 // compact copy: len[x] entries from src + soff[x] to dst + doff[x], one CTA per run
@@ -651,10 +681,12 @@ struct DevBufs {
 struct Ctx {
     DevBufs mem;
     Mesh M{};
-    Blocks B{};
-    int nblk = 0;
-    std::vector<int64_t> rptr, cptr, trptr, tcptr;
-    const unsigned char *sym = nullptr;   // per block: mirror the upper triangle
+    Blocks B{};   // the call's blocks on the device (the ACA works on them)
+    int nblk = 0, nt = 0;
+    const int32_t *tri = nullptr;                   // host, the caller's (valid during the call)
+    std::vector<int64_t> rptr, cptr, trptr, tcptr;  // host copies
+    std::vector<int> ridx, cidx;
+    std::vector<unsigned char> sym;                 // per block: mirror the upper triangle
 };
 
 int check_mesh(int nv, const double *V, int nt, const int32_t *T, int nb, const int32_t *tri, const int32_t *fv,
@@ -714,6 +746,25 @@ template <class T> cudaError_t upload(DevBufs &mem, const T **dst, const std::ve
     cudaError_t e = mem.up(&d, v);
     *dst = d;
     return e;
+}
+
+// a set of blocks (RWG row and column lists) on the device with their distinct triangles
+cudaError_t upload_blocks(DevBufs &mem, int nt, const int32_t *tri, const std::vector<int64_t> &rptr,
+                          const std::vector<int> &ridx, const std::vector<int64_t> &cptr,
+                          const std::vector<int> &cidx, Blocks &B, std::vector<int64_t> &trptr,
+                          std::vector<int64_t> &tcptr)
+{
+    const int nblk = (int)rptr.size() - 1;
+    std::vector<int> tridx, tcidx, rloc, cloc;
+    side_lists(nt, nblk, rptr.data(), ridx.data(), tri, trptr, tridx, rloc);
+    side_lists(nt, nblk, cptr.data(), cidx.data(), tri, tcptr, tcidx, cloc);
+    cudaError_t e;
+    if ((e = upload(mem, &B.rptr, rptr)) || (e = upload(mem, &B.cptr, cptr)) || (e = upload(mem, &B.trptr, trptr)) ||
+        (e = upload(mem, &B.tcptr, tcptr)) || (e = upload(mem, &B.ridx, ridx)) || (e = upload(mem, &B.cidx, cidx)) ||
+        (e = upload(mem, &B.tridx, tridx)) || (e = upload(mem, &B.tcidx, tcidx)) || (e = upload(mem, &B.rloc, rloc)) ||
+        (e = upload(mem, &B.cloc, cloc)))
+        return e;
+    return cudaSuccess;
 }
 
 cudaError_t ctx_init(Ctx &X, const double *V, int nt, const int32_t *T, int nb, const int32_t *tri,
@@ -777,69 +828,88 @@ cudaError_t ctx_init(Ctx &X, const double *V, int nt, const int32_t *T, int nb, 
         (e = upload(X.mem, &M.btri, btri)))
         return e;
     X.nblk = nblk;
+    X.nt = nt;
+    X.tri = tri;
     X.rptr.assign(rptr, rptr + nblk + 1);
     X.cptr.assign(cptr, cptr + nblk + 1);
-    std::vector<int> tridx, tcidx, rloc, cloc;
-    side_lists(nt, nblk, rptr, ridx, tri, X.trptr, tridx, rloc);
-    side_lists(nt, nblk, cptr, cidx, tri, X.tcptr, tcidx, cloc);
-    const std::vector<int> vr(ridx, ridx + rptr[nblk]), vc(cidx, cidx + cptr[nblk]);
-    Blocks &B = X.B;
-    if ((e = upload(X.mem, &B.rptr, X.rptr)) || (e = upload(X.mem, &B.cptr, X.cptr)) ||
-        (e = upload(X.mem, &B.trptr, X.trptr)) || (e = upload(X.mem, &B.tcptr, X.tcptr)) ||
-        (e = upload(X.mem, &B.ridx, vr)) || (e = upload(X.mem, &B.cidx, vc)) ||
-        (e = upload(X.mem, &B.tridx, tridx)) || (e = upload(X.mem, &B.tcidx, tcidx)) ||
-        (e = upload(X.mem, &B.rloc, rloc)) || (e = upload(X.mem, &B.cloc, cloc)))
-        return e;
-    std::vector<unsigned char> sym(nblk, 0);
+    X.ridx.assign(ridx, ridx + rptr[nblk]);
+    X.cidx.assign(cidx, cidx + cptr[nblk]);
+    X.sym.assign(nblk, 0);
     for (int b = 0; b < nblk && mirror; ++b)
-        sym[b] = rptr[b + 1] - rptr[b] == cptr[b + 1] - cptr[b] &&
-                 std::equal(ridx + rptr[b], ridx + rptr[b + 1], cidx + cptr[b]);
-    return upload(X.mem, &X.sym, sym);
+        X.sym[b] = rptr[b + 1] - rptr[b] == cptr[b + 1] - cptr[b] &&
+                   std::equal(ridx + rptr[b], ridx + rptr[b + 1], cidx + cptr[b]);
+    return upload_blocks(X.mem, nt, tri, X.rptr, X.ridx, X.cptr, X.cidx, X.B, X.trptr, X.tcptr);
 }
 
-// dense blocks `list` into host memory, block list[x] at host + hoff[x]
+// dense blocks `list` of X into host memory, block list[x] at host + hoff[x].  A block is
+// cut into tiles of at most FILL_TR x FILL_TC RWG functions (one CTA each), so that a large
+// block is spread over the SMs; the tiles of a chunk of blocks get their own triangle lists.
 cudaError_t fill_dense(Ctx &X, const std::vector<int> &list, const std::vector<int64_t> &hoff, hm_c128 *host,
                        size_t chunk_bytes)
 {
     cudaError_t e;
-    int *d_list = nullptr;
-    int64_t *d_poff = nullptr, *d_ooff = nullptr;
     double2 *d_pairs = nullptr, *d_out = nullptr;
-    size_t h_list = 0, h_poff = 0, h_ooff = 0, h_pairs = 0, h_out = 0;
+    size_t h_pairs = 0, h_out = 0;
     size_t x0 = 0;
     while (x0 < list.size()) {
-        std::vector<int> cl;
-        std::vector<int64_t> po(1, 0), oo(1, 0);
+        std::vector<int64_t> trp(1, 0), tcp(1, 0), ooff, pofs, soff;
+        std::vector<int> tr, tc, lds, sm;
         size_t bytes = 0, x1 = x0;
+        int64_t out_len = 0;
         while (x1 < list.size()) {
             const int b = list[x1];
-            const int64_t mn = (X.rptr[b + 1] - X.rptr[b]) * (X.cptr[b + 1] - X.cptr[b]);
+            const int64_t m = X.rptr[b + 1] - X.rptr[b], n = X.cptr[b + 1] - X.cptr[b];
+            // pair scratch estimated from the block's own distinct triangles (its tiles share a few)
             const int64_t P = (X.trptr[b + 1] - X.trptr[b]) * (X.tcptr[b + 1] - X.tcptr[b]);
-            const size_t nbytes = sizeof(double2) * (size_t)(NPV * P + mn);
+            const size_t nbytes = sizeof(double2) * (size_t)(NPV * P * 3 / 2 + m * n);
             if (x1 > x0 && bytes + nbytes > chunk_bytes) break;
+            const int *R = X.ridx.data() + X.rptr[b], *C = X.cidx.data() + X.cptr[b];
+            if (X.sym[b]) {
+                soff.push_back(out_len);
+                sm.push_back((int)m);
+            }
+            for (int64_t c0 = 0; c0 < n; c0 += FILL_TC)
+                for (int64_t r0 = 0; r0 < m; r0 += FILL_TR) {
+                    const int64_t r1 = std::min(m, r0 + FILL_TR), c1 = std::min(n, c0 + FILL_TC);
+                    tr.insert(tr.end(), R + r0, R + r1);
+                    tc.insert(tc.end(), C + c0, C + c1);
+                    trp.push_back((int64_t)tr.size());
+                    tcp.push_back((int64_t)tc.size());
+                    ooff.push_back(out_len + r0 + c0 * m);
+                    lds.push_back((int)m);
+                }
+            pofs.push_back(out_len);
+            out_len += m * n;
             bytes += nbytes;
-            cl.push_back(b);
-            po.push_back(po.back() + NPV * P);
-            oo.push_back(oo.back() + mn);
             ++x1;
         }
-        const int nl = (int)cl.size();
-        if ((e = X.mem.grow(&d_list, &h_list, nl)) || (e = X.mem.grow(&d_poff, &h_poff, nl + 1)) ||
-            (e = X.mem.grow(&d_ooff, &h_ooff, nl + 1)) || (e = X.mem.grow(&d_pairs, &h_pairs, po.back())) ||
-            (e = X.mem.grow(&d_out, &h_out, oo.back())))
+        DevBufs tmem;   // the chunk's tiles
+        Blocks TB{};
+        std::vector<int64_t> ttrp, ttcp;
+        if ((e = upload_blocks(tmem, X.nt, X.tri, trp, tr, tcp, tc, TB, ttrp, ttcp))) return e;
+        const int ntile = (int)ooff.size();
+        std::vector<int64_t> po(ntile + 1, 0);
+        for (int t = 0; t < ntile; ++t) po[t + 1] = po[t] + NPV * (ttrp[t + 1] - ttrp[t]) * (ttcp[t + 1] - ttcp[t]);
+        const int64_t *d_po, *d_oo, *d_so;
+        const int *d_ld, *d_sm;
+        if ((e = X.mem.grow(&d_pairs, &h_pairs, (size_t)po.back())) || (e = X.mem.grow(&d_out, &h_out, (size_t)out_len)) ||
+            (e = upload(tmem, &d_po, po)) || (e = upload(tmem, &d_oo, ooff)) || (e = upload(tmem, &d_ld, lds)) ||
+            (e = upload(tmem, &d_so, soff)) || (e = upload(tmem, &d_sm, sm)))
             return e;
-        if ((e = cudaMemcpy(d_list, cl.data(), sizeof(int) * nl, cudaMemcpyHostToDevice)) ||
-            (e = cudaMemcpy(d_poff, po.data(), sizeof(int64_t) * (nl + 1), cudaMemcpyHostToDevice)) ||
-            (e = cudaMemcpy(d_ooff, oo.data(), sizeof(int64_t) * (nl + 1), cudaMemcpyHostToDevice)))
-            return e;
-        k_efie_fill<<<nl, NT>>>(X.M, X.B, nl, d_list, d_poff, d_pairs, d_ooff, d_out, X.sym);
+        k_efie_fill<<<ntile, NT>>>(X.M, TB, ntile, d_po, d_pairs, d_oo, d_ld, d_out);
+        if (!soff.empty()) k_mirror<<<(unsigned)soff.size(), NT>>>((int)soff.size(), d_so, d_sm, d_out);
         if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize())) return e;
         // copy out, one copy per run of blocks adjacent in the host layout
+        const size_t nl = x1 - x0;
         size_t y = 0;
-        while (y < (size_t)nl) {
+        auto block_end = [&](size_t q) {   // end of block x0 + q in the chunk's output
+            const int b = list[x0 + q];
+            return pofs[q] + (X.rptr[b + 1] - X.rptr[b]) * (X.cptr[b + 1] - X.cptr[b]);
+        };
+        while (y < nl) {
             size_t z = y + 1;
-            while (z < (size_t)nl && hoff[x0 + z] == hoff[x0 + y] + (oo[z] - oo[y])) ++z;
-            if ((e = cudaMemcpy(host + hoff[x0 + y], d_out + oo[y], sizeof(double2) * (oo[z] - oo[y]),
+            while (z < nl && hoff[x0 + z] == hoff[x0 + y] + (pofs[z] - pofs[y])) ++z;
+            if ((e = cudaMemcpy(host + hoff[x0 + y], d_out + pofs[y], sizeof(double2) * (block_end(z - 1) - pofs[y]),
                                 cudaMemcpyDeviceToHost)))
                 return e;
             y = z;
@@ -907,7 +977,7 @@ extern "C" int hm_efie_far(int32_t nv, const double *V, int32_t nt, const int32_
     Ctx X;
     if ((e = ctx_init(X, V, nt, T, nb, tri, free_v, k, eta0, r_abs, c_rel, nblk, rptr, ridx, cptr, cidx, false)))
         return status(e, "hm_efie_far");
-    const size_t smem = sizeof(double2) * 2 * ACA_RCAP * ACA_RCAP;
+    const size_t smem = sizeof(double2) * 2 * RC_SMALL * RC_SMALL;
     if ((e = cudaFuncSetAttribute(k_aca_recompress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return status(e, "hm_efie_far");
     // work slots per block, relative to the block's chunk: pair partials, U and V (cap columns),
@@ -941,9 +1011,12 @@ extern "C" int hm_efie_far(int32_t nv, const double *V, int32_t nt, const int32_
     if ((e = upload(X.mem, &W.poff, wp)) || (e = upload(X.mem, &W.uoff, wu)) || (e = upload(X.mem, &W.voff, wv)) ||
         (e = upload(X.mem, &W.foff, wf)) || (e = X.mem.alloc(&W.rank, nblk)))
         return status(e, "hm_efie_far");
-    double2 *Uo = nullptr, *Vo = nullptr, *d_cu = nullptr, *d_cv = nullptr;
+    double2 *Uo = nullptr, *Vo = nullptr, *d_cu = nullptr, *d_cv = nullptr, *d_big = nullptr;
     int64_t *d_so = nullptr, *d_do = nullptr, *d_len = nullptr;
-    size_t hp = 0, hu = 0, hv = 0, hf = 0, huo = 0, hvo = 0, hcu = 0, hcv = 0, hso = 0, hdo = 0, hlen = 0;
+    int *d_blist = nullptr;
+    size_t hp = 0, hu = 0, hv = 0, hf = 0, huo = 0, hvo = 0, hcu = 0, hcv = 0, hso = 0, hdo = 0, hlen = 0, hbig = 0,
+           hbl = 0;
+    constexpr int BIG_BATCH = 128;   // blocks of rank > 64 re-compressed per launch (2 MiB scratch each)
     int64_t tot_u = 0, tot_v = 0;
     std::vector<int> dense;
     std::vector<int64_t> dense_off;
@@ -954,7 +1027,22 @@ extern "C" int hm_efie_far(int32_t nv, const double *V, int32_t nt, const int32_
             (e = X.mem.grow(&Uo, &huo, cneed_u[ci])) || (e = X.mem.grow(&Vo, &hvo, cneed_v[ci])))
             return status(e, "hm_efie_far");
         k_efie_aca<<<nc, NT>>>(X.M, X.B, b0, nc, eps, W);
+        if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize()) ||
+            (e = cudaMemcpy(rank + b0, W.rank + b0, sizeof(int) * nc, cudaMemcpyDeviceToHost)))
+            return status(e, "hm_efie_far");
+        std::vector<int> big;   // ACA ranks above what the shared-memory re-compression holds
+        for (int b = b0; b < b1; ++b)
+            if (rank[b] > RC_SMALL) big.push_back(b);
         k_aca_recompress<<<nc, NT, smem>>>(b0, nc, X.B.rptr, X.B.cptr, eps, W, Uo, Vo);
+        for (size_t x0 = 0; x0 < big.size(); x0 += BIG_BATCH) {
+            const int nbl = (int)std::min<size_t>(BIG_BATCH, big.size() - x0);
+            if ((e = X.mem.grow(&d_big, &hbig, (size_t)nbl * 2 * ACA_RCAP * ACA_RCAP)) ||
+                (e = X.mem.grow(&d_blist, &hbl, (size_t)nbl)) ||
+                (e = cudaMemcpy(d_blist, big.data() + x0, sizeof(int) * nbl, cudaMemcpyHostToDevice)))
+                return status(e, "hm_efie_far");
+            k_aca_recompress_big<<<nbl, NT>>>(nbl, d_blist, X.B.rptr, X.B.cptr, eps, W, Uo, Vo, d_big);
+            if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize())) return status(e, "hm_efie_far");
+        }
         if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize()) ||
             (e = cudaMemcpy(rank + b0, W.rank + b0, sizeof(int) * nc, cudaMemcpyDeviceToHost)))
             return status(e, "hm_efie_far");

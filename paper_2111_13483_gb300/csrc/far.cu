@@ -149,7 +149,6 @@ __global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, cons
     const int ldw = stage_ldw(ni, TR), ldr = stage_ldr(nrhs, TC);
     const int half = budget / 2, kmax = half / (ldw + ldr);   // >= 32 for ni <= 64
     T *const bufs[2] = {(T *)smraw, (T *)smraw + half};
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     Tile<T, TR, TC, NT> acc;
     tile_load(acc, (const T *)nullptr, 0, 0, ni, nrhs, nrt, ntiles);
     const int w1 = part_ptr[blockIdx.x + 1];
@@ -159,23 +158,46 @@ __global__ void __launch_bounds__(256) k_far_y(int nl, const int *leaf_ptr, cons
         const bool fit = q < w1 && kcum[q + 1] - kcum[p] <= kmax;
         return __syncthreads_count(fit);
     };
+    // the chunk's stacked contraction rows kk = 0 .. klen-1 (segment q's rows kcum[p+q] - k0 ..)
+    // copied by all threads: entry e of the coefficient rows is (kk, i) = (e / ni, e % ni), of
+    // the vector rows (e / nrhs, e % nrhs); a thread's kk only grows, so it follows the segments
+    // in order and reloads a segment's descriptor when it moves to the next
     auto stage = [&](int p, int cnt, T *buf) {
-        const int k0 = kcum[p];
+        const int k0 = kcum[p], klen = kcum[p + cnt] - k0;
         T *Wst = buf, *Yst = buf + kmax * ldw;
-        for (int q = wp; q < cnt; q += nwarp) {
-            const FarSegD g = segs[p + q];
-            const int kb = kcum[p + q] - k0;
-            const T *F = ((g.src & 1) ? V : U) + g.foff;
-            const int ys = g.src >> 1;
-            const T *Yb = (ys == 0 ? t : (ys == 1 ? s : u)) + g.yrow * nrhs;
-            for (int k = 0; k < g.len; ++k) {
-                for (int i = lane; i < ni; i += 32)
-                    cp_async_el(Wst + (kb + k) * ldw + i, F + (int64_t)i * g.fi + (int64_t)k * g.fk);
-                for (int r = lane; r < nrhs; r += 32) cp_async_el(Yst + (kb + k) * ldr + r, Yb + (int64_t)k * nrhs + r);
+        int q = -1, qlo = 0, qhi = 0;
+        const T *F = nullptr;
+        int64_t fi = 0, fk = 0;
+        for (int e = threadIdx.x; e < klen * ni; e += blockDim.x) {
+            const int kk = e / ni, i = e - kk * ni;
+            while (kk >= qhi) {
+                ++q;
+                qlo = kcum[p + q] - k0;
+                qhi = kcum[p + q + 1] - k0;
+                const FarSegD g = segs[p + q];
+                F = ((g.src & 1) ? V : U) + g.foff;
+                fi = g.fi;
+                fk = g.fk;
             }
+            cp_async_el(Wst + kk * ldw + i, F + (int64_t)i * fi + (int64_t)(kk - qlo) * fk);
+        }
+        q = -1;
+        qhi = 0;
+        const T *Yb = nullptr;
+        for (int e = threadIdx.x; e < klen * nrhs; e += blockDim.x) {
+            const int kk = e / nrhs, r = e - kk * nrhs;
+            while (kk >= qhi) {
+                ++q;
+                qlo = kcum[p + q] - k0;
+                qhi = kcum[p + q + 1] - k0;
+                const FarSegD g = segs[p + q];
+                const int ys = g.src >> 1;
+                Yb = (ys == 0 ? t : (ys == 1 ? s : u)) + g.yrow * nrhs;
+            }
+            cp_async_el(Yst + kk * ldr + r, Yb + (int64_t)(kk - qlo) * nrhs + r);
         }
         cp_async_commit();
-        return kcum[p + cnt] - k0;
+        return klen;
     };
     int p = part_ptr[blockIdx.x];
     if (p < w1) {

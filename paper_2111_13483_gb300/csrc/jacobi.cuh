@@ -1,4 +1,5 @@
-// One-sided (Hestenes) Jacobi SVD of a small complex matrix held in shared memory by one CTA,
+// One-sided (Hestenes) Jacobi SVD of a small complex matrix held by one CTA (in shared memory,
+// or in global memory for the larger ACA cores),
 // and the truncation rank of Sec. 3.4 / Eq. 10 (smallest r whose singular-value tail has
 // Frobenius norm <= tol times the total).  Used by the fill-in compression and by the
 // re-compression of ACA factors.
@@ -111,8 +112,8 @@ __device__ void column_norms2(const TC *A, int nr, int nc, typename Real<TC>::ty
 
 // one thread: ord <- columns by descending sig (stable); returns the smallest r with
 // sqrt(sum_{i >= r} sigma_i^2) <= tol sqrt(sum sigma_i^2) (suffix sums from the smallest up,
-// so that no cancellation enters the tail); nc <= 64
-template <class R> __device__ int truncation_rank(const R *sig, int *ord, int nc, double tol)
+// so that no cancellation enters the tail); nc <= MAXN
+template <class R, int MAXN = 64> __device__ int truncation_rank(const R *sig, int *ord, int nc, double tol)
 {
     for (int c = 0; c < nc; ++c) ord[c] = c;
     for (int a = 1; a < nc; ++a) {
@@ -124,7 +125,7 @@ template <class R> __device__ int truncation_rank(const R *sig, int *ord, int nc
         }
         ord[b + 1] = v;
     }
-    double suf[65];
+    double suf[MAXN + 1];
     suf[nc] = 0.0;
     for (int i = nc - 1; i >= 0; --i) suf[i] = suf[i + 1] + (double)sig[ord[i]];
     const double thr = tol * sqrt(suf[0]);

@@ -1506,15 +1506,11 @@ static int sweep_groups(hm_ctx *h, bool fp32, bool forward, int nrhs, SweepTune 
             // the same sums, more or fewer threads busy on small block rows.
             for (int tv = 0; tv < (gw > 4 ? 3 : 1); ++tv) t.cand[t.ncand++] = G | (1 << 4) | (tv << 8);
         }
-        // complex FP32: the cluster-chained kinds with 1 or 2 groups (8 or 16 CTAs per cluster)
-        for (int G = 1; fp32 && G <= 2; G *= 2) {
-            const int gw = (nrhs + G - 1) / G;
-            if (G > 1 && gw < 4) continue;
-            const int cmax = gw <= 4 ? sweep_cl_max<1, 1, 1>(4)
-                                     : gw <= 16 ? sweep_cl_max<2, 2, 1>(16) : sweep_cl_max<2, 4, 2>(64);
-            if (cmax >= 8) t.cand[t.ncand++] = G | (5 << 4);
-            if (cmax >= 16) t.cand[t.ncand++] = G | (6 << 4);
-        }
+        // The cluster-chained kinds (5, 6) stay selectable but are not tried: on the
+        // 30,720-unknown sphere they measured 8-14% slower than kind 1 at every width (1: 3.69
+        // against 3.24 ms per forward sweep; 64 in two groups: 5.74 against 5.18 ms) -- a
+        // finished CTA holds its slot until the whole cluster is done, and a row's wait is not
+        // dominated by the L2 round trip that distributed shared memory removes.
     }
     if (t.ncand == 1) return t.best = t.cand[0];
     if (t.trial < t.ncand) {

@@ -525,10 +525,13 @@ def hm_efie_far(mesh, rows_list, cols_list, eps, device=0, cap=None, scratch_byt
     uoff = np.zeros(nb, dtype=np.int64)
     voff = np.zeros(nb, dtype=np.int64)
     need = np.zeros(2, dtype=np.int64)
-    if cap is None:   # a first guess: rank 12 factors for every block
+    if cap is None:
+        # every block at its ACA rank cap (only the pages written are ever touched); more is
+        # needed only where dense blocks outgrow that, and the call then reports it
         m = np.diff(rptr)
         n = np.diff(cptr)
-        cap = (int(np.sum(np.minimum(m * n, 12 * m))), int(np.sum(np.minimum(m * n, 12 * n))))
+        cb = np.minimum(np.minimum(np.minimum(m, n), m * n // (m + n) + 1), 256)
+        cap = (int(np.sum(np.minimum(m * n, m * cb))), int(np.sum(n * cb)))
     for _ in range(2):
         U = np.empty(max(cap[0], 1), dtype=np.complex128)
         V = np.empty(max(cap[1], 1), dtype=np.complex128)

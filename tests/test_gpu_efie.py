@@ -193,3 +193,25 @@ def test_results_do_not_depend_on_the_scratch_chunking(H, sphere1920):
     many = H.hm_efie_far(mesh, rl, cl, 1e-3, scratch_bytes=1 << 20)
     for x, y in zip(one, many):
         assert np.array_equal(x, y)
+
+
+def test_large_blocks_are_tiled(H, sphere1920):
+    """Blocks larger than one CTA's tile (128 x 64 RWG functions) are cut into tiles: a 300 x 200
+    block and a ragged 129 x 65 one match the host entries, and a 200 x 200 block whose rows and
+    columns are the same list, with mirror, is exactly symmetric with its upper triangle the
+    host's."""
+    P = sphere1920
+    rng = np.random.default_rng(17)
+    perm = rng.permutation(P.n)
+    rows = [perm[:300], perm[300:429], perm[1000:1200]]
+    cols = [perm[500:700], perm[700:765], perm[1000:1200]]
+    out, off = H.hm_efie_fill(_mesh(H, P), rows, cols, mirror=1)
+    ref, roff = _ev(P).blocks(rows, cols)
+    assert np.array_equal(off, roff)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(out[:off[2]] - ref[:off[2]])) <= 1e-12 * scale
+    S = out[off[2]:].reshape(200, 200).T
+    Sr = ref[off[2]:].reshape(200, 200).T
+    assert np.array_equal(S, S.T)
+    iu = np.triu_indices(200)
+    assert np.max(np.abs(S[iu] - Sr[iu])) <= 1e-12 * scale
