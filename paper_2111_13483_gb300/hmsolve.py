@@ -375,7 +375,8 @@ def hm_far_apply_noalloc(h, dx, dy):
 
 def hm_set_sweep_schedule(h, groups=0, kind=0, tile=0):
     """Pins the sweep schedule (column groups 1/2/4; kind 1 row per CTA, 2 two rows, 3 chain +
-    helpers, 4 tensor cores; tile shape 0-2 of kind 1); (0, 0) = tuned."""
+    helpers, 4 tensor cores, 5 / 6 clusters of 8 / 16 CTAs; tile shape 0-2 of kind 1); (0, 0) =
+    tuned."""
     h.check(load().hm_set_sweep_schedule(h.ptr, groups, kind, tile), "hm_set_sweep_schedule")
 
 
