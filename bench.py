@@ -118,6 +118,8 @@ def parse():
                          "of the measured (mixed) solutions; 0 = skip")
     ap.add_argument("--schedule", default="0,0",
                     help="sweep schedule 'groups,kind[,tile]' for --profile-op (0,0 = tuned)")
+    ap.add_argument("--update-schedule", type=int, default=0,
+                    help="complex-FP32 Schur updates for --profile-op: 1 CUDA cores, 2 tensor cores, 0 default")
     ap.add_argument("--far-schedule", type=int, default=0,
                     help="complex-FP32 far-field kind for --profile-op: 1 CUDA cores, 2 tensor cores, 0 default")
     return ap.parse_args()
@@ -932,6 +934,7 @@ def run_profile_op(args):
     import paper_2111_13483_gb300 as hm
     P = load_problem(args.workload, 0, 1, args.build)
     h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision)
+    hm.hmsolve.hm_set_update_schedule(h, args.update_schedule)
     hm.precond_setup(h)
     sched = [int(v) for v in args.schedule.split(",")]
     hm.hmsolve.hm_set_sweep_schedule(h, *sched)

@@ -312,6 +312,20 @@ int hm_tc_cgemm(int32_t m, int32_t k, int32_t ncols, const void *dA, int64_t lda
  */
 int hm_set_far_schedule(hm_handle h, int32_t kind);
 
+/*
+ * How the complex-FP32 Schur updates of a precision 1 handle's precond_setup (Sec. 3.1, Eq. 19:
+ * A_ij -= A_ik W_kj for i >= j in S_k, the dense contraction of the elimination) are computed:
+ * kind 1 = register-tiled FMAs on the CUDA cores, one CTA per row block and group of column
+ * blocks; kind 2 = the tensor-core micro-kernel of hm_tc_cgemm (TF32 operands split into a
+ * rounded part and a remainder, FP32 accumulation), one CTA per row block and 64 columns of the
+ * panel W_k; 0 = the default (1: on the 30,720-unknown sphere kind 2 took 275 against 252 ms of
+ * updates per setup -- its operands are loaded, split and drained by the threads, and the
+ * products of ~28-unknown blocks are too short to hide that).  Both sum every output's terms in
+ * a fixed order; the FP64 setup always runs on the CUDA cores.  Takes effect at the next
+ * precond_setup.  HM_EINVAL for other values.
+ */
+int hm_set_update_schedule(hm_handle h, int32_t kind);
+
 /* ---- continuous batching (serving) ---------------------------------------------------- */
 
 /*

@@ -568,6 +568,13 @@ int hm_set_far_schedule(hm_handle h, int32_t kind)
     return HM_OK;
 }
 
+int hm_set_update_schedule(hm_handle h, int32_t kind)
+{
+    if (!h || kind < 0 || kind > 2) return HM_EINVAL;
+    h->update_kind = kind == 0 ? 1 : kind;
+    return HM_OK;
+}
+
 int hm_profile(hm_handle h, int32_t mode)
 {
     if (!h || mode < 0 || mode > 2) return HM_EINVAL;

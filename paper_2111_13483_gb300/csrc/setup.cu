@@ -22,6 +22,7 @@
 
 #include "cplx.cuh"
 #include "hm_internal.h"
+#include "tc.cuh"
 #include "tile.cuh"
 
 namespace hm {
@@ -446,6 +447,90 @@ __global__ void __launch_bounds__(256, 2) k_update_grp(int k, int ns, int gb, co
     }
 }
 
+// Schur updates of step k on the tensor cores (complex-FP32 setup, update kind 2).  The step's
+// products are one lower-triangular product of the stacked column [A_ik; i in S_k] (M_k x n_k)
+// with the panel W_k (n_k x M_k): CTA t takes row block a of S_k (i = S_k[a], n_i rows) and 64
+// consecutive columns of W_k among those of blocks b <= a (tasks of row a: ceil((srow_a + n_i) /
+// 64), ucum[e0 + a] the tasks before row a).  C = A_ik W_k[:, c0 : c0 + nc] runs as tcgen05
+// MMAs on 3xTF32 operands (tc::Acc, chunks of tc::KC along n_k); every output column is then
+// subtracted from its block A_ij (j = the S_k block holding the column; the diagonal block in Ad
+// when j = i).  Each output adds its n_k terms in one fixed order.
+__global__ void __launch_bounds__(256) k_update_tc(int k, int ns, const int *ucum, const int *size, const int *sptr,
+                                                   const int *sidx, const int *srow, const int *M, const int64_t *coff,
+                                                   const int64_t *doff, const float2 *W, float2 *A, float2 *Ad,
+                                                   int *err, unsigned long long bound)
+{
+    extern __shared__ unsigned char smraw[];
+    __shared__ uint64_t s_mbar;
+    __shared__ uint32_t s_tslot;
+    __shared__ float2 *s_col[64];
+    const int e0 = sptr[k], t = blockIdx.x;
+    int lo = 0, hi = ns;   // row a: the largest with ucum[e0 + a] <= t
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ucum[e0 + mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    const int a = lo, i = sidx[e0 + a], ni = size[i], nk = size[k], Mk = M[k];
+    const int c0 = (t - ucum[e0 + a]) * 64, nc = min(64, srow[e0 + a] + ni - c0);
+    if (threadIdx.x < nc) {   // where output column c0 + x goes
+        const int c = c0 + threadIdx.x;
+        int l2 = 0, h2 = a + 1;   // block b holding column c: the largest with srow[e0 + b] <= c
+        while (h2 - l2 > 1) {
+            const int mid = (l2 + h2) >> 1;
+            if (srow[e0 + mid] <= c) l2 = mid;
+            else h2 = mid;
+        }
+        const int j = sidx[e0 + l2], cl = c - srow[e0 + l2];
+        float2 *dst = nullptr;
+        if (j == i) {
+            dst = Ad + doff[i] + (int64_t)cl * ni;
+        } else {
+            const int r = find_row(sptr, sidx, srow, j, i);   // >= 0 when S is the symbolic fill
+            if (r >= 0) dst = A + coff[j] + r + (int64_t)cl * M[j];
+        }
+        s_col[threadIdx.x] = dst;
+    }
+    tc::Acc acc;
+    unsigned char *base = tc::align1024(smraw);
+    acc.planes = base;
+    acc.mbar = &s_mbar;
+    acc.tslot = &s_tslot;
+    acc.open(ni, nc);
+    const float2 *Aik = A + coff[k] + srow[e0 + a];        // n_i x n_k, ld M_k (panel k is not written)
+    const float2 *Wc = W + coff[k] + (int64_t)c0 * nk;     // n_k x nc, ld n_k
+    for (int q0 = 0; q0 < nk; q0 += tc::KC) {
+        const int kl = min(tc::KC, nk - q0);
+        acc.wait(err, bound);   // the previous chunk's MMAs have read the planes
+        for (int e = threadIdx.x; e < ni * kl; e += blockDim.x) {
+            const int r = e % ni, q = e / ni;
+            acc.put_a(r, q, Aik[r + (int64_t)(q0 + q) * Mk]);
+        }
+        for (int e = threadIdx.x; e < kl * nc; e += blockDim.x) {
+            const int q = e % kl, c = e / kl;
+            acc.put_b(c, q, Wc[(q0 + q) + (int64_t)c * nk]);
+        }
+        acc.zero_pad(kl);
+        acc.issue(kl);
+    }
+    acc.wait(err, bound);
+    float *dsm = (float *)base;
+    if (acc.drain(dsm)) {
+        for (int e = threadIdx.x; e < ni * nc; e += blockDim.x) {
+            const int r = e % ni, c = e / ni;
+            float2 *dst = s_col[c];
+            if (dst) {
+                const float2 v = acc.entry(dsm, r, c);
+                float2 o = dst[r];
+                o.x -= v.x;
+                o.y -= v.y;
+                dst[r] = o;
+            }
+        }
+    }
+    acc.close();
+}
+
 // Column blocks per CTA of the grouped update: the most (up to 8) that still leaves at least
 // four CTAs per SM.
 static int upd_group(int ns, int nsm)
@@ -479,6 +564,26 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
     if ((e = cudaFuncSetAttribute(k_update_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UPD_SMEM))) return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    if (sizeof(S) == 8 && h->update_kind == 2) {
+        if (!h->d_ucum) {   // tensor-core update tasks: per row a of S_k, 64-column pieces of W_k
+            std::vector<int> uc(std::max<size_t>(P.sidx.size(), 1));
+            h->utot.assign(P.nb, 0);
+            for (int k = 0; k < P.nb; ++k) {
+                int c = 0;
+                for (int x = P.sptr[k]; x < P.sptr[k + 1]; ++x) {
+                    uc[x] = c;
+                    c += (P.srow[x] + P.size[P.sidx[x]] + 63) / 64;
+                }
+                h->utot[k] = c;
+            }
+            if ((e = h->arena.alloc((void **)&h->d_ucum, sizeof(int) * uc.size())) ||
+                (e = cudaMemcpyAsync(h->d_ucum, uc.data(), sizeof(int) * uc.size(), cudaMemcpyHostToDevice, st)) ||
+                (e = cudaStreamSynchronize(st)))
+                return e;
+        }
+        if ((e = cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES)))
+            return e;
+    }
     for (int k = 0; k < P.nb; ++k) {
         int nk = P.size[k];
         HM_LAUNCH(h, K_PIVOT,
@@ -492,6 +597,14 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
                                                                           DinvS, A, W));
             if (h->opts.compress_in_setup && (e = compress_step<S>(h, k, W))) return e;
             if constexpr (sizeof(S) == 8) {
+                if (h->update_kind == 2) {
+                    HM_LAUNCH(h, K_UPDATE,
+                              k_update_tc<<<(unsigned)h->utot[k], 256, tc::SMEM_BYTES, st>>>(
+                                  k, ns, h->d_ucum, h->d_size, h->d_sptr, h->d_sidx, h->d_srow, h->d_M, h->d_coff,
+                                  h->d_doff, W, A, Ad, h->d_err, WAIT_NS_DEFAULT));
+                    if ((e = cudaGetLastError())) return e;
+                    continue;
+                }
                 const int gb = upd_group(ns, nsm);
                 HM_LAUNCH(h, K_UPDATE,
                           k_update_grp<<<(unsigned)upd_first(ns, gb), 256, UPD_SMEM, st>>>(
@@ -511,6 +624,7 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
     if ((e = cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st))) return e;
     if ((e = cudaStreamSynchronize(st))) return e;
     if (herr == 0x7fffffff) return cudaErrorInvalidValue;   // plan / pattern mismatch
+    if (herr == ERR_TIMEOUT) return cudaErrorLaunchTimeout;   // a tensor-core wait gave up
     if (herr > 0) *bad_block = herr - 1;
     return cudaSuccess;
 }

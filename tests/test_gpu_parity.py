@@ -175,6 +175,35 @@ def test_mixed_factors_close_to_fp64(cfg1, cfg1_mixed):
         assert rel(D, F.D[k]) < 1e-4, k
 
 
+def test_update_schedules_match(cfg1, sphere1920):
+    """The complex-FP32 Schur updates on the CUDA cores (kind 1) and on the tensor cores (kind 2,
+    3xTF32): every D_k, D_k^{-1} and panel W_k within FP32 rounding of the oracle's FP64 factors
+    and of each other, and each kind's setup bitwise reproducible."""
+    P, order, F, S, h = cfg1
+    got = {}
+    for kind in (1, 2, 2):
+        g = hm.hmat_create(sphere1920, ordering=1, precision=1)
+        hm.hmsolve.hm_set_update_schedule(g, kind)
+        hm.precond_setup(g)
+        blocks = []
+        for k in range(F.nb):
+            nk = int(F.size[k])
+            D = hm.hm_get_block(g, 0, k, (nk, nk))
+            assert rel(D, F.D[k]) < 1e-4, (kind, k)
+            blocks.append(D)
+            if F.S[k]:
+                M = int(sum(F.size[j] for j in F.S[k]))
+                Wk = hm.hm_get_block(g, 2, k, (nk, M))
+                Wo = np.concatenate([F.W[(k, j)] for j in F.S[k]], axis=1)
+                assert rel(Wk, Wo) < 1e-3, (kind, k)
+                blocks.append(Wk)
+        if kind in got:
+            assert all(np.array_equal(x, y) for x, y in zip(blocks, got[kind]))
+        got[kind] = blocks
+        hm.hmat_destroy(g)
+    assert max(rel(x, y) for x, y in zip(got[1], got[2])) < 1e-3
+
+
 def test_mixed_solution_error_against_tight_oracle(cfg1, cfg1_mixed, cfg1_tight):
     """The FP64 refinement loop stops on the true residual ||V - Z I||/||V||; at 1e-5 (the
     setting the benchmark uses for its 1e-4 error bar) the solution is within 1e-4 of the
