@@ -243,8 +243,7 @@ int hm_get_profile_cols(hm_handle h, int32_t cls, int64_t *cols);
  * column-major, ld = n, not overlapping.  Scratch is one static 16 MiB device array
  * (1,048,576 complex doubles) held by every GPU that loads the library until exit; a call
  * needing more than n*nrhs + 2*sum(rank)*nrhs entries of it returns HM_EINVAL.  The first
- * call on a device looks up the array's device address: make it before any stream capture.
- * The address is cached per device for the life of the process and belongs to the device's
+ * call on a device looks up the array's device address.  The address is cached per device for the life of the process and belongs to the device's
  * primary context as the first call found it: after cudaDeviceReset the library must be
  * unloaded and loaded again before this call is used.  All calls share the array, so calls that overlap on the GPU race and must be serialised.
  * Synchronises the handle's stream before returning.

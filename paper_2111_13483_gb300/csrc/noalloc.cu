@@ -17,10 +17,9 @@
 //
 // Set-up: host code must not use the array's name as a device address (on the host it
 // names a host-side stand-in).  The first call on each device, with that device current,
-// asks the runtime for the array's device address (cudaGetSymbolAddress) and caches it; make
-// that first call on a device before any stream capture starts.  The cached address belongs
-// to the device's primary context as the first call found it; a caller that resets the
-// device (cudaDeviceReset) must reload the library before calling again.
+// asks the runtime for the array's device address (cudaGetSymbolAddress) and caches it.  The
+// cached address belongs to the device's primary context as the first call found it; a caller
+// that resets the device (cudaDeviceReset) must reload the library before calling again.
 #include <mutex>
 
 #include "hm_internal.h"
