@@ -215,3 +215,23 @@ def test_large_blocks_are_tiled(H, sphere1920):
     assert np.array_equal(S, S.T)
     iu = np.triu_indices(200)
     assert np.max(np.abs(S[iu] - Sr[iu])) <= 1e-12 * scale
+
+
+def test_aca_ranks_above_64_recompressed_in_global_scratch(H, sphere1920):
+    """Blocks of neighbouring clusters at tight eps need ACA ranks above 64 (the cores then take
+    the global-scratch re-compression): the stored blocks stay within 10 eps of the exact ones."""
+    P = sphere1920
+    perm = P.perm
+    rows = [perm[0:300], perm[0:300], perm[300:700]]
+    cols = [perm[300:600], perm[600:900], perm[700:1100]]
+    exact, eoff = _ev(P).blocks(rows, cols)
+    seen = []
+    for eps in (1e-6, 1e-8):
+        rank, uoff, voff, U, V = H.hm_efie_far(_mesh(H, P), rows, cols, eps)
+        for b in range(len(rows)):
+            m, n = len(rows[b]), len(cols[b])
+            A = exact[eoff[b]:eoff[b + 1]].reshape(n, m).T
+            Ab = _expand(rank, uoff, voff, U, V, m, n, b)
+            assert np.linalg.norm(Ab - A) <= 10 * eps * np.linalg.norm(A), (eps, b, rank[b])
+            seen.append(int(rank[b]))
+    assert max(seen) > 64, seen
