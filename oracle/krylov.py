@@ -87,6 +87,12 @@ class System:
                 v[lp[s]:lp[s + 1]] += B.T @ u[lp[t]:lp[t + 1]]
         return v
 
+    def Z_new(self, x):
+        """Z x in the new (block) order: near blocks as stored plus the far factors."""
+        u = np.zeros(x.shape, dtype=np.complex128)
+        u[self.new2cl] = x
+        return (self.near_cluster(u) + self.far_cluster(u))[self.new2cl]
+
     def Z_orig(self, x_orig):
         """Z x in the original RWG order (near blocks + far factors)."""
         perm = np.asarray(self.prob.perm)
@@ -157,10 +163,28 @@ class BlockJacobi(System):
         v = self.split(x)
         return self.join([sla.lu_solve(self.lu[k], v[k]) for k in range(self.F.nb)])
 
-    def Z_new(self, x):
-        u = np.zeros(x.shape, dtype=np.complex128)
-        u[self.new2cl] = x
-        return (self.near_cluster(u) + self.far_cluster(u))[self.new2cl]
+    def apply_A(self, x):
+        return self.M_solve(self.Z_new(x))
+
+    def rhs(self, b_orig):
+        return self.M_solve(self.to_new(b_orig))
+
+    def solution(self, xt):
+        return self.to_orig(xt)
+
+
+class NullField(System):
+    """The null-field comparison preconditioner, as read here (Sec. 3: the near field scaled
+    to diagonal blocks from one side, the fill-in blocks ignored): the elimination of
+    ``schur.setup`` restricted to the near-field pattern (``drop_fill``), M = L D L^T, and
+    GMRES on M^{-1} Z x = M^{-1} b with M^{-1} = L^{-T} D^{-1} L^{-1} (left preconditioned,
+    the same GMRES as for Eq. 28, x~ = x)."""
+
+    def __init__(self, prob, order):
+        super().__init__(prob, _schur.setup(prob, order, fill_tol=0.0, drop_fill=True))
+
+    def M_solve(self, x):
+        return self.LT_inv(self.D_solve(self.L_inv(x)))
 
     def apply_A(self, x):
         return self.M_solve(self.Z_new(x))

@@ -18,6 +18,12 @@ Notation (blocks numbered 0..nb-1 in the ordering of Algorithm 1, n_k unknowns e
   rank r whose singular-value tail has Frobenius norm <= fill_tol * ||W_kj||_F, kept
   dense when r (n_k + n_j) >= n_k n_j.  Reading taken: compression acts on the stored
   coefficients used by the sweeps, not on the blocks that feed later Schur updates.
+* Null-field comparison (Sec. 1 and Sec. 5.2 name it; Sec. 3 says it scales the near field
+  to diagonal blocks from one side while ignoring the fill-in blocks).  Reading taken: the
+  same block elimination restricted to the near-field pattern, every update whose target
+  block is not a near-field pair dropped (a block incomplete factorisation with no fill),
+  so that Z_N ~ M = L D L^T with M equal to Z_N on every near-field block pair; the
+  preconditioner M^{-1} = L^{-T} D^{-1} L^{-1} is applied from the left.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -41,6 +47,15 @@ def symbolic_fill(nb, pairs):
                 if a != b:
                     adj[a].add(b)
     return S
+
+
+def near_lists(nb, pairs):
+    """S_k without fill: the later blocks that are near-field neighbours of k."""
+    S = [set() for _ in range(nb)]
+    for i, j in pairs:
+        if i != j:
+            S[min(i, j)].add(max(i, j))
+    return [sorted(x) for x in S]
 
 
 class Factor:
@@ -67,7 +82,7 @@ def near_blocks_in_order(prob, order):
     return A
 
 
-def setup(prob, order, fill_tol=1e-2, max_steps=None, compress_in_setup=False):
+def setup(prob, order, fill_tol=1e-2, max_steps=None, compress_in_setup=False, drop_fill=False):
     """The preconditioner of Sec. 3 for block order ``order`` (Algorithm 1 output).
     ``max_steps`` stops after that many elimination steps (a timing sample; the factor is
     then incomplete and only its first steps are valid).
@@ -77,12 +92,15 @@ def setup(prob, order, fill_tol=1e-2, max_steps=None, compress_in_setup=False):
     the sweeps use the truncations.  ``compress_in_setup`` (the abstract's "compressing the
     fill-in blocks in preconditioner computation"): at elimination step k the fill-in blocks
     W_kj of the new panel are truncated as soon as they are formed, and the Schur updates of
-    that step (and so every later pivot block and panel) use the truncations."""
+    that step (and so every later pivot block and panel) use the truncations.
+
+    ``drop_fill`` (the null-field reading): S_k = the later near-field neighbours of k, and an
+    update A_ij -= A_ik W_kj whose target (i, j) is not a near-field pair is not made."""
     nb = len(order)
     size = np.array([prob.leaf_ptr[order[p] + 1] - prob.leaf_ptr[order[p]] for p in range(nb)], dtype=np.int64)
     A = near_blocks_in_order(prob, order)
     near_pairs = set(A.keys())
-    S = symbolic_fill(nb, list(A.keys()))
+    S = near_lists(nb, list(A.keys())) if drop_fill else symbolic_fill(nb, list(A.keys()))
     F = Factor()
     F.order, F.size, F.S, F.nb = np.asarray(order), size, S, nb
     F.near_pairs = near_pairs
@@ -105,7 +123,7 @@ def setup(prob, order, fill_tol=1e-2, max_steps=None, compress_in_setup=False):
                 upd = Aik @ Wk[j]
                 if (i, j) in A:
                     A[(i, j)] = A[(i, j)] - upd
-                else:
+                elif not drop_fill:
                     A[(i, j)] = -upd
         for j in S[k]:
             del A[(j, k)]

@@ -379,6 +379,90 @@ def test_block_jacobi_exact_on_block_diagonal_systems():
     assert np.linalg.norm(x - np.linalg.solve(Z, b)) / np.linalg.norm(x) < 1e-12
 
 
+# ---- null-field comparison preconditioner (Sec. 3: one-sided near-field scaling without fill) ----
+def _cycle(rng, far=None):
+    """Five blocks on a cycle 0-1-2-3-4-0: eliminating block 0 couples 1 and 4, which are not
+    near-field neighbours, so the complete elimination fills (1, 4) and later pairs."""
+    sizes = [3, 5, 4, 2, 6]
+    pairs = [(t, t) for t in range(5)] + [(0, 1), (1, 2), (2, 3), (3, 4), (0, 4)]
+    return block_problem(sizes, pairs, rng, far=far, diag_boost=6.0)
+
+
+def _near_block_mask(F, near_pairs):
+    off = np.concatenate([[0], np.cumsum(F.size)])
+    n = int(off[-1])
+    mask = np.zeros((n, n), dtype=bool)
+    for i in range(F.nb):
+        for j in range(F.nb):
+            if i == j or (max(i, j), min(i, j)) in near_pairs:
+                mask[off[i]:off[i + 1], off[j]:off[j + 1]] = True
+    return mask
+
+
+def test_null_field_factor_is_the_incomplete_factorisation_of_the_near_pattern():
+    """The elimination without fill is characterised without reference to its algorithm: L is
+    unit lower triangular with blocks only on near-field pairs, D is block diagonal, and
+    M = L D L^T equals Z_N on every near-field block pair (these equations have one solution).
+    Off the pattern M differs from Z_N, which the complete factorisation reproduces exactly."""
+    rng = np.random.default_rng(41)
+    p, Z, ZF = _cycle(rng)
+    for order in (np.arange(5), np.array([2, 0, 4, 1, 3])):
+        S = krylov.NullField(p, order)
+        F = S.F
+        assert F.S == schur.near_lists(5, list(F.near_pairs))
+        Zn = Z[np.ix_(S.new2orig, S.new2orig)]
+        L, D = schur.ldlt_dense(F)
+        mask = _near_block_mask(F, F.near_pairs)
+        assert np.all(L[~mask] == 0) and np.allclose(np.diag(L), 1) and np.all(np.triu(L, 1) == 0)
+        M = L @ D @ L.T
+        assert np.abs(M - Zn)[mask].max() < 1e-12 * np.abs(Zn).max()
+        assert np.abs(M - Zn)[~mask].max() > 1e-3 * np.abs(Zn).max()
+        Fc = schur.setup(p, order, fill_tol=0.0)
+        Lc, Dc = schur.ldlt_dense(Fc)
+        assert np.abs(Lc @ Dc @ Lc.T - Zn).max() < 1e-12 * np.abs(Zn).max()
+
+
+def test_null_field_equals_the_schur_factor_when_the_pattern_has_no_fill():
+    """A block-tridiagonal near field in its natural order has no fill-in: the two
+    eliminations coincide, M = Z_N, so with no far field GMRES ends after one step."""
+    rng = np.random.default_rng(42)
+    sizes = [4, 3, 5, 2]
+    pairs = [(t, t) for t in range(4)] + [(0, 1), (1, 2), (2, 3)]
+    p, Z, ZF = block_problem(sizes, pairs, rng, diag_boost=6.0)
+    order = np.arange(4)
+    S = krylov.NullField(p, order)
+    Fc = schur.setup(p, order, fill_tol=0.0)
+    assert S.F.S == Fc.S
+    for k in range(4):
+        assert np.array_equal(S.F.D[k], Fc.D[k])
+    for key in Fc.W:
+        assert np.array_equal(S.F.W[key], Fc.W[key])
+    b = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    x, it, rr, ok = krylov.solve(S, b, tol=1e-12, restart=10)
+    assert ok and it == 1
+    assert np.linalg.norm(x - np.linalg.solve(Z, b)) / np.linalg.norm(x) < 1e-12
+
+
+def test_null_field_operator_is_dense_M_inverse_Z_and_solves():
+    """M^{-1} (Z_N + Z_F) against a dense solve with the (pinned) M, and a tight solve of the
+    full system."""
+    rng = np.random.default_rng(43)
+    far = [((1, 3), 0.3 * (rng.standard_normal((5, 2)) + 1j * rng.standard_normal((5, 2))))]
+    p, Z, ZF = _cycle(rng, far=far)
+    order = np.array([2, 0, 4, 1, 3])
+    S = krylov.NullField(p, order)
+    L, D = schur.ldlt_dense(S.F)
+    P = np.eye(Z.shape[0])[S.new2orig]            # P x_orig = x_new
+    M = P.T @ (L @ D @ L.T) @ P                   # M in the original order
+    x = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    ref = np.linalg.solve(M, (Z + ZF) @ x)
+    assert np.linalg.norm(S.to_orig(S.apply_A(S.to_new(x))) - ref) / np.linalg.norm(ref) < 1e-12
+    b = rng.standard_normal(Z.shape[0]) + 1j * rng.standard_normal(Z.shape[0])
+    assert np.linalg.norm(S.rhs(b) - S.to_new(np.linalg.solve(M, b))) < 1e-12 * np.linalg.norm(b)
+    xs, it, rr, ok = krylov.solve(S, b, tol=1e-13, restart=30)
+    assert ok and np.linalg.norm(xs - np.linalg.solve(Z + ZF, b)) / np.linalg.norm(xs) < 1e-11
+
+
 # ---- Sec. 3.4 read as compression during the setup (the abstract's reading) ---------------------
 def test_compression_in_setup_changes_exactly_the_later_updates():
     """Star 0-1, 0-2: eliminating block 0 couples 1 and 2, so W_12 is a fill-in block.  With
