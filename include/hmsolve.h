@@ -95,6 +95,13 @@ typedef struct {
  *              preconditioner of Sec. 1, a comparison): GMRES on M^{-1} Z x = M^{-1} b with
  *              the same engine, no coefficients, blocks in the ordering's order; precision 0
  *              only (HM_EINVAL otherwise);
+ *              2 = null field, the one-sided comparison of Sec. 3 and Sec. 5.2 as read here:
+ *              the elimination of Sec. 3.1 restricted to the near-field pattern (S_k = the
+ *              later near-field neighbours of k; an update whose target block is not a
+ *              near-field pair is dropped), M = L D L^T, and GMRES on M^{-1} Z x = M^{-1} b
+ *              with M^{-1} = L^{-T} D^{-1} L^{-1} applied from the left (x~ = x); no fill-in
+ *              blocks, so fill_tol has nothing to compress; precision 0 only (HM_EINVAL
+ *              otherwise);
  *   compress_in_setup  with fill_tol > 0: 0 = the fill-in coefficient blocks are truncated once
  *              the elimination is complete and only the sweeps use the truncations; 1 = each is
  *              truncated as soon as its elimination step forms it, so that the Schur updates of
@@ -203,7 +210,9 @@ int hm_get_fill_ranks(hm_handle h, int32_t *rank);
 
 /*
  * Applies one operator to nrhs device vectors (solve order, column-major, ld = n):
- *   op 0: y = A x   with A = D^{-1}[D + L^{-1} Z_F L^{-T}]  (Eq. 28, paper form);
+ *   op 0: y = A x   with A = D^{-1}[D + L^{-1} Z_F L^{-T}]  (Eq. 28, paper form); for the
+ *         comparison preconditioners A = M^{-1} Z (block Jacobi: M^{-1} = D^{-1}, ops 1 and
+ *         2 copy; null field: M^{-1} = L^{-T} D^{-1} L^{-1});
  *   op 1: y = L^{-1} x     (Eq. 23, the left scalings);
  *   op 2: y = L^{-T} x     (Eq. 24, the right scalings);
  *   op 3: y = Z_F x        (far field, Eq. 11);

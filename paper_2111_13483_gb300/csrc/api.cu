@@ -153,9 +153,9 @@ int hmat_create(const hm_desc *d, const hm_opts *opts, hm_handle *out)
     else hm_default_opts(&h->opts);
     int st;
     if (h->opts.ordering < 0 || h->opts.ordering > 2 || h->opts.fill_tol < 0 || h->opts.precision < 0 ||
-        h->opts.precision > 1 || h->opts.preconditioner < 0 || h->opts.preconditioner > 1 ||
+        h->opts.precision > 1 || h->opts.preconditioner < 0 || h->opts.preconditioner > 2 ||
         h->opts.compress_in_setup < 0 || h->opts.compress_in_setup > 1 ||
-        (h->opts.preconditioner == 1 && h->opts.precision != 0)) {
+        (h->opts.preconditioner != 0 && h->opts.precision != 0)) {
         delete h;
         return HM_EINVAL;
     }

@@ -289,6 +289,7 @@ struct Engine {
     hm_ctx *h = nullptr;
     int S = 0, m = 0, n = 0, nchunk = 0;
     bool fp32 = false;
+    bool left = false;   // preconditioner applied from the left only (null field): x = x~
     // per-slot vectors (slot stride n): V, I (original order), FP64 residual, c and x~ (solve order)
     double2 *B = nullptr, *XO = nullptr, *R = nullptr, *C = nullptr, *XT = nullptr;
     double2 *Vb = nullptr;                   // Krylov basis: vector i of slot c at (i*S + c) * n
@@ -321,6 +322,7 @@ struct Engine {
         n = h->plan.n;
         nchunk = (n + DOT_CHUNK - 1) / DOT_CHUNK;
         fp32 = h->opts.precision == 1;
+        left = h->opts.preconditioner == 2;
         sl.assign(S, Slot());
         cudaError_t e;
         auto A = [&](void **p, size_t b) {
@@ -433,7 +435,10 @@ struct Engine {
         const int *id = upload(E);
         cudaError_t e;
         vec(0, k, ref(XT, id), ref(XT, id), packed(PX));
-        if ((e = op(2, PX, PY, k)) || (e = to_orig_order(h, PY, PT, n, k))) return e;
+        if (left) {   // x = x~
+            if ((e = to_orig_order(h, PX, PT, n, k))) return e;
+        } else if ((e = op(2, PX, PY, k)) || (e = to_orig_order(h, PY, PT, n, k)))
+            return e;
         vec(fp32 ? 2 : 0, k, packed(PT), packed(PT), ref(XO, id));
         for (int c : E) {
             Slot &z = sl[c];
@@ -449,6 +454,7 @@ struct Engine {
     }
 
     // start (FP64) or continue (mixed) the refinement: residual, stopping test, c = D^{-1} L^{-1} r
+    // (null field: c = L^{-T} D^{-1} L^{-1} r)
     cudaError_t outer(const std::vector<int> &O)
     {
         cudaError_t e;
@@ -503,7 +509,8 @@ struct Engine {
         const int k = (int)go.size();
         const int *id = upload(go);
         vec(0, k, ref(fp32 ? R : B, id), ref(B, id), packed(PX));
-        if ((e = to_solve_order(h, PX, n, PY, k)) || (e = op(1, PY, PT, k)) || (e = op(4, PT, PX, k))) return e;
+        if ((e = to_solve_order(h, PX, n, PY, k)) || (e = op(1, PY, PT, k))) return e;
+        if (left ? ((e = op(4, PT, PY, k)) || (e = op(2, PY, PX, k))) : (bool)(e = op(4, PT, PX, k))) return e;
         vec(0, k, packed(PX), packed(PX), ref(C, id));
         vec(3, k, packed(PX), packed(PX), ref(XT, id));
         norms(k, ref(C, id), tmp, id);

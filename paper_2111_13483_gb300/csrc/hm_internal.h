@@ -256,7 +256,7 @@ void plan_far(hm_ctx *h);
 std::vector<int> rcm_order(int nl, const std::vector<int> &t, const std::vector<int> &s);
 std::vector<int> sloan_order(int nl, const std::vector<int> &t, const std::vector<int> &s);
 void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &pj, std::vector<int> &sptr,
-                   std::vector<int> &sidx);
+                   std::vector<int> &sidx, bool closure = true);
 
 // kernels (setup.cu / solve.cu): return cudaError_t of the launches
 cudaError_t setup_run(hm_ctx *h, int *bad_block);

@@ -1731,6 +1731,18 @@ static cudaError_t op_chain(hm_ctx *h, const OpData<T> &d, int op, const T *x, T
             default: break;
             }
         }
+        if (h->opts.preconditioner == 2 && op == 0) {
+            // null-field comparison: A x = M^{-1} (Z_N + Z_F) x, M^{-1} = L^{-T} D^{-1} L^{-1}
+            // with the factors of the elimination without fill
+            if ((e = far_apply<T>(h, d, x, w1, nrhs, w2))) return e;   // w2: cluster-order copy of x
+            HM_LAUNCH(h, K_NEAR,
+                      k_near_mv<<<h->nl, 128, 0, h->stream>>>(h->nl, h->d_leaf_ptr, h->d_nptr, h->d_nent, h->d_near_t,
+                                                              h->d_near_s, h->d_near_off, h->d_near, w2, h->d_cl2new,
+                                                              n, nrhs, w1));
+            if ((e = sweep<T>(h, d, true, w1, w0, nrhs))) return e;
+            if ((e = diag<T>(h, d, 1, w0, (const T *)nullptr, w1, nrhs))) return e;
+            return sweep<T>(h, d, false, w1, y, nrhs);
+        }
     }
     switch (op) {
     case 0:   // A x = D^{-1} [D x + L^{-1} Z_F L^{-T} x]

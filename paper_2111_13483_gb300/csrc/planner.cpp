@@ -296,9 +296,10 @@ std::vector<int> sloan_order(int nl, const std::vector<int> &t, const std::vecto
 
 // Symbolic elimination on bitsets (Sec. 3.3, the fill of Figs. 3b-7b): eliminating block
 // k couples every pair of its later neighbours.  Pairs (i, j) in block numbering; returns
-// S_k (sorted, > k) as CSR.
+// S_k (sorted, > k) as CSR.  closure = false: S_k = the later near-field neighbours of k only
+// (the elimination without fill of the null-field comparison).
 void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &pj, std::vector<int> &sptr,
-                   std::vector<int> &sidx)
+                   std::vector<int> &sidx, bool closure)
 {
     const int W = (nl + 63) / 64;
     std::vector<uint64_t> bits((size_t)nl * W, 0);
@@ -326,10 +327,11 @@ void symbolic_fill(int nl, const std::vector<int> &pi, const std::vector<int> &p
                 x &= x - 1;
             }
         }
-        for (int a : later) {
-            uint64_t *ra = &bits[(size_t)a * W];
-            for (int w = k / 64; w < W; ++w) ra[w] |= mask[w];
-        }
+        if (closure)
+            for (int a : later) {
+                uint64_t *ra = &bits[(size_t)a * W];
+                for (int w = k / 64; w < W; ++w) ra[w] |= mask[w];
+            }
         sidx.insert(sidx.end(), later.begin(), later.end());
         sptr[k + 1] = (int)sidx.size();
     }
@@ -442,20 +444,22 @@ void plan_order(hm_ctx *h)
         bj[b] = P.pos[h->near_s[b]];
         P.bandwidth = std::max(P.bandwidth, std::abs(bi[b] - bj[b]));
     }
-    symbolic_fill(nl, bi, bj, P.sptr, P.sidx);
+    const bool no_fill = h->opts.preconditioner == 2;
+    symbolic_fill(nl, bi, bj, P.sptr, P.sidx, !no_fill);
+    // near pairs (i > j) as keys i * nl + j, sorted
+    std::vector<int64_t> nkey;
+    nkey.reserve(bi.size());
+    for (size_t b = 0; b < bi.size(); ++b)
+        if (bi[b] != bj[b]) nkey.push_back((int64_t)std::max(bi[b], bj[b]) * nl + std::min(bi[b], bj[b]));
+    std::sort(nkey.begin(), nkey.end());
     {
         // entries of the coefficient pattern that are not near pairs: the fill-in blocks
-        std::vector<int64_t> nk;
-        nk.reserve(bi.size());
-        for (size_t b = 0; b < bi.size(); ++b)
-            if (bi[b] != bj[b]) nk.push_back((int64_t)std::max(bi[b], bj[b]) * nl + std::min(bi[b], bj[b]));
-        std::sort(nk.begin(), nk.end());
         P.fill_e.clear();
         P.fill_k.clear();
         P.fill_ptr.assign(nl + 1, 0);
         for (int k = 0; k < nl; ++k) {
             for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e)
-                if (!std::binary_search(nk.begin(), nk.end(), (int64_t)P.sidx[e] * nl + k)) {
+                if (!std::binary_search(nkey.begin(), nkey.end(), (int64_t)P.sidx[e] * nl + k)) {
                     P.fill_e.push_back(e);
                     P.fill_k.push_back(k);
                 }
@@ -490,7 +494,17 @@ void plan_order(hm_ctx *h)
         double run = 0;
         for (int e = P.sptr[k]; e < P.sptr[k + 1]; ++e) {
             run += P.size[P.sidx[e]];
-            macs += (double)P.size[P.sidx[e]] * nk * run;
+            if (!no_fill) {
+                macs += (double)P.size[P.sidx[e]] * nk * run;
+                continue;
+            }
+            // without fill only the updates of near pairs (and of the diagonal blocks) are made
+            const int i = P.sidx[e];
+            for (int f = P.sptr[k]; f <= e; ++f) {
+                const int j = P.sidx[f];
+                if (i == j || std::binary_search(nkey.begin(), nkey.end(), (int64_t)i * nl + j))
+                    macs += (double)P.size[i] * (double)P.size[k] * P.size[j];
+            }
         }
     }
     P.setup_flops = 8.0 * macs;

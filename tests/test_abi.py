@@ -132,6 +132,17 @@ def test_create_rejects_malformed_descriptions(hm, breakage):
     assert ei.value.code == hm.HM_EINVAL
 
 
+@pytest.mark.parametrize("opts", [dict(preconditioner=3), dict(preconditioner=-1), dict(preconditioner=1, precision=1),
+                                  dict(preconditioner=2, precision=1), dict(ordering=3), dict(precision=2),
+                                  dict(fill_tol=-1.0), dict(compress_in_setup=2)])
+def test_create_rejects_bad_options(hm, opts):
+    """Option values outside their ranges, and the comparison preconditioners (block Jacobi,
+    null field) with the mixed precision, are rejected before any device work."""
+    with pytest.raises(hm.HMError) as ei:
+        hm.hmat_create(_tiny_problem(), **opts)
+    assert ei.value.code == hm.HM_EINVAL
+
+
 @pytest.mark.parametrize("breakage", ["row_index", "col_index", "empty_block", "mirror", "triangle", "free_vertex",
                                       "wavenumber", "eps"])
 def test_efie_calls_reject_bad_arguments_before_any_device_work(hm, breakage):

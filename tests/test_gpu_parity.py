@@ -486,6 +486,50 @@ def test_block_jacobi_matches_oracle(which, request):
         hm.precond_setup(hm.hmat_create(P, ordering=1, preconditioner=1, precision=1))
 
 
+# ---- null field (the one-sided comparison of Sec. 3 / Sec. 5.2: elimination without fill) --------
+@pytest.mark.parametrize("which", ["small", "cfg1"])
+def test_null_field_matches_oracle(which, request):
+    P, order, F, S, h = request.getfixturevalue(which)
+    N = krylov.NullField(P, order)
+    g = hm.hmat_create(P, ordering=1, preconditioner=2, fill_tol=1e-2)
+    hm.precond_setup(g)
+    ptr, idx = hm.hm_get_fill(g)
+    assert ptr[-1] < len(hm.hm_get_fill(h)[1])            # the Schur factor of this order fills
+    for k in range(N.F.nb):
+        assert list(idx[ptr[k]:ptr[k + 1]]) == N.F.S[k]
+    assert np.all(hm.hmsolve.hm_get_fill_ranks(g) == -1)   # nothing to compress without fill
+    st = hm.hmat_stats(g)
+    assert st["coef_entries"] == st["coef_entries_dense"]
+    for k in range(N.F.nb):
+        nk = int(N.F.size[k])
+        assert rel(hm.hm_get_block(g, 0, k, (nk, nk)), N.F.D[k]) < 1e-10, k
+        assert rel(hm.hm_get_block(g, 1, k, (nk, nk)), np.linalg.inv(N.F.D[k])) < 1e-9, k
+        if N.F.S[k]:
+            M = int(sum(N.F.size[j] for j in N.F.S[k]))
+            Wo = np.concatenate([N.F.W[(k, j)] for j in N.F.S[k]], axis=1)
+            assert rel(hm.hm_get_block(g, 2, k, (nk, M)), Wo) < 1e-10, k
+    rng = np.random.default_rng(24)
+    X = rng.standard_normal((S.n, 3)) + 1j * rng.standard_normal((S.n, 3))
+    for op, f in ((hm.hmsolve.OP_A, N.apply_A), (hm.hmsolve.OP_DINV, N.D_solve),
+                  (hm.hmsolve.OP_LINV, N.L_inv), (hm.hmsolve.OP_LTINV, N.LT_inv)):
+        dy = torch.empty_like(_dev(X))
+        hm.hm_apply(g, op, _dev(X), dy)
+        Y = _host(dy)
+        for c in range(3):
+            assert rel(Y[:, c], f(X[:, c])) < 1e-10, (op, c)
+    b = P.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
+    x, it, rr, code = hm.solve(g, b, tol=1e-6, restart=30, maxit=3000)
+    xo, ito, rro, ok = krylov.solve(N, b, tol=1e-6, restart=30, maxit=3000)
+    assert code == 0 and ok and abs(int(it[0]) - ito) <= 1
+    assert rel(x, xo) <= 1e-8
+    # a column in a batch gives the bits of its solo solve
+    B = np.stack([b, P.plane_wave([1.0, 0.0, 0.0], [0.0, 0.0, 1.0])], axis=1)
+    xb, itb, rrb, codeb = hm.solve(g, B, tol=1e-6, restart=30, maxit=3000)
+    assert np.array_equal(xb[:, 0], x) and int(itb[0]) == int(it[0])
+    with pytest.raises(hm.HMError):
+        hm.hmat_create(P, ordering=1, preconditioner=2, precision=1)
+
+
 # ---- Sec. 3.4, compression during the setup (the abstract's reading) -----------------------------
 def test_compression_in_setup_matches_oracle(sphere1920):
     P = sphere1920
