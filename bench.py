@@ -120,6 +120,13 @@ def parse():
                     help="sweep schedule 'groups,kind[,tile]' for --profile-op (0,0 = tuned)")
     ap.add_argument("--update-schedule", type=int, default=0,
                     help="complex-FP32 Schur updates for --profile-op: 1 CUDA cores, 2 tensor cores, 0 default")
+    ap.add_argument("--pivot-schedule", type=int, default=0,
+                    help="CTAs per FP64 pivot inversion in every setup of the run: 1, or a cluster of 2, 4 "
+                         "or 8; 0 = the library default")
+    ap.add_argument("--profile-setup", type=int, default=0,
+                    help="profiling case: run precond_setup this many times on the workload (--precision, "
+                         "--fill-tol, --pivot-schedule, --update-schedule), print each setup's device ms "
+                         "and the last one's per-class ms, and exit; no bench line")
     ap.add_argument("--far-schedule", type=int, default=0,
                     help="complex-FP32 far-field kind for --profile-op: 1 CUDA cores, 2 tensor cores, 0 default")
     return ap.parse_args()
@@ -618,6 +625,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision, device=local,
                        stream=stream.cuda_stream)
+    hm.hmsolve.hm_set_pivot_schedule(h, args.pivot_schedule)
     stats = hm.hmat_stats(h)
     dV = torch.from_numpy(np.ascontiguousarray(Vh.T)).to("cuda")
     dI = torch.zeros_like(dV)
@@ -703,6 +711,7 @@ def run_ours(args):
             ft64 = args.fill_tol if args.fp64_fill_tol is None else args.fp64_fill_tol
             g = hm.hmat_create(P, ordering=args.ordering, fill_tol=ft64, precision=0, device=local,
                                stream=stream.cuda_stream)
+            hm.hmsolve.hm_set_pivot_schedule(g, args.pivot_schedule)
             hm.precond_setup(g)           # first call allocates the factors
             hm.precond_setup(g)
             setup64 = hm.hmat_stats(g)["setup_ms"]
@@ -779,6 +788,7 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             g = hm.hmat_create(Q, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision, device=local,
                                stream=stream.cuda_stream)
+            hm.hmsolve.hm_set_pivot_schedule(g, args.pivot_schedule)
             hm.precond_setup(g)
             I, it2, rr2, code = hm.solve(g, Vp.numpy().T, tol=args.tol, restart=args.restart, maxit=5000)
             hm.hmat_destroy(g)
@@ -931,6 +941,29 @@ def run_table7(args):
     print(json.dumps(out), flush=True)
 
 
+def run_profile_setup(args):
+    """Setup timings for one schedule: the device ms of each precond_setup and, for the last,
+    the event-profiler ms per kernel class."""
+    import paper_2111_13483_gb300 as hm
+    P = load_problem(args.workload, 0, 1, args.build)
+    h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision)
+    hm.hmsolve.hm_set_update_schedule(h, args.update_schedule)
+    hm.hmsolve.hm_set_pivot_schedule(h, args.pivot_schedule)
+    ms = []
+    for i in range(args.profile_setup):
+        if i == args.profile_setup - 1:
+            hm.hm_profile(h, 2)
+            hm.hm_profile(h, 1)
+        hm.precond_setup(h)
+        ms.append(hm.hmat_stats(h)["setup_ms"])
+    pr = hm.hm_get_profile(h)
+    hm.hm_profile(h, 0)
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "fill_tol": args.fill_tol,
+                      "pivot_schedule": args.pivot_schedule, "update_schedule": args.update_schedule,
+                      "setup_ms": ms, "class_ms_last": {k: round(v[2], 3) for k, v in pr.items() if v[0]},
+                      "class_launches_last": {k: v[0] for k, v in pr.items() if v[0]}}), flush=True)
+
+
 def run_profile_op(args):
     """A short, deterministic case for ncu captures (no timing of its own)."""
     import torch
@@ -938,6 +971,7 @@ def run_profile_op(args):
     P = load_problem(args.workload, 0, 1, args.build)
     h = hm.hmat_create(P, ordering=args.ordering, fill_tol=args.fill_tol, precision=args.precision)
     hm.hmsolve.hm_set_update_schedule(h, args.update_schedule)
+    hm.hmsolve.hm_set_pivot_schedule(h, args.pivot_schedule)
     hm.precond_setup(h)
     sched = [int(v) for v in args.schedule.split(",")]
     hm.hmsolve.hm_set_sweep_schedule(h, *sched)
@@ -959,6 +993,9 @@ def main():
         return
     if args.profile_op > 0:
         run_profile_op(args)
+        return
+    if args.profile_setup > 0:
+        run_profile_setup(args)
         return
     if args.profile_build:
         import torch

@@ -334,6 +334,17 @@ int hm_set_far_schedule(hm_handle h, int32_t kind);
  */
 int hm_set_update_schedule(hm_handle h, int32_t kind);
 
+/*
+ * How many CTAs invert each pivot block D_k in precond_setup (Sec. 3.1, Eq. 14: the FP64
+ * Gauss-Jordan inverse with partial pivoting that every coefficient panel of step k needs):
+ * 1 = one CTA; 2, 4 or 8 = a thread-block cluster of that many CTAs on as many SMs, each
+ * eliminating a share of the columns, the pivot column passed through distributed shared
+ * memory with one cluster barrier per pivot (same arithmetic per entry: the inverses are bitwise
+ * those of one CTA); 0 = the default (1).  Both precisions; the block-Jacobi setup always uses
+ * one CTA per block.  Takes effect at the next precond_setup.  HM_EINVAL for other values.
+ */
+int hm_set_pivot_schedule(hm_handle h, int32_t ctas);
+
 /* ---- continuous batching (serving) ---------------------------------------------------- */
 
 /*

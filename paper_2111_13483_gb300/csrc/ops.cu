@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "cluster.cuh"
 #include "cplx.cuh"
 #include "hm_internal.h"
 #include "tc.cuh"
@@ -205,49 +206,6 @@ struct CLink {
     unsigned buf;       // shared-window address of the result buffer (same in every CTA)
     unsigned flag;      // shared-window address of the ready word
 };
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ unsigned cluster_rank()
-{
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_size()
-{
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-// every thread of every CTA of the cluster
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n"
-                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ unsigned cluster_map(unsigned a, unsigned rank)
-{
-    unsigned d;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(rank));
-    return d;
-}
-__device__ __forceinline__ unsigned ld_cluster_u32(unsigned a)
-{
-    unsigned v;
-    asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ float2 ld_cluster_f2(unsigned a)
-{
-    float2 v;
-    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
-__device__ __forceinline__ void st_cluster_u32(unsigned a, unsigned v)
-{
-    asm volatile("st.relaxed.cluster.shared::cta.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
 
 // Ys[e] <- entry e of the finished block of cluster CTA `rank` (count entries, its result
 // buffer's layout), once its ready word carries this launch's epoch; a thread with no entry

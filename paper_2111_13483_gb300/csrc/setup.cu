@@ -20,6 +20,7 @@
 // operator) and everything else stays FP32, so no step converts between the two.
 #include <cstdio>
 
+#include "cluster.cuh"
 #include "cplx.cuh"
 #include "hm_internal.h"
 #include "tc.cuh"
@@ -82,6 +83,45 @@ __global__ void k_scatter_near(int n_near, const int *near_t, const int *near_s,
     }
 }
 
+// Pivot search of Gauss-Jordan step c by one warp over rows r >= c of column `col` of a
+// (row-major, leading dimension ld): the largest |a_rc|^2, the lowest row on ties.  The
+// squares are compared as the integer bit patterns of non-negative doubles (same order as
+// the values), which keeps the compares off the slow FP64 pipe.  Lane 0 returns the row p,
+// 1 / pivot in *d, and whether the pivot is singular (|pivot|^2 <= 1e-300 or not finite).
+__device__ __forceinline__ int gj_pivot(const double2 *a, int ld, int col, int c, int n, double2 *d, bool *bad)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long best = 0;
+    int bi = n;
+    for (int r = c + lane; r < n; r += 32) {
+        double2 v = a[r * ld + col];
+        unsigned long long key = (unsigned long long)__double_as_longlong(fma(v.x, v.x, v.y * v.y));
+        if (key > best || (key == best && r < bi) || bi == n) { best = key; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi < n && (ob > best || (ob == best && oi < bi) || bi == n)) { best = ob; bi = oi; }
+    }
+    const double pv = __longlong_as_double((long long)best);
+    *bad = !(pv > 1e-300) || best >= 0x7ff0000000000000ull;
+    const double2 pvv = a[bi * ld + col];
+    *d = make_double2(pvv.x / pv, -pvv.y / pv);
+    return bi;
+}
+
+// Entry (r, j) of Gauss-Jordan step c: row c takes the scaled pivot row rc; column c becomes
+// -f d; every other entry cur - f rc (f = entry r of the pivot column after the interchange,
+// d = 1 / pivot).  Both inverse kernels use these two functions, so their results agree bit
+// for bit.
+__device__ __forceinline__ double2 gj_row(double2 ap, double2 d, bool pivot_col) { return pivot_col ? d : cmul(ap, d); }
+__device__ __forceinline__ double2 gj_entry(bool is_row, bool is_col, double2 rc, double2 f, double2 d, double2 cur)
+{
+    if (is_row) return rc;
+    if (is_col) return make_double2(-(f.x * d.x - f.y * d.y), -(f.x * d.y + f.y * d.x));
+    return make_double2(fma(-f.x, rc.x, fma(f.y, rc.y, cur.x)), fma(-f.x, rc.y, fma(-f.y, rc.x, cur.y)));
+}
+
 // In-place Gauss-Jordan inverse with partial pivoting (largest modulus, lowest row on
 // ties) of D_k = Ad[k], in FP64 whatever S is; result to Dinv[k] (and its FP32 copy when
 // Dinv32 is given).  err <- k+1 on a singular pivot.  Per column: one warp finds the pivot;
@@ -109,30 +149,14 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int kbase, const int *siz
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
-        // Pivot search over rows r >= c by one warp: largest |a_rc|^2, lowest row on ties.
-        // The squares are compared as the integer bit patterns of non-negative doubles
-        // (same order as the values), which keeps the compares off the slow FP64 pipe.
         if (threadIdx.x < 32) {
-            unsigned long long best = 0;
-            int bi = n;
-            for (int r = c + threadIdx.x; r < n; r += 32) {
-                double2 v = a[r * ld + c];
-                unsigned long long key = (unsigned long long)__double_as_longlong(fma(v.x, v.x, v.y * v.y));
-                if (key > best || (key == best && r < bi) || bi == n) { best = key; bi = r; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (oi < n && (ob > best || (ob == best && oi < bi) || bi == n)) { best = ob; bi = oi; }
-            }
+            double2 d;
+            bool bad;
+            const int bi = gj_pivot(a, ld, c, c, n, &d, &bad);
             if (threadIdx.x == 0) {
                 s_p = bi;
                 piv[c] = bi;
-                // singular: |pivot|^2 <= 1e-300 or not finite (exponent bits all ones)
-                const double pv = __longlong_as_double((long long)best);
-                const bool bad = !(pv > 1e-300) || best >= 0x7ff0000000000000ull;
-                double2 pvv = a[bi * ld + c];
-                s_d = make_double2(pvv.x / pv, -pvv.y / pv);   // 1 / pivot
+                s_d = d;
                 if (bad) atomicCAS(err, 0, k + 1);
             }
         }
@@ -142,25 +166,14 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int kbase, const int *siz
         // rows c and p interchanged: the new row c is the old row p
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             const double2 ap = a[p * ld + j];
-            rowc[j] = (j == c) ? d : cmul(ap, d);
+            rowc[j] = gj_row(ap, d, j == c);
             colc[j] = a[(j == p ? c : j) * ld + c];
             if (p != c) a[p * ld + j] = a[c * ld + j];
         }
         __syncthreads();
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const int r = e / n, j = e % n;
-            double2 nv;
-            if (r == c) nv = rowc[j];
-            else {
-                const double2 f = colc[r];
-                if (j == c) nv = make_double2(-(f.x * d.x - f.y * d.y), -(f.x * d.y + f.y * d.x));
-                else {
-                    const double2 cur = a[r * ld + j], rc = rowc[j];
-                    nv.x = fma(-f.x, rc.x, fma(f.y, rc.y, cur.x));
-                    nv.y = fma(-f.x, rc.y, fma(-f.y, rc.x, cur.y));
-                }
-            }
-            a[r * ld + j] = nv;
+            a[r * ld + j] = gj_entry(r == c, j == c, rowc[j], colc[r], d, a[r * ld + j]);
         }
         __syncthreads();
     }
@@ -180,6 +193,105 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int kbase, const int *siz
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int r = e % n, c = e / n;
         const double2 v = a[r * ld + c];
+        out[e] = v;
+        if (out32) out32[e] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// The same inverse on a cluster of CL CTAs (one block per cluster), so that the FP64 pipes of
+// CL SMs share the elimination.  CTA q keeps the columns j = q, q + CL, ... of the in-place
+// array (row-major, n x nloc).  Step c: the CTA that owns column c finds the pivot and
+// stores p, 1 / pivot and the interchanged column c into every CTA of the cluster (two
+// alternating buffers, distributed shared memory), then one cluster barrier; every CTA then
+// interchanges, scales and eliminates its own columns with gj_row / gj_entry, entry for entry
+// the operations of k_pivot_inverse, so the inverse is bitwise the same.  The row
+// interchanges are undone by writing column x of the result from the column the interchanges
+// moved there.  Every CTA takes all n + 1 cluster barriers (a CTA without columns too).
+// Buffer b = c & 1 is rewritten at step c + 2 only after every CTA has passed the barrier of
+// step c + 1, which it reaches after its elimination of step c.
+template <class S, int CL>
+__global__ void __launch_bounds__(128) k_pivot_inverse_cl(int kbase, const int *size, const int64_t *doff, const S *Ad,
+                                                          double2 *Dinv, float2 *Dinv32, int *err)
+{
+    const int q = (int)cluster_rank();
+    const int k = kbase + (int)(blockIdx.x / CL);
+    extern __shared__ double2 sm[];
+    const int n = size[k];
+    const int nloc = (n - q + CL - 1) / CL;    // columns q, q + CL, ... below n
+    const int ld = nloc + 1;
+    double2 *a = sm;                           // n x ld, a[r * ld + jl] = column jl * CL + q
+    double2 *rowc = sm + n * ld;               // nloc: the scaled pivot row
+    __shared__ double2 s_col[2][64];           // pivot column after the interchange (pushed)
+    __shared__ double2 s_d[2];                 // 1 / pivot (pushed)
+    __shared__ int s_p[2];                     // pivot row (pushed)
+    __shared__ int piv[64];
+    __shared__ int at[64];
+    const S *D = Ad + doff[k];
+    for (int e = threadIdx.x; e < n * nloc; e += blockDim.x) {
+        const int r = e % n, jl = e / n;
+        a[r * ld + jl] = cwiden(D[r + (int64_t)(jl * CL + q) * n]);
+    }
+    cluster_sync();   // every CTA of the cluster is running before any remote store
+    for (int c = 0; c < n; ++c) {
+        const int b = c & 1;
+        if (q == c % CL) {
+            const int col = c / CL;
+            __shared__ int o_p;
+            __shared__ double2 o_d;
+            if (threadIdx.x < 32) {
+                double2 d;
+                bool bad;
+                const int bi = gj_pivot(a, ld, col, c, n, &d, &bad);
+                if (threadIdx.x == 0) {
+                    o_p = bi;
+                    o_d = d;
+                    if (bad) atomicCAS(err, 0, k + 1);
+                }
+            }
+            __syncthreads();
+            const int p = o_p;
+            for (int x = threadIdx.x; x < CL * (n + 1); x += blockDim.x) {
+                const int dst = x / (n + 1), r = x % (n + 1);
+                if (r < n)
+                    st_remote_d2(cluster_map(smem_addr(&s_col[b][r]), (unsigned)dst), a[(r == p ? c : r) * ld + col]);
+                else {
+                    st_remote_d2(cluster_map(smem_addr(&s_d[b]), (unsigned)dst), o_d);
+                    st_remote_s32(cluster_map(smem_addr(&s_p[b]), (unsigned)dst), p);
+                }
+            }
+        }
+        cluster_sync();
+        const int p = s_p[b];
+        const double2 d = s_d[b];
+        if (threadIdx.x == 0) piv[c] = p;
+        for (int jl = threadIdx.x; jl < nloc; jl += blockDim.x) {
+            const int j = jl * CL + q;
+            rowc[jl] = gj_row(a[p * ld + jl], d, j == c);
+            if (p != c) a[p * ld + jl] = a[c * ld + jl];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * nloc; e += blockDim.x) {
+            const int r = e / nloc, jl = e % nloc;
+            a[r * ld + jl] = gj_entry(r == c, jl * CL + q == c, rowc[jl], s_col[b][r], d, a[r * ld + jl]);
+        }
+        __syncthreads();
+    }
+    // at[x] = the column of the array that the interchanges (undone last first) move to x
+    if (threadIdx.x == 0) {
+        for (int x = 0; x < n; ++x) at[x] = x;
+        for (int c = n - 1; c >= 0; --c) {
+            const int t = at[c];
+            at[c] = at[piv[c]];
+            at[piv[c]] = t;
+        }
+    }
+    __syncthreads();
+    double2 *out = Dinv + doff[k];
+    float2 *out32 = Dinv32 ? Dinv32 + doff[k] : nullptr;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e % n, x = e / n, src = at[x];
+        if (src % CL != q) continue;
+        const double2 v = a[r * ld + src / CL];
         out[e] = v;
         if (out32) out32[e] = make_float2((float)v.x, (float)v.y);
     }
@@ -540,6 +652,39 @@ static int upd_group(int ns, int nsm)
     return gb;
 }
 
+// one pivot block on a cluster of h->pivot_cl CTAs (2, 4 or 8)
+template <class S>
+static cudaError_t pivot_cluster(hm_ctx *h, int k, int nk, const S *Ad, float2 *Dinv32)
+{
+    const int C = h->pivot_cl;
+    const int nloc = (nk + C - 1) / C;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3(128, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(double2) * ((size_t)nk * (nloc + 1) + nloc);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    const int *sz = h->d_size;
+    const int64_t *dof = h->d_doff;
+    double2 *Dinv = h->d_Dinv;
+    int *err = h->d_err;
+    if (C == 2)
+        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 2>, k, sz, dof, Ad, Dinv, Dinv32, err));
+    else if (C == 4)
+        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 4>, k, sz, dof, Ad, Dinv, Dinv32, err));
+    else
+        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 8>, k, sz, dof, Ad, Dinv, Dinv32, err));
+    if (e) return e;
+    return cudaGetLastError();
+}
+
 template <class S>
 static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *Dinv32, int *bad_block)
 {
@@ -586,9 +731,12 @@ static cudaError_t setup_typed(hm_ctx *h, S *A, S *Ad, S *W, S *DinvS, float2 *D
     }
     for (int k = 0; k < P.nb; ++k) {
         int nk = P.size[k];
-        HM_LAUNCH(h, K_PIVOT,
-                  k_pivot_inverse<S><<<1, 256, sizeof(double2) * (nk * (nk + 1) + 2 * nk), st>>>(
-                      k, h->d_size, h->d_doff, Ad, h->d_Dinv, Dinv32, h->d_err));
+        if (h->pivot_cl > 1) {
+            if ((e = pivot_cluster<S>(h, k, nk, Ad, Dinv32))) return e;
+        } else
+            HM_LAUNCH(h, K_PIVOT,
+                      k_pivot_inverse<S><<<1, 256, sizeof(double2) * (nk * (nk + 1) + 2 * nk), st>>>(
+                          k, h->d_size, h->d_doff, Ad, h->d_Dinv, Dinv32, h->d_err));
         int ns = P.sptr[k + 1] - P.sptr[k];
         if (ns > 0) {
             int Mk = P.M[k];

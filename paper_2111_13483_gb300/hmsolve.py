@@ -62,7 +62,8 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_far_apply_noalloc", "hm_get_fill_ranks", "hm_batch_bytes", "hm_batch_open", "hm_batch_submit",
            "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
            "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm", "hm_plan_order_method",
-           "hm_set_far_schedule", "hm_efie_fill", "hm_efie_far", "hm_set_update_schedule"]
+           "hm_set_far_schedule", "hm_efie_fill", "hm_efie_far", "hm_set_update_schedule",
+           "hm_set_pivot_schedule"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -121,6 +122,7 @@ def load(build_if_missing=True):
     L.hm_test_hold.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
     L.hm_set_far_schedule.argtypes = [vp, ctypes.c_int32]
     L.hm_set_update_schedule.argtypes = [vp, ctypes.c_int32]
+    L.hm_set_pivot_schedule.argtypes = [vp, ctypes.c_int32]
     L.hm_tc_cgemm.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_int64, vp, ctypes.c_int64,
                               vp, ctypes.c_int64, vp]
     mesh = [ctypes.c_int32, _f64p, ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, ctypes.c_double,
@@ -404,6 +406,12 @@ def hm_set_far_schedule(h, kind=0):
 def hm_set_update_schedule(h, kind=0):
     """Complex-FP32 Schur updates of precond_setup: 1 CUDA cores, 2 tensor cores, 0 default (1)."""
     h.check(load().hm_set_update_schedule(h.ptr, kind), "hm_set_update_schedule")
+
+
+def hm_set_pivot_schedule(h, ctas=0):
+    """CTAs per FP64 pivot inversion in precond_setup: 1, or a cluster of 2, 4 or 8 (bitwise
+    the same inverses); 0 = the default."""
+    h.check(load().hm_set_pivot_schedule(h.ptr, ctas), "hm_set_pivot_schedule")
 
 
 def hm_get_fill_ranks(h):

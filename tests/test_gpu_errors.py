@@ -34,9 +34,11 @@ def _zero_first_pivot(P):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_singular_pivot_block(sphere480, prec):
+@pytest.mark.parametrize("ctas", [1, 4])
+def test_singular_pivot_block(sphere480, prec, ctas):
     Q = _zero_first_pivot(sphere480)
     h = hm.hmat_create(Q, ordering=1, precision=prec)
+    hm.hmsolve.hm_set_pivot_schedule(h, ctas)
     with pytest.raises(hm.HMError) as ei:
         hm.precond_setup(h)
     assert ei.value.code == H.HM_ESINGULAR

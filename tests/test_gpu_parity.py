@@ -204,6 +204,42 @@ def test_update_schedules_match(cfg1, sphere1920):
     assert max(rel(x, y) for x, y in zip(got[1], got[2])) < 1e-3
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pivot_schedules_bitwise_equal(sphere1920, prec):
+    """The pivot inverses on clusters of 2, 4 and 8 CTAs do each entry's Gauss-Jordan operations
+    of the one-CTA kernel: D_k^{-1}, the panels built from them and a solve are bitwise those of
+    one CTA (FP64 and mixed setups), and within 1e-9 of the oracle's inverses (FP64)."""
+    nl = len(sphere1920.leaf_ptr) - 1
+    F = schur.setup(sphere1920, ordering.rcm(nl, list(zip(sphere1920.near_t.tolist(), sphere1920.near_s.tolist()))),
+                    fill_tol=0.0) if prec == 0 else None
+    b = sphere1920.plane_wave([0.0, 0.0, -1.0], [1.0, 0.0, 0.0])
+    ref = None
+    for ctas in (1, 2, 4, 8):
+        g = hm.hmat_create(sphere1920, ordering=1, precision=prec, fill_tol=1e-2)
+        hm.hmsolve.hm_set_pivot_schedule(g, ctas)
+        hm.precond_setup(g)
+        ptr, idx = hm.hm_get_fill(g)
+        size = np.diff(sphere1920.leaf_ptr)[hm.hm_get_order(g)]
+        got = []
+        for k in range(len(size)):
+            nk = int(size[k])
+            Di = hm.hm_get_block(g, 1, k, (nk, nk))
+            if F is not None and k % 7 == 0:
+                assert rel(Di, np.linalg.inv(F.D[k])) < 1e-9, (ctas, k)
+            got.append(Di)
+            if ptr[k + 1] > ptr[k]:
+                got.append(hm.hm_get_block(g, 2, k, (nk, int(size[idx[ptr[k]:ptr[k + 1]]].sum()))))
+        x, it, rr, code = hm.solve(g, b, tol=1e-5, restart=30)
+        got.append(x)
+        if ref is None:
+            ref = got
+        else:
+            assert all(np.array_equal(u, v) for u, v in zip(got, ref)), ctas
+        hm.hmat_destroy(g)
+    with pytest.raises(hm.HMError):
+        hm.hmsolve.hm_set_pivot_schedule(hm.hmat_create(sphere1920, ordering=1), 3)
+
+
 def test_mixed_solution_error_against_tight_oracle(cfg1, cfg1_mixed, cfg1_tight):
     """The FP64 refinement loop stops on the true residual ||V - Z I||/||V||; at 1e-5 (the
     setting the benchmark uses for its 1e-4 error bar) the solution is within 1e-4 of the
