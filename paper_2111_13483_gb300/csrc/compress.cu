@@ -14,7 +14,9 @@
 // (surplus columns of a wide block could never become mutually orthogonal: they would keep
 // rotating at rounding level); the rounding floor of the skip rule is u^2 ||W||_F^2.  Then
 // sigma_i = ||a_i||, A ~ sum over the r largest of a_i v_i^H.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "cplx.cuh"
 #include "hm_internal.h"
@@ -97,6 +99,86 @@ __global__ void __launch_bounds__(256) k_compress(int nfill, const int *fill_e, 
         }
     }
     if (threadIdx.x == 0) rank_out[f] = r;
+}
+
+// The same compression with one warp per fill-in block (jacobi_sweeps_warp), for the
+// factorised panels after the elimination.  The host packs the blocks, largest shared-memory
+// footprint first, into CTAs of up to CW_WARPS warps whose regions fit CW_BYTES; warp w of CTA
+// b takes block item[first[b] + w] in the region at soff (entries of TC): A (nr x nc, leading
+// dimension nr | 1), V (nc x nc, leading dimension nc | 1), then the norms and the order of
+// the truncation.  Ranks, factors and their layout are those of k_compress.
+constexpr int CW_WARPS = 8;
+constexpr int CW_BYTES = 110 * 1024;
+
+__host__ __device__ __forceinline__ int cw_footprint(int m, int n)
+{
+    const int nr = m < n ? n : m, nc = m < n ? m : n;
+    return nc * ((nr | 1) + (nc | 1)) + 64;   // entries; the last 64 hold the norms and the order
+}
+
+template <class TC>
+__global__ void __launch_bounds__(CW_WARPS * 32) k_compress_w(const int *first, const int *item, const int *soff,
+                                                              const int *fill_e, const int *fill_k, const int *size,
+                                                              const int *sidx, const int *srow, const int64_t *coff,
+                                                              TC *W, double tol, int *rank_out)
+{
+    typedef typename Real<TC>::type R;
+    extern __shared__ unsigned char smraw[];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int x = first[blockIdx.x] + wp;
+    if (x >= first[blockIdx.x + 1]) return;   // the rest of the kernel uses warp barriers only
+    const int f = item[x];
+    const int e = fill_e[f], k = fill_k[f];
+    const int m = size[k], n = size[sidx[e]];
+    TC *Wb = W + coff[k] + (int64_t)srow[e] * m;   // m x n, column-major, ld m
+    const bool tr = m < n;                       // A = W^H (rows nr = n, columns nc = m)
+    const int nr = tr ? n : m, nc = tr ? m : n;
+    const int lda = nr | 1, ldv = nc | 1;
+    TC *A = (TC *)smraw + soff[x];
+    TC *V = A + nc * lda;
+    R *sig = (R *)(V + nc * ldv);
+    int *ord = (int *)(sig + 64);
+    R fro2 = 0;
+    for (int t = lane; t < m * n; t += 32) {
+        const int r = t % m, c = t / m;
+        const TC w = Wb[t];
+        fro2 += w.x * w.x + w.y * w.y;
+        if (tr) A[r * lda + c] = jconj(w);
+        else A[c * lda + r] = w;
+    }
+    for (int t = lane; t < nc * nc; t += 32) {
+        const int r = t % nc, c = t / nc;
+        V[c * ldv + r] = (r == c) ? cconv<TC>(make_double2(1.0, 0.0)) : czero(TC());
+    }
+    for (int o = 16; o > 0; o >>= 1) fro2 += __shfl_xor_sync(0xffffffffu, fro2, o);
+    __syncwarp();
+    const R floor2 = JacobiEps<TC>::u() * JacobiEps<TC>::u() * fro2;   // rounding level of the block
+    jacobi_sweeps_warp<TC>(A, lda, V, ldv, nr, nc, floor2);
+    for (int c = lane; c < nc; c += 32) {   // singular values squared
+        R s2 = 0;
+        for (int r = 0; r < nr; ++r) s2 += A[c * lda + r].x * A[c * lda + r].x + A[c * lda + r].y * A[c * lda + r].y;
+        sig[c] = s2;
+    }
+    __syncwarp();
+    int r = 0;
+    if (lane == 0) {
+        r = truncation_rank(sig, ord, nc, tol);
+        if ((int64_t)r * (m + n) >= (int64_t)m * n) r = -1;
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    __syncwarp();
+    if (r >= 0) {   // the factors, as k_compress writes them
+        TC *Pb = Wb, *Qb = Wb + (int64_t)m * r;
+        for (int t = lane; t < m * r; t += 32) {
+            const int row = t % m, o = ord[t / m];
+            Pb[t] = tr ? V[o * ldv + row] : A[o * lda + row];
+        }
+        for (int t = lane; t < n * r; t += 32) {
+            const int c = t % n, o = ord[t / n];
+            Qb[t] = jconj(tr ? A[o * lda + c] : V[o * ldv + c]);
+        }
+    }
+    if (lane == 0) rank_out[f] = r;
 }
 
 // dst[e] <- the block's stored entries (dense n_k n_j, or r (n_k + n_j) factor entries), one
@@ -206,26 +288,66 @@ cudaError_t compress_run(hm_ctx *h)
     if (nfill == 0 || !(h->opts.fill_tol > 0)) return cudaSuccess;
     cudaError_t e;
     if (!h->d_fill_rank && (e = h->arena.alloc((void **)&h->d_fill_rank, sizeof(int) * nfill))) return e;
-    const size_t smem64 = sizeof(double2) * 2 * 64 * 64, smem32 = sizeof(float2) * 2 * 64 * 64;
-    static bool attr = false;
-    if (!attr) {
-        if ((e = cudaFuncSetAttribute(k_compress<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64)) ||
-            (e = cudaFuncSetAttribute(k_compress<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32)))
-            return e;
-        attr = true;
-    }
     // FP64 Jacobi on the FP64 factors (the oracle's rank decisions); FP32 on the FP32 factors
     // of the mixed-precision setup
-    if (h->opts.precision == 1)
+    const bool mixed = h->opts.precision == 1;
+    if (h->cw_first.empty()) {   // pack the blocks into CTAs (once per handle)
+        const int esz = mixed ? (int)sizeof(float2) : (int)sizeof(double2);
+        const int cap = CW_BYTES / esz;
+        std::vector<int> foot(nfill), ordv(nfill);
+        for (int f = 0; f < nfill; ++f) {
+            foot[f] = cw_footprint(P.size[P.fill_k[f]], P.size[P.sidx[P.fill_e[f]]]);
+            ordv[f] = f;
+        }
+        std::stable_sort(ordv.begin(), ordv.end(), [&](int a, int b) { return foot[a] > foot[b]; });
+        std::vector<int> off(nfill);
+        h->cw_first.assign(1, 0);
+        int used = 0, cnt = 0;
+        h->cw_smem = 0;
+        for (int x = 0; x < nfill; ++x) {
+            const int fp = foot[ordv[x]];
+            if (cnt == CW_WARPS || (cnt > 0 && used + fp > cap)) {
+                h->cw_first.push_back(x);
+                used = cnt = 0;
+            }
+            off[x] = used;
+            used += fp;
+            ++cnt;
+            h->cw_smem = std::max<size_t>(h->cw_smem, (size_t)used * esz);
+        }
+        h->cw_first.push_back(nfill);
+        if ((e = h->arena.alloc((void **)&h->d_cw, sizeof(int) * (h->cw_first.size() + 2 * (size_t)nfill))) ||
+            (e = cudaMemcpyAsync(h->d_cw, h->cw_first.data(), sizeof(int) * h->cw_first.size(), cudaMemcpyHostToDevice,
+                                 h->stream)) ||
+            (e = cudaMemcpyAsync(h->d_cw + h->cw_first.size(), ordv.data(), sizeof(int) * nfill,
+                                 cudaMemcpyHostToDevice, h->stream)) ||
+            (e = cudaMemcpyAsync(h->d_cw + h->cw_first.size() + nfill, off.data(), sizeof(int) * nfill,
+                                 cudaMemcpyHostToDevice, h->stream)) ||
+            (e = cudaStreamSynchronize(h->stream)))
+            return e;
+    }
+    // a block larger than CW_BYTES (FP64, n_k = n_j = 64: 134 KB) has a CTA of its own
+    static size_t attr_w[2] = {0, 0};
+    if (h->cw_smem > attr_w[mixed]) {
+        if ((e = mixed ? cudaFuncSetAttribute(k_compress_w<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)h->cw_smem)
+                       : cudaFuncSetAttribute(k_compress_w<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)h->cw_smem)))
+            return e;
+        attr_w[mixed] = h->cw_smem;
+    }
+    const unsigned ncta = (unsigned)h->cw_first.size() - 1;
+    const int *d_first = h->d_cw, *d_item = h->d_cw + h->cw_first.size(), *d_off = d_item + nfill;
+    if (mixed)
         HM_LAUNCH(h, K_COMPRESS,
-                  k_compress<float2><<<nfill, 256, smem32, h->stream>>>(nfill, h->d_fill_e, h->d_fill_k, h->d_size,
-                                                                        h->d_sidx, h->d_srow, h->d_coff, h->d_W32,
-                                                                        h->opts.fill_tol, h->d_fill_rank));
+                  k_compress_w<float2><<<ncta, CW_WARPS * 32, h->cw_smem, h->stream>>>(
+                      d_first, d_item, d_off, h->d_fill_e, h->d_fill_k, h->d_size, h->d_sidx, h->d_srow, h->d_coff,
+                      h->d_W32, h->opts.fill_tol, h->d_fill_rank));
     else
         HM_LAUNCH(h, K_COMPRESS,
-                  k_compress<double2><<<nfill, 256, smem64, h->stream>>>(nfill, h->d_fill_e, h->d_fill_k, h->d_size,
-                                                                         h->d_sidx, h->d_srow, h->d_coff, h->d_W,
-                                                                         h->opts.fill_tol, h->d_fill_rank));
+                  k_compress_w<double2><<<ncta, CW_WARPS * 32, h->cw_smem, h->stream>>>(
+                      d_first, d_item, d_off, h->d_fill_e, h->d_fill_k, h->d_size, h->d_sidx, h->d_srow, h->d_coff,
+                      h->d_W, h->opts.fill_tol, h->d_fill_rank));
     if ((e = cudaGetLastError())) return e;
     if ((e = cudaMemcpyAsync(h->fill_ranks.data(), h->d_fill_rank, sizeof(int) * nfill, cudaMemcpyDeviceToHost,
                              h->stream)))

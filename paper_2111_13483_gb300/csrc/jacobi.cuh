@@ -2,7 +2,7 @@
 // or in global memory for the larger ACA cores),
 // and the truncation rank of Sec. 3.4 / Eq. 10 (smallest r whose singular-value tail has
 // Frobenius norm <= tol times the total).  Used by the fill-in compression and by the
-// re-compression of ACA factors.
+// re-compression of ACA factors; a one-warp form serves the many small fill-in blocks.
 //
 // A (nr x nc, nr >= nc, column c at A + c * LD) is rotated in place until its columns are
 // mutually orthogonal; V (nc x nc, same stride, the identity on entry) accumulates the
@@ -93,6 +93,76 @@ __device__ void jacobi_sweeps(TC *A, TC *V, int nr, int nc, typename Real<TC>::t
         }
         if (!*s_rot) break;
         __syncthreads();
+    }
+}
+
+// The same sweeps by one warp, one lane per column pair of a round (nc <= 64, so a round has
+// at most 32 pairs), each lane summing its pair's inner products over the rows by itself:
+// no shuffles and no CTA barrier (only __syncwarp between rounds).  A has leading dimension
+// lda, V ldv (runtime).  Pairs, rotations, the skip rule and the sweep limit are those of
+// jacobi_sweeps; the inner products are summed row by row in order.
+template <class TC>
+__device__ void jacobi_sweeps_warp(TC *A, int lda, TC *V, int ldv, int nr, int nc, typename Real<TC>::type floor2)
+{
+    typedef typename Real<TC>::type R;
+    const int lane = threadIdx.x & 31;
+    const R ctol = sqrt(R(nr)) * JacobiEps<TC>::u();
+    const int np = (nc + 1) & ~1;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        bool rot = false;
+        for (int t = 0; t < np - 1; ++t) {
+            int p = t, q = np - 1;
+            if (lane > 0) {
+                p = t + lane;
+                if (p >= np - 1) p -= np - 1;
+                q = t - lane + np - 1;
+                if (q >= np - 1) q -= np - 1;
+            }
+            if (lane < np / 2 && p < nc && q < nc) {
+                TC *ap = A + p * lda, *aq = A + q * lda;
+                R al = 0, be = 0;
+                TC ga = czero(TC());
+#pragma unroll 4
+                for (int r = 0; r < nr; ++r) {
+                    const TC x = ap[r], y = aq[r];
+                    al += x.x * x.x + x.y * x.y;
+                    be += y.x * y.x + y.y * y.y;
+                    ga.x += x.x * y.x + x.y * y.y;   // conj(x) y
+                    ga.y += x.x * y.y - x.y * y.x;
+                }
+                const R g = sqrt(ga.x * ga.x + ga.y * ga.y);
+                if (g > ctol * sqrt(al * be) && g > floor2) {
+                    const R zeta = (be - al) / (2 * g);
+                    const R tt = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+                    const R cs = R(1) / sqrt(R(1) + tt * tt), sn = cs * tt;
+                    TC ph;   // conj(gamma) / |gamma|
+                    ph.x = ga.x / g;
+                    ph.y = -ga.y / g;
+#pragma unroll 4
+                    for (int r = 0; r < nr; ++r) {
+                        const TC x = ap[r];
+                        const TC y = cmul(ph, aq[r]);
+                        ap[r].x = cs * x.x - sn * y.x;
+                        ap[r].y = cs * x.y - sn * y.y;
+                        aq[r].x = sn * x.x + cs * y.x;
+                        aq[r].y = sn * x.y + cs * y.y;
+                    }
+                    TC *vp = V + p * ldv, *vq = V + q * ldv;
+#pragma unroll 4
+                    for (int r = 0; r < nc; ++r) {
+                        const TC x = vp[r];
+                        const TC y = cmul(ph, vq[r]);
+                        vp[r].x = cs * x.x - sn * y.x;
+                        vp[r].y = cs * x.y - sn * y.y;
+                        vq[r].x = sn * x.x + cs * y.x;
+                        vq[r].y = sn * x.y + cs * y.y;
+                    }
+                    rot = true;
+                }
+            }
+            __syncwarp();
+        }
+        if (!__any_sync(0xffffffffu, rot)) break;
     }
 }
 
