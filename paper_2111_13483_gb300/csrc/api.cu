@@ -578,7 +578,7 @@ int hm_set_update_schedule(hm_handle h, int32_t kind)
 int hm_set_pivot_schedule(hm_handle h, int32_t ctas)
 {
     if (!h || !(ctas == 0 || ctas == 1 || ctas == 2 || ctas == 4 || ctas == 8)) return HM_EINVAL;
-    h->pivot_cl = ctas == 0 ? 1 : ctas;
+    h->pivot_cl = ctas == 0 ? 8 : ctas;
     return HM_OK;
 }
 

@@ -228,12 +228,12 @@ struct hm_ctx {
     hm::SweepTune sweep_tune[2][2][5];   // [FP32][forward][width class]
     int sweep_fixed = 0;                 // a schedule code set by hm_set_sweep_schedule, 0 = tuned
     int far_kind = 1;                    // complex-FP32 far field: 1 CUDA cores, 2 tensor cores
-    int update_kind = 1;
-    int pivot_cl = 1;
+    int update_kind = 1;                 // complex-FP32 Schur updates: 1 CUDA cores, 2 tensor cores
+    int pivot_cl = 8;                    // CTAs per pivot inversion (1 = one CTA; 2, 4, 8 = a cluster)
     // fill-in compression packing (compress.cu): CTA b takes the blocks first[b] .. first[b+1]
     std::vector<int> cw_first;
-    int *d_cw = nullptr;   // first, then the block order, then the shared-memory offsets
-    size_t cw_smem = 0;   // CTAs per pivot inversion (1 = one CTA; 2, 4, 8 = a cluster)                 // complex-FP32 Schur updates: 1 CUDA cores, 2 tensor cores
+    int *d_cw = nullptr;                 // first, then the block order, then the shared-memory offsets
+    size_t cw_smem = 0;
     int *d_ucum = nullptr;               // per S-list entry: tensor-core update tasks of the step before it
     std::vector<int> utot;               // per step: tensor-core update tasks
 };

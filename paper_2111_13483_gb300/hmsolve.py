@@ -410,7 +410,7 @@ def hm_set_update_schedule(h, kind=0):
 
 def hm_set_pivot_schedule(h, ctas=0):
     """CTAs per FP64 pivot inversion in precond_setup: 1, or a cluster of 2, 4 or 8 (bitwise
-    the same inverses); 0 = the default."""
+    the same inverses); 0 = the default (8)."""
     h.check(load().hm_set_pivot_schedule(h.ptr, ctas), "hm_set_pivot_schedule")
 
 
