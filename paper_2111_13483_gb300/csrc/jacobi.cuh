@@ -96,11 +96,12 @@ __device__ void jacobi_sweeps(TC *A, TC *V, int nr, int nc, typename Real<TC>::t
     }
 }
 
-// The same sweeps by one warp, one lane per column pair of a round (nc <= 64, so a round has
-// at most 32 pairs), each lane summing its pair's inner products over the rows by itself:
-// no shuffles and no CTA barrier (only __syncwarp between rounds).  A has leading dimension
-// lda, V ldv (runtime).  Pairs, rotations, the skip rule and the sweep limit are those of
-// jacobi_sweeps; the inner products are summed row by row in order.
+// The same sweeps by one warp, each column pair of a round on its own lane (nc <= 64, so a
+// round has at most 32 pairs), or, when a round has at most 16 pairs, on two lanes that take
+// the even and the odd rows and add their partial inner products with one shuffle: no CTA
+// barrier (only __syncwarp between rounds).  A has leading dimension lda, V ldv (runtime).
+// Pairs, rotations, the skip rule and the sweep limit are those of jacobi_sweeps; both lanes
+// of a pair hold the same sums (addition commutes), so they take the same decision.
 template <class TC>
 __device__ void jacobi_sweeps_warp(TC *A, int lda, TC *V, int ldv, int nr, int nc, typename Real<TC>::type floor2)
 {
@@ -108,57 +109,67 @@ __device__ void jacobi_sweeps_warp(TC *A, int lda, TC *V, int ldv, int nr, int n
     const int lane = threadIdx.x & 31;
     const R ctol = sqrt(R(nr)) * JacobiEps<TC>::u();
     const int np = (nc + 1) & ~1;
+    const bool split = np / 2 <= 16;
+    const int pl = split ? (lane & 15) : lane;   // pair of the round
+    const int r0 = split ? (lane >> 4) : 0, rs = split ? 2 : 1;
     for (int sweep = 0; sweep < 40; ++sweep) {
         bool rot = false;
         for (int t = 0; t < np - 1; ++t) {
             int p = t, q = np - 1;
-            if (lane > 0) {
-                p = t + lane;
+            if (pl > 0) {
+                p = t + pl;
                 if (p >= np - 1) p -= np - 1;
-                q = t - lane + np - 1;
+                q = t - pl + np - 1;
                 if (q >= np - 1) q -= np - 1;
             }
-            if (lane < np / 2 && p < nc && q < nc) {
-                TC *ap = A + p * lda, *aq = A + q * lda;
-                R al = 0, be = 0;
-                TC ga = czero(TC());
+            const bool act = pl < np / 2 && p < nc && q < nc;
+            TC *ap = A + p * lda, *aq = A + q * lda;
+            R al = 0, be = 0;
+            TC ga = czero(TC());
+            if (act) {
 #pragma unroll 4
-                for (int r = 0; r < nr; ++r) {
+                for (int r = r0; r < nr; r += rs) {
                     const TC x = ap[r], y = aq[r];
                     al += x.x * x.x + x.y * x.y;
                     be += y.x * y.x + y.y * y.y;
                     ga.x += x.x * y.x + x.y * y.y;   // conj(x) y
                     ga.y += x.x * y.y - x.y * y.x;
                 }
-                const R g = sqrt(ga.x * ga.x + ga.y * ga.y);
-                if (g > ctol * sqrt(al * be) && g > floor2) {
-                    const R zeta = (be - al) / (2 * g);
-                    const R tt = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-                    const R cs = R(1) / sqrt(R(1) + tt * tt), sn = cs * tt;
-                    TC ph;   // conj(gamma) / |gamma|
-                    ph.x = ga.x / g;
-                    ph.y = -ga.y / g;
+            }
+            if (split) {
+                al += __shfl_xor_sync(0xffffffffu, al, 16);
+                be += __shfl_xor_sync(0xffffffffu, be, 16);
+                ga.x += __shfl_xor_sync(0xffffffffu, ga.x, 16);
+                ga.y += __shfl_xor_sync(0xffffffffu, ga.y, 16);
+            }
+            const R g = sqrt(ga.x * ga.x + ga.y * ga.y);
+            if (act && g > ctol * sqrt(al * be) && g > floor2) {
+                const R zeta = (be - al) / (2 * g);
+                const R tt = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+                const R cs = R(1) / sqrt(R(1) + tt * tt), sn = cs * tt;
+                TC ph;   // conj(gamma) / |gamma|
+                ph.x = ga.x / g;
+                ph.y = -ga.y / g;
 #pragma unroll 4
-                    for (int r = 0; r < nr; ++r) {
-                        const TC x = ap[r];
-                        const TC y = cmul(ph, aq[r]);
-                        ap[r].x = cs * x.x - sn * y.x;
-                        ap[r].y = cs * x.y - sn * y.y;
-                        aq[r].x = sn * x.x + cs * y.x;
-                        aq[r].y = sn * x.y + cs * y.y;
-                    }
-                    TC *vp = V + p * ldv, *vq = V + q * ldv;
-#pragma unroll 4
-                    for (int r = 0; r < nc; ++r) {
-                        const TC x = vp[r];
-                        const TC y = cmul(ph, vq[r]);
-                        vp[r].x = cs * x.x - sn * y.x;
-                        vp[r].y = cs * x.y - sn * y.y;
-                        vq[r].x = sn * x.x + cs * y.x;
-                        vq[r].y = sn * x.y + cs * y.y;
-                    }
-                    rot = true;
+                for (int r = r0; r < nr; r += rs) {
+                    const TC x = ap[r];
+                    const TC y = cmul(ph, aq[r]);
+                    ap[r].x = cs * x.x - sn * y.x;
+                    ap[r].y = cs * x.y - sn * y.y;
+                    aq[r].x = sn * x.x + cs * y.x;
+                    aq[r].y = sn * x.y + cs * y.y;
                 }
+                TC *vp = V + p * ldv, *vq = V + q * ldv;
+#pragma unroll 4
+                for (int r = r0; r < nc; r += rs) {
+                    const TC x = vp[r];
+                    const TC y = cmul(ph, vq[r]);
+                    vp[r].x = cs * x.x - sn * y.x;
+                    vp[r].y = cs * x.y - sn * y.y;
+                    vq[r].x = sn * x.x + cs * y.x;
+                    vq[r].y = sn * x.y + cs * y.y;
+                }
+                rot = true;
             }
             __syncwarp();
         }
