@@ -422,6 +422,33 @@ def test_null_field_factor_is_the_incomplete_factorisation_of_the_near_pattern()
         assert np.abs(Lc @ Dc @ Lc.T - Zn).max() < 1e-12 * np.abs(Zn).max()
 
 
+def test_null_field_on_the_sphere_reproduces_the_near_field_on_its_pattern(sphere480):
+    """The same characterisation on the 480-unknown EFIE sphere in RCM order, where the complete
+    elimination fills: L has no block outside the near-field pattern, L D L^T equals Z_N on
+    every near-field block pair, and differs from it off the pattern (the dropped fill)."""
+    P = sphere480
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    S = krylov.NullField(P, order)
+    F = S.F
+    assert sum(len(x) for x in F.S) < sum(len(x) for x in schur.symbolic_fill(nl, list(F.near_pairs)))
+    n = S.n
+    Zn = np.zeros((n, n), dtype=np.complex128)
+    for j in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = 1.0
+        u = np.zeros(n, dtype=np.complex128)
+        u[S.new2cl] = e
+        Zn[:, j] = S.near_cluster(u)[S.new2cl]
+    L, D = schur.ldlt_dense(F)
+    mask = _near_block_mask(F, F.near_pairs)
+    assert np.all(L[~mask] == 0)
+    M = L @ D @ L.T
+    scale = np.abs(Zn).max()
+    assert np.abs(M - Zn)[mask].max() < 1e-11 * scale
+    assert np.abs(M - Zn)[~mask].max() > 1e-6 * scale
+
+
 def test_null_field_equals_the_schur_factor_when_the_pattern_has_no_fill():
     """A block-tridiagonal near field in its natural order has no fill-in: the two
     eliminations coincide, M = Z_N, so with no far field GMRES ends after one step."""
