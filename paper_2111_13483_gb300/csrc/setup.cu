@@ -199,20 +199,17 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(int kbase, const int *siz
 }
 
 // The same inverse on a cluster of CL CTAs (one block per cluster), so that the FP64 pipes of
-// CL SMs share the elimination.  The columns go to the CTAs in panels of PB (panel P = columns
-// P PB .. P PB + PB - 1 to CTA P mod CL), each CTA keeping its columns row-major (n x nloc).
-// Panel P: its CTA runs the PB Gauss-Jordan steps of the panel on the panel's own columns
-// (pivot search, interchange, scaling, elimination), keeping each step's pivot row, 1 / pivot
-// and interchanged pivot column, and stores them into every other CTA's shared memory
-// (distributed shared memory, two alternating buffers); one cluster barrier; then every CTA
-// applies the PB steps, in order, to its other columns.  Every entry thus goes through the
-// operations of k_pivot_inverse (gj_row / gj_entry) in the same order, so the inverse is bitwise
-// that of one CTA, with one cluster barrier per PB pivots.  The row interchanges are undone by
-// writing column x of the result from the column the interchanges moved there.  Every CTA
-// takes all the cluster barriers (a CTA without columns too).  Buffer P & 1 is rewritten for
-// panel P + 2 only after every CTA has passed the barrier of panel P + 1, which it reaches
-// after applying panel P.
-template <class S, int CL, int PB>
+// CL SMs share the elimination.  CTA q keeps the columns j = q, q + CL, ... of the in-place
+// array (row-major, n x nloc).  Step c: the CTA that owns column c finds the pivot and
+// stores p, 1 / pivot and the interchanged column c into every CTA of the cluster (two
+// alternating buffers, distributed shared memory), then one cluster barrier; every CTA then
+// interchanges, scales and eliminates its own columns with gj_row / gj_entry, entry for entry
+// the operations of k_pivot_inverse, so the inverse is bitwise the same.  The row
+// interchanges are undone by writing column x of the result from the column the interchanges
+// moved there.  Every CTA takes all n + 1 cluster barriers (a CTA without columns too).
+// Buffer b = c & 1 is rewritten at step c + 2 only after every CTA has passed the barrier of
+// step c + 1, which it reaches after its elimination of step c.
+template <class S, int CL>
 __global__ void __launch_bounds__(128) k_pivot_inverse_cl(int kbase, const int *size, const int64_t *doff, const S *Ad,
                                                           double2 *Dinv, float2 *Dinv32, int *err)
 {
@@ -220,96 +217,64 @@ __global__ void __launch_bounds__(128) k_pivot_inverse_cl(int kbase, const int *
     const int k = kbase + (int)(blockIdx.x / CL);
     extern __shared__ double2 sm[];
     const int n = size[k];
-    // local column jl of this CTA <-> column j of the block
-    auto gcol = [&](int jl) { return (jl / PB) * (PB * CL) + q * PB + jl % PB; };
-    int nloc = 0;
-    while (gcol(nloc) < n) ++nloc;
+    const int nloc = (n - q + CL - 1) / CL;    // columns q, q + CL, ... below n
     const int ld = nloc + 1;
-    double2 *a = sm;                           // n x ld, a[r * ld + jl]
+    double2 *a = sm;                           // n x ld, a[r * ld + jl] = column jl * CL + q
     double2 *rowc = sm + n * ld;               // nloc: the scaled pivot row
-    __shared__ double2 s_col[2][PB][64];       // pivot columns after the interchange (pushed)
-    __shared__ double2 s_d[2][PB];             // 1 / pivot (pushed)
-    __shared__ int s_p[2][PB];                 // pivot rows (pushed)
+    __shared__ double2 s_col[2][64];           // pivot column after the interchange (pushed)
+    __shared__ double2 s_d[2];                 // 1 / pivot (pushed)
+    __shared__ int s_p[2];                     // pivot row (pushed)
     __shared__ int piv[64];
     __shared__ int at[64];
-    __shared__ int o_p;
-    __shared__ double2 o_d;
     const S *D = Ad + doff[k];
     for (int e = threadIdx.x; e < n * nloc; e += blockDim.x) {
         const int r = e % n, jl = e / n;
-        a[r * ld + jl] = cwiden(D[r + (int64_t)gcol(jl) * n]);
+        a[r * ld + jl] = cwiden(D[r + (int64_t)(jl * CL + q) * n]);
     }
     cluster_sync();   // every CTA of the cluster is running before any remote store
-    const int npan = (n + PB - 1) / PB;
-    for (int P = 0; P < npan; ++P) {
-        const int b = P & 1, c0 = P * PB, w = min(n, c0 + PB) - c0;
-        const bool own = q == P % CL;
-        if (own) {
-            const int jl0 = (P / CL) * PB;     // local index of column c0
-            for (int s = 0; s < w; ++s) {
-                const int c = c0 + s;
-                if (threadIdx.x < 32) {
-                    double2 d;
-                    bool bad;
-                    const int bi = gj_pivot(a, ld, jl0 + s, c, n, &d, &bad);
-                    if (threadIdx.x == 0) {
-                        o_p = bi;
-                        o_d = d;
-                        if (bad) atomicCAS(err, 0, k + 1);
-                    }
-                }
-                __syncthreads();
-                const int p = o_p;
-                const double2 d = o_d;
-                for (int r = threadIdx.x; r < n; r += blockDim.x) s_col[b][s][r] = a[(r == p ? c : r) * ld + jl0 + s];
+    for (int c = 0; c < n; ++c) {
+        const int b = c & 1;
+        if (q == c % CL) {
+            const int col = c / CL;
+            __shared__ int o_p;
+            __shared__ double2 o_d;
+            if (threadIdx.x < 32) {
+                double2 d;
+                bool bad;
+                const int bi = gj_pivot(a, ld, col, c, n, &d, &bad);
                 if (threadIdx.x == 0) {
-                    s_p[b][s] = p;
-                    s_d[b][s] = d;
+                    o_p = bi;
+                    o_d = d;
+                    if (bad) atomicCAS(err, 0, k + 1);
                 }
-                for (int t = threadIdx.x; t < w; t += blockDim.x) {
-                    const int jl = jl0 + t;
-                    rowc[jl] = gj_row(a[p * ld + jl], d, c0 + t == c);
-                    if (p != c) a[p * ld + jl] = a[c * ld + jl];
-                }
-                __syncthreads();
-                for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
-                    const int r = e / w, t = e % w, jl = jl0 + t;
-                    a[r * ld + jl] = gj_entry(r == c, c0 + t == c, rowc[jl], s_col[b][s][r], d, a[r * ld + jl]);
-                }
-                __syncthreads();
             }
-            // the panel's steps to every other CTA of the cluster
-            const int per = w * (n + 1);
-            for (int x = threadIdx.x; x < (CL - 1) * per; x += blockDim.x) {
-                const unsigned dst = (unsigned)((q + 1 + x / per) % CL);
-                const int s = (x % per) / (n + 1), r = (x % per) % (n + 1);
+            __syncthreads();
+            const int p = o_p;
+            for (int x = threadIdx.x; x < CL * (n + 1); x += blockDim.x) {
+                const int dst = x / (n + 1), r = x % (n + 1);
                 if (r < n)
-                    st_remote_d2(cluster_map(smem_addr(&s_col[b][s][r]), dst), s_col[b][s][r]);
+                    st_remote_d2(cluster_map(smem_addr(&s_col[b][r]), (unsigned)dst), a[(r == p ? c : r) * ld + col]);
                 else {
-                    st_remote_d2(cluster_map(smem_addr(&s_d[b][s]), dst), s_d[b][s]);
-                    st_remote_s32(cluster_map(smem_addr(&s_p[b][s]), dst), s_p[b][s]);
+                    st_remote_d2(cluster_map(smem_addr(&s_d[b]), (unsigned)dst), o_d);
+                    st_remote_s32(cluster_map(smem_addr(&s_p[b]), (unsigned)dst), p);
                 }
             }
         }
         cluster_sync();
-        for (int s = 0; s < w; ++s) {
-            const int c = c0 + s, p = s_p[b][s];
-            const double2 d = s_d[b][s];
-            if (threadIdx.x == 0) piv[c] = p;
-            for (int jl = threadIdx.x; jl < nloc; jl += blockDim.x) {
-                const int j = gcol(jl);
-                if (own && j >= c0 && j < c0 + w) continue;   // the panel's columns: done above
-                rowc[jl] = gj_row(a[p * ld + jl], d, j == c);
-                if (p != c) a[p * ld + jl] = a[c * ld + jl];
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < n * nloc; e += blockDim.x) {
-                const int r = e / nloc, jl = e % nloc, j = gcol(jl);
-                if (own && j >= c0 && j < c0 + w) continue;
-                a[r * ld + jl] = gj_entry(r == c, j == c, rowc[jl], s_col[b][s][r], d, a[r * ld + jl]);
-            }
-            __syncthreads();
+        const int p = s_p[b];
+        const double2 d = s_d[b];
+        if (threadIdx.x == 0) piv[c] = p;
+        for (int jl = threadIdx.x; jl < nloc; jl += blockDim.x) {
+            const int j = jl * CL + q;
+            rowc[jl] = gj_row(a[p * ld + jl], d, j == c);
+            if (p != c) a[p * ld + jl] = a[c * ld + jl];
         }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * nloc; e += blockDim.x) {
+            const int r = e / nloc, jl = e % nloc;
+            a[r * ld + jl] = gj_entry(r == c, jl * CL + q == c, rowc[jl], s_col[b][r], d, a[r * ld + jl]);
+        }
+        __syncthreads();
     }
     // at[x] = the column of the array that the interchanges (undone last first) move to x
     if (threadIdx.x == 0) {
@@ -325,8 +290,8 @@ __global__ void __launch_bounds__(128) k_pivot_inverse_cl(int kbase, const int *
     float2 *out32 = Dinv32 ? Dinv32 + doff[k] : nullptr;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int r = e % n, x = e / n, src = at[x];
-        if ((src / PB) % CL != q) continue;
-        const double2 v = a[r * ld + (src / (PB * CL)) * PB + src % PB];
+        if (src % CL != q) continue;
+        const double2 v = a[r * ld + src / CL];
         out[e] = v;
         if (out32) out32[e] = make_float2((float)v.x, (float)v.y);
     }
@@ -687,16 +652,12 @@ static int upd_group(int ns, int nsm)
     return gb;
 }
 
-// pivot columns per cluster barrier of k_pivot_inverse_cl
-constexpr int PIVOT_PB = 4;
-
 // one pivot block on a cluster of h->pivot_cl CTAs (2, 4 or 8)
 template <class S>
 static cudaError_t pivot_cluster(hm_ctx *h, int k, int nk, const S *Ad, float2 *Dinv32)
 {
     const int C = h->pivot_cl;
-    int nloc = 0;   // columns of cluster CTA 0, the most any CTA holds
-    for (int j = 0; j < nk; ++j) nloc += (j / PIVOT_PB) % C == 0;
+    const int nloc = (nk + C - 1) / C;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C, 1, 1);
     cfg.blockDim = dim3(128, 1, 1);
@@ -715,11 +676,11 @@ static cudaError_t pivot_cluster(hm_ctx *h, int k, int nk, const S *Ad, float2 *
     double2 *Dinv = h->d_Dinv;
     int *err = h->d_err;
     if (C == 2)
-        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 2, PIVOT_PB>, k, sz, dof, Ad, Dinv, Dinv32, err));
+        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 2>, k, sz, dof, Ad, Dinv, Dinv32, err));
     else if (C == 4)
-        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 4, PIVOT_PB>, k, sz, dof, Ad, Dinv, Dinv32, err));
+        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 4>, k, sz, dof, Ad, Dinv, Dinv32, err));
     else
-        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 8, PIVOT_PB>, k, sz, dof, Ad, Dinv, Dinv32, err));
+        HM_LAUNCH(h, K_PIVOT, e = cudaLaunchKernelEx(&cfg, k_pivot_inverse_cl<S, 8>, k, sz, dof, Ad, Dinv, Dinv32, err));
     if (e) return e;
     return cudaGetLastError();
 }
