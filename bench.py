@@ -336,13 +336,14 @@ def roofline(prof, fs, stats, n, precision):
 
 
 def sweep_code_digest(texts=None):
-    """Key of the sweep kernels' code: sha256 (first 16 hex digits) of ops.cu + tile.cuh with
-    comments and whitespace removed, so that an edit of comments keeps a measurement valid
-    and any code change invalidates it."""
+    """Key of the sweep kernels' code: sha256 (first 16 hex digits) of ops.cu + tile.cuh +
+    cluster.cuh with comments and whitespace removed, so that an edit of comments keeps a
+    measurement valid and any code change invalidates it."""
     import hashlib
     import re
     if texts is None:
-        texts = [open(os.path.join(ROOT, "paper_2111_13483_gb300", "csrc", f)).read() for f in ("ops.cu", "tile.cuh")]
+        texts = [open(os.path.join(ROOT, "paper_2111_13483_gb300", "csrc", f)).read()
+                 for f in ("ops.cu", "tile.cuh", "cluster.cuh")]
     code = "".join(texts)
     code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
     code = re.sub(r"//[^\n]*", " ", code)

@@ -20,6 +20,7 @@ def _tree(tmp_path, code, records):
     csrc.mkdir(parents=True)
     (csrc / "ops.cu").write_text(code)
     (csrc / "tile.cuh").write_text("// tile\nint t;\n")
+    (csrc / "cluster.cuh").write_text("// cluster\nint u;\n")
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "k.md").write_text("# summary\n\n" + "\n".join(records) + "\n")
@@ -27,7 +28,7 @@ def _tree(tmp_path, code, records):
 
 def test_traffic_record_lookup(tmp_path, monkeypatch):
     code = "__global__ void k() {}\n"
-    digest = bench.sweep_code_digest([code, "// tile\nint t;\n"])
+    digest = bench.sweep_code_digest([code, "// tile\nint t;\n", "// cluster\nint u;\n"])
     _tree(tmp_path, code, [
         "traffic-record: class=sweep_fwd workload=sphere30720 precision=1 columns=64 bytes=123 source=%s" % digest,
         "traffic-record: class=sweep_bwd workload=sphere30720 precision=1 columns=64 bytes=456 source=0000",
