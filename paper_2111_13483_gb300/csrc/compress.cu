@@ -266,10 +266,10 @@ template <class TC> cudaError_t compress_step(hm_ctx *h, int k, TC *W)
     cudaError_t e;
     if (!h->d_fill_rank && (e = h->arena.alloc((void **)&h->d_fill_rank, sizeof(int) * P.fill_e.size()))) return e;
     const size_t smem = sizeof(TC) * 2 * 64 * 64;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (attr.need()) {
         if ((e = cudaFuncSetAttribute(k_compress<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-        attr = true;
+        attr.done();
     }
     HM_LAUNCH(h, K_COMPRESS,
               k_compress<TC><<<nf, 256, smem, h->stream>>>(nf, h->d_fill_e + f0, h->d_fill_k + f0, h->d_size, h->d_sidx,
@@ -326,15 +326,17 @@ cudaError_t compress_run(hm_ctx *h)
             (e = cudaStreamSynchronize(h->stream)))
             return e;
     }
-    // a block larger than CW_BYTES (FP64, n_k = n_j = 64: 134 KB) has a CTA of its own
-    static size_t attr_w[2] = {0, 0};
-    if (h->cw_smem > attr_w[mixed]) {
+    // a block larger than CW_BYTES (FP64, n_k = n_j = 64: 134 KB) has a CTA of its own; the
+    // limit is raised per device (the attribute belongs to the device) to the largest need seen
+    static std::atomic<size_t> attr_w[2][64];
+    const int dev = DeviceOnce::device();
+    if (dev < 0 || dev >= 64 || h->cw_smem > attr_w[mixed][dev].load()) {
         if ((e = mixed ? cudaFuncSetAttribute(k_compress_w<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)h->cw_smem)
                        : cudaFuncSetAttribute(k_compress_w<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)h->cw_smem)))
             return e;
-        attr_w[mixed] = h->cw_smem;
+        if (dev >= 0 && dev < 64) attr_w[mixed][dev].store(h->cw_smem);
     }
     const unsigned ncta = (unsigned)h->cw_first.size() - 1;
     const int *d_first = h->d_cw, *d_item = h->d_cw + h->cw_first.size(), *d_off = d_item + nfill;

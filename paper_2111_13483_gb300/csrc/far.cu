@@ -469,14 +469,14 @@ template <class T> struct FarLaunch {
         const int n = h->plan.n;
         const int budget = stage_need(64, SEG, nrhs, TR, TC);
         const size_t smem = sizeof(T) * (size_t)budget;
-        static bool attr = false;   // one per instantiation
-        if (!attr) {
+        static DeviceOnce attr;   // one per instantiation
+        if (attr.need()) {
             const int smax = (int)(sizeof(T) * (size_t)stage_need(64, SEG, maxw, TR, TC));
             cudaError_t e;
             if ((e = cudaFuncSetAttribute(k_far_t<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)) ||
                 (e = cudaFuncSetAttribute(k_far_y<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)))
                 return e;
-            attr = true;
+            attr.done();
         }
         const int ntask = (int)F.p1_lo.size();
         if (ntask > 0)
@@ -502,13 +502,13 @@ static cudaError_t far_tc_launch(hm_ctx *h, const float2 *U, const float2 *V, fl
 {
     const FarPlan &F = h->fplan;
     const int n = h->plan.n;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (attr.need()) {
         cudaError_t e;
         if ((e = cudaFuncSetAttribute(k_far_t_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM)) ||
             (e = cudaFuncSetAttribute(k_far_y_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM)))
             return e;
-        attr = true;
+        attr.done();
     }
     const int ntask = (int)F.p1_lo.size();
     if (ntask > 0)

@@ -1,5 +1,6 @@
 // Internal declarations of the hmsolve library (host planner, device kernels, C-ABI).
 #pragma once
+#include <atomic>
 
 #include <cuda_runtime.h>
 
@@ -253,6 +254,29 @@ constexpr int ERR_TIMEOUT = 0x40000000;   // d_err bit: a bounded device-side wa
 // sweeps leave out (test hook, -1 = none) and the bound on one device-side wait (uint64 ns)
 constexpr int ERR_CODE = 0, ERR_HOLD = 1, ERR_BOUND = 2, ERR_WORDS = 4;
 constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ull;
+
+// A kernel's attributes (its dynamic shared-memory limit, cluster sizes) belong to one device:
+// a process with handles on several GPUs must set them on each.  A call site keeps one of these
+// and sets its attributes when need() says the current device has not had them yet.
+struct DeviceOnce {
+    std::atomic<unsigned long long> mask{0};   // device ordinals 0..63 done
+    static int device()
+    {
+        int d = 0;
+        cudaGetDevice(&d);
+        return d;
+    }
+    bool need() const
+    {
+        const int d = device();
+        return d < 0 || d >= 64 || !((mask.load() >> d) & 1ull);
+    }
+    void done()
+    {
+        const int d = device();
+        if (d >= 0 && d < 64) mask.fetch_or(1ull << d);
+    }
+};
 
 // planner.cpp
 int validate_and_copy(hm_ctx *h, const hm_desc *d);

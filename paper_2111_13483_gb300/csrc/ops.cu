@@ -1243,12 +1243,12 @@ static cudaError_t sweep_shape(hm_ctx *h, const OpData<T> &d, bool forward, cons
     };
     const int budget = need(gw);
     const size_t smem = sizeof(T) * (size_t)budget;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (attr.need()) {
         const int smax = (int)(sizeof(T) * (size_t)need(maxw));
         cudaFuncSetAttribute(k_sweep_fwd<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         cudaFuncSetAttribute(k_sweep_bwd<T, TR, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-        attr = true;
+        attr.done();
     }
     const unsigned grid = (unsigned)(P.nb * G);
     if (forward)
@@ -1273,13 +1273,13 @@ template <int TR, int TC, int NT> static size_t sweep_cl_smem(int w)
 }
 template <int TR, int TC, int NT> static void sweep_cl_attrs(int maxw)
 {
-    static bool done = false;
-    if (done) return;
+    static DeviceOnce attr;
+    if (!attr.need()) return;
     for (auto k : {k_sweep_cl<TR, TC, NT, true>, k_sweep_cl<TR, TC, NT, false>}) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_cl_smem<TR, TC, NT>(maxw));
         cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     }
-    done = true;
+    attr.done();
 }
 
 template <int TR, int TC, int NT>
@@ -1321,14 +1321,15 @@ static cudaError_t sweep_cl_shape(hm_ctx *h, const OpData<float2> &d, bool forwa
 }
 
 // Largest cluster (16 or 8 CTAs; 0: neither) with which a cluster-chained sweep of the tile
-// shape fits the device at the shape's widest group (maxw); asked once per shape.
+// shape fits the device at the shape's widest group (maxw); asked once per shape and device.
 template <int TR, int TC, int NT>
 static int sweep_cl_max(int maxw)
 {
-    static int cached = -1;
-    if (cached >= 0) return cached;
+    static std::atomic<int> cache[64];   // per device: the answer + 1, 0 = not asked yet
+    const int dev = DeviceOnce::device();
+    if (dev >= 0 && dev < 64 && cache[dev].load() > 0) return cache[dev].load() - 1;
     sweep_cl_attrs<TR, TC, NT>(maxw);
-    cached = 0;
+    int cached = 0;
     for (int C = 16; C >= 8; C /= 2) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)C);
@@ -1349,6 +1350,7 @@ static int sweep_cl_max(int maxw)
         }
         cudaGetLastError();
     }
+    if (dev >= 0 && dev < 64) cache[dev].store(cached + 1);
     return cached;
 }
 
@@ -1360,12 +1362,12 @@ static cudaError_t sweep_sr_shape(hm_ctx *h, const OpData<T> &d, bool forward, c
     Plan &P = h->plan;
     const int budget = stage_need(64 * SWEEP_SR, 64, gw, TR, TC);
     const size_t smem = sizeof(T) * (size_t)budget;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (attr.need()) {
         const int smax = (int)(sizeof(T) * (size_t)stage_need(64 * SWEEP_SR, 64, maxw, TR, TC));
         cudaFuncSetAttribute(k_sweep_sr<T, TR, TC, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         cudaFuncSetAttribute(k_sweep_sr<T, TR, TC, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-        attr = true;
+        attr.done();
     }
     const int nsr = (P.nb + SWEEP_SR - 1) / SWEEP_SR, dir = forward ? 0 : 1;
     const unsigned grid = (unsigned)(nsr * G);
@@ -1391,13 +1393,13 @@ static cudaError_t sweep_ch_shape(hm_ctx *h, const OpData<T> &d, bool forward, c
     Plan &P = h->plan;
     const int budget = std::max(stage_need(64, 64, gw, TR, TC), (SWEEP_T + 1) * 64 * gw + 2 * CHAIN_WCAP);
     const size_t smem = sizeof(T) * (size_t)budget;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (attr.need()) {
         const int smax = (int)(sizeof(T) * (size_t)std::max(stage_need(64, 64, maxw, TR, TC),
                                                             (SWEEP_T + 1) * 64 * maxw + 2 * CHAIN_WCAP));
         cudaFuncSetAttribute(k_sweep_ch<T, TR, TC, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         cudaFuncSetAttribute(k_sweep_ch<T, TR, TC, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-        attr = true;
+        attr.done();
     }
     const unsigned grid = (unsigned)(G * (P.nb + 1));
     if (forward)
@@ -1422,11 +1424,11 @@ static cudaError_t sweep_tc_launch(hm_ctx *h, const OpData<float2> &d, bool forw
 {
     Plan &P = h->plan;
     const size_t smem = tc::REGION_BYTES + 2 * TCW_BYTES + 1024;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (attr.need()) {
         cudaFuncSetAttribute(k_sweep_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_sweep_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        attr.done();
     }
     const unsigned grid = (unsigned)(P.nb * G);
     if (forward)
@@ -1643,11 +1645,11 @@ cudaError_t ensure_solve_workspace(hm_ctx *h, int nrhs)
         if ((e = h->arena.alloc((void **)&h->d_ytag, sizeof(uint4) * (size_t)n * 64))) return e;
         if ((e = cudaMemsetAsync(h->d_ytag, 0, sizeof(uint4) * (size_t)n * 64, h->stream))) return e;
     }
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (attr.need()) {
         set_attrs<double2>();
         set_attrs<float2>();
-        attr = true;
+        attr.done();
     }
     return cudaSuccess;
 }

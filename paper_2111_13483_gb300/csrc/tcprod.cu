@@ -64,12 +64,12 @@ extern "C" int hm_tc_cgemm(int32_t m, int32_t k, int32_t ncols, const void *dA, 
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     const int zero = 0;
-    static bool attr = false;
-    if (!attr) {
+    static hm::DeviceOnce attr;
+    if (attr.need()) {
         if ((e = cudaFuncSetAttribute(hm::k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)hm::tc::SMEM_BYTES)))
             return HM_ECUDA;
-        attr = true;
+        attr.done();
     }
     if ((e = cudaMemcpyToSymbolAsync(hm::g_tc_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st)))
         return HM_ECUDA;
