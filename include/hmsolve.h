@@ -105,8 +105,8 @@ typedef struct {
  *   compress_in_setup  with fill_tol > 0: 0 = the fill-in coefficient blocks are truncated once
  *              the elimination is complete and only the sweeps use the truncations; 1 = each is
  *              truncated as soon as its elimination step forms it, so that the Schur updates of
- *              that step (and every later block) use it (the abstract's "compressing the fill-in
- *              blocks in preconditioner computation"; Sec. 3.4 is silent on the point).
+ *              that step (and every later block) use it (the abstract has the fill-in blocks
+ *              compressed while the preconditioner is computed; Sec. 3.4 is silent on the point).
  */
 typedef struct {
     int32_t ordering;

@@ -89,8 +89,8 @@ def setup(prob, order, fill_tol=1e-2, max_steps=None, compress_in_setup=False, d
 
     Fill-in compression (Sec. 3.4) has two readings.  Default (after the factorisation):
     every fill-in coefficient block is truncated once the elimination is complete, and only
-    the sweeps use the truncations.  ``compress_in_setup`` (the abstract's "compressing the
-    fill-in blocks in preconditioner computation"): at elimination step k the fill-in blocks
+    the sweeps use the truncations.  ``compress_in_setup`` (the abstract's reading: the fill-in
+    blocks are compressed while the preconditioner is being computed): at elimination step k the fill-in blocks
     W_kj of the new panel are truncated as soon as they are formed, and the Schur updates of
     that step (and so every later pivot block and panel) use the truncations.
 
