@@ -430,6 +430,15 @@ int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int3
                  int32_t *idx, int64_t idx_cap);
 
 /*
+ * hm_plan_fill with a choice of lists: closure 1 = the symbolic fill (as hm_plan_fill);
+ * closure 0 = no fill, S_k = the later near-field neighbours of k only (the lists of the
+ * null-field comparison, hm_opts.preconditioner = 2).  Same outputs and errors as
+ * hm_plan_fill; HM_EINVAL for other closure values.
+ */
+int hm_plan_fill_closure(int32_t closure, int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int32_t *j,
+                         int32_t *ptr, int32_t *idx, int64_t idx_cap);
+
+/*
  * The library's plan of the far-field product Z_F u (the U (V^T u) products of Sec. 2, Eq. 11,
  * over the admissible blocks of Eq. 8) for the far blocks of an H-matrix description, in
  * cluster order: the same checks as hmat_create on n, leaf_ptr and the far arrays (fields of

@@ -701,20 +701,27 @@ extern "C" int hm_plan_order(int32_t n_leaves, int32_t n_pairs, const int32_t *t
     return hm_plan_order_method(1, n_leaves, n_pairs, t, s, order);
 }
 
-extern "C" int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int32_t *j, int32_t *ptr,
-                            int32_t *idx, int64_t idx_cap)
+extern "C" int hm_plan_fill_closure(int32_t closure, int32_t n_blocks, int32_t n_pairs, const int32_t *i,
+                                    const int32_t *j, int32_t *ptr, int32_t *idx, int64_t idx_cap)
 {
-    if (n_blocks <= 0 || n_pairs < 0 || !ptr || (n_pairs > 0 && (!i || !j))) return HM_EINVAL;
+    if ((closure != 0 && closure != 1) || n_blocks <= 0 || n_pairs < 0 || !ptr || (n_pairs > 0 && (!i || !j)))
+        return HM_EINVAL;
     for (int b = 0; b < n_pairs; ++b)
         if (i[b] < 0 || j[b] < 0 || i[b] >= n_blocks || j[b] >= n_blocks) return HM_EINVAL;
     std::vector<int> iv(i, i + n_pairs), jv(j, j + n_pairs), sp, si;
-    hm::symbolic_fill(n_blocks, iv, jv, sp, si);
+    hm::symbolic_fill(n_blocks, iv, jv, sp, si, closure == 1);
     std::memcpy(ptr, sp.data(), sizeof(int32_t) * (n_blocks + 1));
     if (idx) {
         if ((int64_t)si.size() > idx_cap) return HM_EINVAL;
         std::memcpy(idx, si.data(), sizeof(int32_t) * si.size());
     }
     return HM_OK;
+}
+
+extern "C" int hm_plan_fill(int32_t n_blocks, int32_t n_pairs, const int32_t *i, const int32_t *j, int32_t *ptr,
+                            int32_t *idx, int64_t idx_cap)
+{
+    return hm_plan_fill_closure(1, n_blocks, n_pairs, i, j, ptr, idx, idx_cap);
 }
 
 extern "C" int hm_plan_far(int32_t n, int32_t n_leaves, const int32_t *leaf_ptr, int32_t n_far, const int32_t *far_r0,

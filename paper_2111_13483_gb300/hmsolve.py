@@ -63,7 +63,7 @@ EXPORTS = ["hm_default_opts", "hmat_create", "precond_setup", "solve", "solve_de
            "hm_batch_step", "hm_batch_result", "hm_batch_close", "hm_set_sweep_schedule",
            "hm_get_profile_cols", "hm_plan_far", "hm_test_hold", "hm_tc_cgemm", "hm_plan_order_method",
            "hm_set_far_schedule", "hm_efie_fill", "hm_efie_far", "hm_set_update_schedule",
-           "hm_set_pivot_schedule"]
+           "hm_set_pivot_schedule", "hm_plan_fill_closure"]
 
 KCLASS = ["scatter", "pivot", "panel", "update", "sweep_fwd", "sweep_bwd", "far1", "far2", "diag", "permute",
           "near", "dots", "vec", "small", "compress"]
@@ -105,6 +105,8 @@ def load(build_if_missing=True):
     L.hm_plan_order.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]
     L.hm_plan_order_method.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]
     L.hm_plan_fill.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, ctypes.c_int64]
+    L.hm_plan_fill_closure.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p,
+                                       ctypes.c_int64]
     L.hm_plan_far.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p,
                               _i64p, _i64p, ctypes.c_int32, _i64p, _i64p]
     L.hm_profile.argtypes = [vp, ctypes.c_int32]
@@ -306,17 +308,19 @@ def hm_plan_order_method(method, n_leaves, t, s):
     return out
 
 
-def hm_plan_fill(n_blocks, i, j):
-    """Host-only symbolic fill (no GPU): returns [S_0, S_1, ...] as lists."""
+def hm_plan_fill(n_blocks, i, j, closure=1):
+    """Host-only S_k lists (no GPU): closure 1 = the symbolic fill, 0 = no fill (the later
+    near-field neighbours, the null-field lists).  Returns [S_0, S_1, ...] as lists."""
     i = np.ascontiguousarray(i, dtype=np.int32)
     j = np.ascontiguousarray(j, dtype=np.int32)
     ptr = np.zeros(n_blocks + 1, dtype=np.int32)
     L = load()
-    code = L.hm_plan_fill(n_blocks, len(i), _p(i, _i32p), _p(j, _i32p), _p(ptr, _i32p), None, 0)
+    code = L.hm_plan_fill_closure(closure, n_blocks, len(i), _p(i, _i32p), _p(j, _i32p), _p(ptr, _i32p), None, 0)
     if code != HM_OK:
         raise HMError(code, "hm_plan_fill")
     idx = np.zeros(max(1, int(ptr[-1])), dtype=np.int32)
-    code = L.hm_plan_fill(n_blocks, len(i), _p(i, _i32p), _p(j, _i32p), _p(ptr, _i32p), _p(idx, _i32p), len(idx))
+    code = L.hm_plan_fill_closure(closure, n_blocks, len(i), _p(i, _i32p), _p(j, _i32p), _p(ptr, _i32p),
+                                  _p(idx, _i32p), len(idx))
     if code != HM_OK:
         raise HMError(code, "hm_plan_fill")
     return [idx[ptr[k]:ptr[k + 1]].tolist() for k in range(n_blocks)]

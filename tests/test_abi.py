@@ -67,6 +67,34 @@ def test_planner_random_graphs_match_oracle(hm):
         assert hm.hm_plan_fill(n, t, s) == schur.symbolic_fill(n, pairs)
 
 
+def test_planner_no_fill_lists_match_oracle(hm, sphere1920):
+    """The null-field lists (closure 0: the later near-field neighbours only) equal the
+    oracle's, on random graphs and on the 1920-unknown sphere in RCM order, and are contained
+    in the symbolic fill; other closure values are rejected."""
+    rng = np.random.default_rng(12)
+    for n in (1, 2, 7, 40, 130):
+        m = rng.integers(0, 3 * n + 1)
+        t = rng.integers(0, n, m)
+        s = rng.integers(0, n, m)
+        pairs = list(zip(t.tolist(), s.tolist()))
+        got = hm.hm_plan_fill(n, t, s, closure=0)
+        assert got == schur.near_lists(n, pairs)
+        full = hm.hm_plan_fill(n, t, s)
+        assert all(set(a) <= set(b) for a, b in zip(got, full))
+    P = sphere1920
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    pos = np.empty(nl, dtype=np.int64)
+    pos[order] = np.arange(nl)
+    bi, bj = pos[P.near_t], pos[P.near_s]
+    pairs = list(zip(bi.tolist(), bj.tolist()))
+    got = hm.hm_plan_fill(nl, bi, bj, closure=0)
+    assert got == schur.near_lists(nl, pairs)
+    assert sum(map(len, got)) < sum(map(len, hm.hm_plan_fill(nl, bi, bj)))
+    with pytest.raises(hm.HMError):
+        hm.hm_plan_fill(3, [0, 1], [1, 2], closure=2)
+
+
 def test_planner_sloan_matches_oracle(hm, sphere1920, sphere480):
     import efie_problem as ep
     for P in (sphere480, sphere1920, ep.build("plate1160")):
