@@ -379,6 +379,27 @@ def test_block_jacobi_exact_on_block_diagonal_systems():
     assert np.linalg.norm(x - np.linalg.solve(Z, b)) / np.linalg.norm(x) < 1e-12
 
 
+def test_preconditioned_spectrum_clusters_near_one(sphere480):
+    """Fig. 13's observation, as a soft check on the 480-unknown sphere: the eigenvalues of the
+    Eq. 28 operator A = D^{-1} [D + L^{-1} Z_F L^{-T}] lie closer to 1 than those of Z scaled by
+    its own diagonal, and A is exactly the identity when the far field is left out (Eq. 21)."""
+    P = sphere480
+    nl = len(P.leaf_ptr) - 1
+    order = ordering.rcm(nl, list(zip(P.near_t.tolist(), P.near_s.tolist())))
+    S = krylov.System(P, schur.setup(P, order, fill_tol=0.0))
+    n = S.n
+    I = np.eye(n, dtype=np.complex128)
+    A = np.stack([S.apply_A(I[:, j]) for j in range(n)], axis=1)
+    Z = np.stack([S.Z_orig(I[:, j]) for j in range(n)], axis=1)
+    lam_a = np.linalg.eigvals(A)
+    lam_z = np.linalg.eigvals(Z / np.diag(Z)[:, None])
+    da, dz = np.abs(lam_a - 1.0), np.abs(lam_z - 1.0)
+    assert np.median(da) < 0.5 * np.median(dz) and np.max(da) < np.max(dz)
+    # without Z_F the operator is D^{-1} D = I
+    N = np.stack([S.D_solve(S.D_mul(I[:, j])) for j in range(n)], axis=1)
+    assert np.abs(N - I).max() < 1e-10
+
+
 # ---- null-field comparison preconditioner (Sec. 3: one-sided near-field scaling without fill) ----
 def _cycle(rng, far=None):
     """Five blocks on a cycle 0-1-2-3-4-0: eliminating block 0 couples 1 and 4, which are not
