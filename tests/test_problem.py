@@ -154,6 +154,29 @@ def test_plate_level2_leaf_sizes_match_table5():
     assert set(g["table5_block_sizes"]) <= set(sizes)
 
 
+def test_plate_level2_table6_nnz_is_a_full_block_triangle():
+    """Table 6's level-2 "no compression" count equals, within 0.3%, the full block lower
+    triangle (plus the identity diagonal) on the 16 leaves of this octree, whose sizes Table 5
+    fixes: at level 2 the paper's fill is complete.  The near field read here (Eq. 8 with
+    eta = 1) fills 85-100% of that triangle -- the narrower level-2 near field of reading 4;
+    at level 3, where the fill is partial, the counts agree (next test)."""
+    g = golden("paper_plate_5985.txt")
+    V, T = mesh.plate(45, 5.0, jitter=0.0)
+    rwg = mesh.RWG(V, T)
+    root, leaves, perm = tree.build_tree(rwg.midpoints(), vertices=V, fixed_level=2)
+    blo, bhi = rwg.support_boxes()
+    tree.attach_boxes(root, perm, blo, bhi)
+    near, far = tree.partition(root, 1.0)
+    nl = len(leaves)
+    sz = np.array([lf.hi - lf.lo for lf in leaves])
+    full = sum(int(sz[k] * sz[j]) for k in range(nl) for j in range(k + 1, nl)) + rwg.n
+    ref = g["table6_nnz_level2_uncompressed"][0]
+    assert abs(full - ref) / ref < 0.003
+    S = schur.symbolic_fill(nl, sorted({(min(a, b), max(a, b)) for a, b in near}))
+    nnz = sum(int(sz[k] * sz[j]) for k in range(nl) for j in S[k]) + rwg.n
+    assert 0.85 * full <= nnz <= full
+
+
 def test_plate_level3_fill_nnz_matches_table6():
     """Uncompressed scaling-coefficient NNZ (Table 6, oct-tree 3, no ordering) within 3%."""
     g = golden("paper_plate_5985.txt")
